@@ -1,0 +1,134 @@
+"""Pins of the CPU oracle's Ising application test (CPU only): the exact
+finite-lattice solution against brute force, the paper's printed exact row
+and Onsager's infinite-lattice result; the checkerboard Metropolis chain
+against the exact moments."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import ising_exact as X
+
+mp = pytest.importorskip("mpmath")
+BETA_C = float(np.log(1 + np.sqrt(2)) / 2)
+
+
+@pytest.mark.parametrize("beta", [0.2, 0.4, BETA_C, 0.6])
+def test_kaufman_matches_brute_force_4x4(beta):
+    lz, mE, mE2 = X.brute_force_moments(4, beta)
+    lz2, mE_, mE2_ = X.exact_moments(4, beta)
+    assert abs(lz - lz2) < 1e-10
+    assert abs(mE - mE_) < 1e-9
+    assert abs(mE2 - mE2_) < 1e-7
+
+
+def test_exact_row_of_table_1(golden):
+    # Table 1, row "exact": e = 1.106079207, C_V = 0.8616983594 (L = 1024,
+    # beta = 0.4).  The closed form evaluated at 40 digits gives
+    # 1.1060792037 and 0.8616983568: both within 4e-9 of the printed values,
+    # three orders of magnitude below the table's smallest statistical error
+    # (1.4e-6), so the printed row is read as carrying ~3e-9 numerical error.
+    g = golden["ising_exact_1024_beta04"]
+    e, cv = X.exact_e_cv(g["L"], g["beta"])
+    assert abs(e - g["e"]) < 5e-9
+    assert abs(cv - g["C_V"]) < 5e-9
+
+
+def test_finite_lattice_agrees_with_onsager_at_beta_04():
+    # Independent formula: Onsager's infinite-lattice free energy
+    # -beta f = ln(2 cosh 2K) + (1/2pi) int_0^pi ln[(1 + sqrt(1 - k^2 sin^2 t))/2] dt,
+    # k = 2 sinh 2K / cosh^2 2K.  At beta = 0.4 the correlation length is a
+    # few sites, so the L = 1024 torus equals the infinite lattice to 1e-12.
+    with mp.workdps(30):
+        def f(K):
+            k = 2 * mp.sinh(2 * K) / mp.cosh(2 * K) ** 2
+            return mp.log(2 * mp.cosh(2 * K)) + mp.quad(
+                lambda t: mp.log((1 + mp.sqrt(1 - k**2 * mp.sin(t) ** 2)) / 2), [0, mp.pi]) / (2 * mp.pi)
+        K = mp.mpf("0.4")
+        e_inf = float(mp.diff(f, K, 1))
+        cv_inf = float(K**2 * mp.diff(f, K, 2))
+    e, cv = X.exact_e_cv(1024, 0.4)
+    assert abs(e - e_inf) < 1e-12
+    assert abs(cv - cv_inf) < 1e-10
+
+
+def test_threshold_is_floor_of_2_32_boltzmann_factor():
+    with mp.workdps(50):
+        for beta in [0.1, 0.3, 0.4, BETA_C, 0.6, 2.0]:
+            for dE in (4, 8):
+                exact = int(mp.floor(mp.mpf(2) ** 32 * mp.exp(-mp.mpf(beta) * dE)))
+                assert O.ising_threshold(beta, dE) == exact
+    assert O.ising_threshold(50.0, 4) == 0
+
+
+def test_observables_of_simple_configurations():
+    L = 8
+    up = np.ones((L, L), dtype=np.int8)
+    assert O.ising_energy(up) == (-2 * L * L, L * L)
+    neel = np.fromfunction(lambda y, x: 1 - 2 * ((x + y) % 2), (L, L)).astype(np.int8)
+    assert O.ising_energy(neel) == (2 * L * L, 0)
+
+
+def test_initial_spins_are_balanced():
+    s = O.ising_init_spins(256, 99)
+    n = s.size
+    assert set(np.unique(s)) == {-1, 1}
+    assert abs(int(s.astype(np.int64).sum())) < 5 * np.sqrt(n)
+
+
+@pytest.mark.parametrize("kind", [O.XORWOW, O.XS1024W, O.PHILOX4X32_10, O.LCG64])
+@pytest.mark.parametrize("beta", [0.3, 0.4])
+def test_checkerboard_chain_reproduces_exact_energy(kind, beta):
+    # Application test of Sec. 2 on a lattice whose exact values are cheap:
+    # e and C_V of an 8x8 torus, estimated from 50 independent chunks.
+    L, chunks, per = 8, 50, 2000
+    e_chunks, cv_chunks = [], []
+    N = L * L
+    for c in range(chunks):
+        s0, _, _ = O.ising_run(L, beta, kind, 5000 + c, 200)  # equilibration
+        s, acc, nm = O.ising_run(L, beta, kind, 9000 + c, per, measure_every=1, spins=s0)
+        mE = acc[0] / nm
+        mE2 = acc[1] / nm
+        e_chunks.append(-mE / N)
+        cv_chunks.append(beta * beta * (mE2 - mE * mE) / N)
+    e_ex, cv_ex = X.exact_e_cv(L, beta)
+    e_est, e_err = np.mean(e_chunks), np.std(e_chunks, ddof=1) / np.sqrt(chunks)
+    cv_est, cv_err = np.mean(cv_chunks), np.std(cv_chunks, ddof=1) / np.sqrt(chunks)
+    assert abs(e_est - e_ex) < 4.5 * e_err, (e_est, e_ex, e_err)
+    # per-chunk variance estimates are biased by O(tau/per); allow that too
+    assert abs(cv_est - cv_ex) < 4.5 * cv_err + 0.02 * cv_ex, (cv_est, cv_ex, cv_err)
+
+
+def test_zero_temperature_energy_never_increases():
+    L = 16
+    s = O.ising_init_spins(L, 3)
+    E_prev = O.ising_energy(s)[0]
+    for t in range(20):
+        s, _, _ = O.ising_run(L, 50.0, O.XORWOW, 3 + t, 1, spins=s)
+        E = O.ising_energy(s)[0]
+        assert E <= E_prev
+        E_prev = E
+
+
+def test_isolated_flipped_spin_is_restored_at_zero_temperature():
+    L = 8
+    s = np.ones((L, L), dtype=np.int8)
+    s[3, 4] = -1  # colour (4 + 3) & 1 = 1; neighbours all +1, dE = -8
+    out, _, _ = O.ising_run(L, 50.0, O.PHILOX4X32_10, 1, 1, spins=s)
+    assert np.all(out == 1)
+
+
+def test_measurement_accumulators():
+    L = 8
+    s, acc, nm = O.ising_run(L, 0.4, O.XORWOW, 7, 10, measure_every=5)
+    assert nm == 2
+    s1, _, _ = O.ising_run(L, 0.4, O.XORWOW, 7, 5)
+    E1, M1 = O.ising_energy(s1)
+    E2, M2 = O.ising_energy(s)
+    assert acc.tolist() == [E1 + E2, E1 * E1 + E2 * E2, M1 * M1 + M2 * M2, abs(M1) + abs(M2)]
+
+
+def test_runs_are_deterministic_and_seeded():
+    a = O.ising_run(16, 0.4, O.MWC, 11, 7)[0]
+    b = O.ising_run(16, 0.4, O.MWC, 11, 7)[0]
+    c = O.ising_run(16, 0.4, O.MWC, 12, 7)[0]
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
