@@ -1,0 +1,237 @@
+/*
+ * rng_gb300.h -- C ABI of librng_gb300.so: per-thread pseudo-random streams
+ * for massively parallel simulations and their consumption by a
+ * checkerboard Metropolis update of the 2D Ising ferromagnet, after
+ * Manssen, Weigel and Hartmann, "Random number generators for massively
+ * parallel simulations on GPU" (arXiv:1204.6193).
+ *
+ * Problem statement (Sec. 1): many generator instances, one per thread,
+ * each producing its own stream, set up so that the streams are independent
+ * (by random seeding, by skip-ahead into sub-streams of one sequence, or by
+ * distinct keys), then consumed in place by the threads of a simulation.
+ *
+ * General conventions
+ *  - Every function returns a status (RNG_OK = 0 or an RNG_E* code).  No
+ *    function exits, throws or prints.  rng_last_error() gives a
+ *    thread-local one-line description of the last failure.
+ *  - Device pointers (d_*) are CUDA global-memory pointers owned by the
+ *    caller; host pointers (host_*) are ordinary host memory owned by the
+ *    caller.  Generator state, lattices and scratch buffers are owned by the
+ *    library and live on the device that was current at creation.
+ *  - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Generation and sweep calls are asynchronous on that stream;
+ *    calls that return host data (observables, get_state, get_spins)
+ *    synchronise it.
+ *  - Handles are not thread-safe: one host thread at a time per handle.
+ *  - A "stream" s_i[0], s_i[1], ... is the uint32 output sequence of
+ *    instance i.  A generation call with n_per_instance = K emits draws
+ *    s_i[p], ..., s_i[p+K-1] of every instance, p being the number of draws
+ *    already consumed, and advances every instance by K.
+ */
+#ifndef RNG_GB300_H
+#define RNG_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rng_s *rng_t;
+typedef struct ising_s *ising_t;
+
+/* Status codes. */
+enum {
+    RNG_OK = 0,
+    RNG_EINVAL = 1,       /* bad argument (null pointer, size, combination) */
+    RNG_ENOMEM = 2,       /* device or host allocation failed */
+    RNG_EUNSUPPORTED = 3, /* operation not defined for this generator */
+    RNG_ECUDA = 4,        /* a CUDA call failed (detail in rng_last_error) */
+    RNG_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
+    RNG_EBUSY = 6         /* no free slot or memory to admit a request */
+};
+
+/* Generator kinds (Sec. 2-7). */
+enum {
+    RNG_LCG32 = 0,          /* Sec. 2, Eq. (1): a = 1664525, c = 1013904223, m = 2^32 */
+    RNG_LCG64 = 1,          /* Sec. 2: a = 2862933555777941757, c = 1442695040888963407, m = 2^64; top 32 bits */
+    RNG_MWC = 2,            /* Sec. 3: multiply-with-carry, base 2^32, safe-prime multipliers */
+    RNG_XORWOW = 3,         /* Sec. 6: Marsaglia's 160-bit xorshift plus Weyl sequence */
+    RNG_PHILOX4X32_10 = 4,  /* Sec. 7: counter-based Philox4x32, 10 rounds */
+    RNG_XS1024W = 5,        /* Sec. 6, Listing 1: the paper's 1024-bit warp-shared xorshift plus Weyl */
+    RNG_MT19937_SHARED = 6  /* Sec. 5: MT19937, one block-shared state per generator */
+};
+
+/* Seeding flags (rng_create). */
+enum {
+    RNG_SEED_RANDOM = 0,    /* each instance seeded from its own SplitMix64 words */
+    RNG_SEED_LEAPFROG = 1,  /* LCGs only, Sec. 2 Eq. (2): instances interleave one serial sequence */
+    RNG_SEED_SUBSTREAM = 2, /* XS1024W only, Sec. 6: warp j starts 2^137 j steps into one sequence */
+    RNG_MWC_SAME_A = 4      /* MWC only, Sec. 3: one shared multiplier instead of one per instance */
+};
+
+/* Output layouts (rng_generate_*). */
+enum {
+    RNG_STEP_MAJOR = 0,     /* d_out[k * n + i] = draw k of instance i ("warp order", Sec. 6) */
+    RNG_INSTANCE_MAJOR = 1, /* d_out[i * K + k] ("single-thread order", Sec. 6) */
+    RNG_XOR_REDUCE = 2      /* consume in registers: d_out[i] = XOR of the K output words
+                               (u32 and f32 bit patterns); for normals the float sum */
+};
+
+/* Ising lattice layouts. */
+enum {
+    ISING_INT8 = 0,         /* one int8 (+1 or -1) per site */
+    ISING_MULTISPIN32 = 1   /* 32 same-colour sites per uint32, bit set = spin -1; L % 64 == 0 */
+};
+
+/* ---------------------------------------------------------------- streams */
+
+/* Creates n_instances generator instances of `kind` on the current device
+ * (Sec. 1: one instance per thread; for RNG_XS1024W an instance is one lane
+ * of a warp-shared 1024-bit state, Sec. 6, so n_instances must be a multiple
+ * of 32; for RNG_MT19937_SHARED an instance is one MT19937 generator whose
+ * 624-word state a thread block shares, Sec. 5).  `flags` is an OR of the
+ * RNG_SEED_* / RNG_MWC_SAME_A values valid for the kind, else
+ * RNG_EUNSUPPORTED.  The instances are unseeded until rng_seed.
+ * RNG_MWC without RNG_MWC_SAME_A needs n_instances distinct multipliers
+ * (more than 10^6 exist below 2^32, Sec. 3); beyond the table, RNG_EINVAL. */
+int rng_create(rng_t *out, int kind, uint64_t n_instances, uint32_t flags, void *cuda_stream);
+
+/* Like rng_create, but the handle holds instances [first, first + count) of
+ * an n_total-instance generator: seeding, leapfrog and sub-stream positions
+ * use the global instance index, so shards on several devices together give
+ * exactly the streams of one n_total handle.  XS1024W: first and count
+ * multiples of 32. */
+int rng_create_shard(rng_t *out, int kind, uint64_t n_total, uint64_t first, uint64_t count,
+                     uint32_t flags, void *cuda_stream);
+
+int rng_destroy(rng_t h);
+
+/* Seeds every instance from one 64-bit master seed, expanded by SplitMix64
+ * into words w_k = mix64(seed + (k+1) 0x9E3779B97F4A7C15) (the paper seeds
+ * instances "with an independent RNG", Sec. 4 and 6).  Per kind: LCG32 x_0 =
+ * low32(w_i); LCG64 x_0 = w_i; LEAPFROG: instance i starts at x_(i+1-n) of
+ * the serial sequence from w_0 and steps by (a_n, c_n), Eq. (2); MWC x =
+ * low32(w_i), c = high32(w_i) mod a_i; XORWOW (x,y),(z,w),(v,d) from
+ * w_3i..w_3i+2; Philox key = w_i, counter = block index; XS1024W lane l of
+ * warp j = low32(w_(32j+l)), or with SUBSTREAM base words from w_0..w_15 and
+ * warp j advanced by j 2^137 steps; MT generator g seeded with low32(w_g).
+ * Resets the draw position to 0. */
+int rng_seed(rng_t h, uint64_t seed);
+
+/* Advances every instance by n draws without producing them (Sec. 2 Eq. (2)
+ * for LCGs; v <- v a^n mod (a 2^32 - 1) for MWC; the n-th power of the
+ * GF(2) transition matrix for XORWOW and XS1024W, Sec. 6; a counter add for
+ * Philox, Sec. 7).  RNG_MT19937_SHARED: RNG_EUNSUPPORTED.  Allocates and
+ * frees device scratch on the handle's stream for the matrix kinds. */
+int rng_skipahead(rng_t h, uint64_t n);
+
+/* Raw 32-bit draws.  d_out holds n * n_per_instance words (n for
+ * RNG_XOR_REDUCE) in the chosen layout. */
+int rng_generate_u32(rng_t h, uint32_t *d_out, uint64_t n_per_instance, int layout, void *cuda_stream);
+
+/* Uniform floats u = (r >> 8) 2^-24 in [0, 1), exact in single precision
+ * (Sec. 2: u_n = x_n / m, here on the 24 high bits). */
+int rng_generate_f32(rng_t h, float *d_out, uint64_t n_per_instance, int layout, void *cuda_stream);
+
+/* Standard normal deviates by Box-Muller on consecutive pairs (r0, r1) of a
+ * stream: u1 = ((r0 >> 8) + 1) 2^-24, u2 = (r1 >> 8) 2^-24,
+ * z0 = sqrt(-2 ln u1) cos(2 pi u2), z1 = sqrt(-2 ln u1) sin(2 pi u2), in
+ * single precision (within 2e-6 of the exact values).  n_per_instance must
+ * be even.  The paper has no normal deviates; this is the conventional
+ * transform of its uniform output. */
+int rng_generate_normal(rng_t h, float *d_out, uint64_t n_per_instance, int layout, void *cuda_stream);
+
+/* Checkpoint: copies the full generator state (plus kind, sizes, flags and
+ * draw position) into host_buf.  With host_buf == NULL only *bytes is set
+ * to the required size.  rng_set_state restores a blob taken from a handle
+ * of the same kind, size and flags.  Counter-based and Weyl parts need no
+ * stored state beyond the position (Sec. 6 and 7). */
+int rng_get_state(rng_t h, void *host_buf, size_t *bytes);
+int rng_set_state(rng_t h, const void *host_buf, size_t bytes);
+
+/* Kind, number of instances held, first global instance, and draws consumed. */
+int rng_info(rng_t h, int *kind, uint64_t *n_instances, uint64_t *first, uint64_t *position);
+
+/* The MWC multipliers in use: the descending list of a < 2^32 with a 2^32 - 1
+ * and a 2^31 - 1 prime (Sec. 3), entries [first, first + count) copied to
+ * host_out.  Found on the device by Miller-Rabin; cached per device. */
+int rng_mwc_multipliers(uint64_t first, uint64_t count, uint32_t *host_out);
+
+/* ------------------------------------------------------------------ Ising */
+
+/* Creates an L x L periodic 2D Ising ferromagnet (J = 1, zero field) at
+ * inverse temperature beta >= 0, updated by checkerboard Metropolis (Sec. 2,
+ * application test).  Colour of site (x, y) = (x + y) & 1; the colour-c
+ * sites are numbered q = y (L/2) + (x >> 1); stream s owns q in
+ * [sG, (s+1)G) of both colours, giving L^2/(2G) streams of generator
+ * `rng_kind` seeded by rng_seed(seed) semantics with `rng_flags`
+ * (RNG_MT19937_SHARED: RNG_EUNSUPPORTED; the paper ran no Ising test with
+ * it, Sec. 5).  Initial spins: site j = y L + x is +1 iff bit j % 64 of
+ * SplitMix64 word j / 64 of (seed XOR 0x5350494E) is set.  Requires L even,
+ * G dividing L^2/2 (and L^2/64 for the multispin layout), L % 64 == 0 for
+ * ISING_MULTISPIN32. */
+int ising_create(ising_t *out, uint32_t L, double beta, int layout, int rng_kind, uint32_t rng_flags,
+                 uint64_t seed, uint32_t G, void *cuda_stream);
+
+/* n_sweeps sweeps (colour 0 then colour 1).  In a half-sweep every stream
+ * draws one number per owned site in increasing q, whatever the energy
+ * change dE = 2 s_i sum_nn s_j, and the flip is accepted iff dE <= 0 or
+ * r < T[dE], T[dE] = floor(2^32 exp(-beta dE)) computed once in double.
+ * With measure_every > 0 the energy E and magnetisation M are measured
+ * after every measure_every-th sweep and accumulated (see
+ * ising_observables).  Persistent fused kernel: random numbers never leave
+ * registers and the lattice stays on chip between half-sweeps. */
+int ising_sweep(ising_t h, uint64_t n_sweeps, uint32_t measure_every, void *cuda_stream);
+
+/* Same result as ising_sweep, one kernel launch per half-sweep with the
+ * generator state and lattice in global memory (the baseline the
+ * persistent kernel is compared with). */
+int ising_sweep_plain(ising_t h, uint64_t n_sweeps, uint32_t measure_every, void *cuda_stream);
+
+/* Current E = -sum_bonds s_i s_j and M = sum_i s_i, and the accumulators
+ * acc = {sum E, sum E^2, sum M^2, sum |M|} over n_meas measurements (the
+ * quantities of Table 1: e = -<E>/N, C_V = beta^2 (<E^2> - <E>^2)/N).
+ * Synchronises the handle's stream.  Any output pointer may be NULL. */
+int ising_observables(ising_t h, int64_t *E, int64_t *M, int64_t acc[4], uint64_t *n_meas);
+
+/* Spins as int8 +-1, row-major y L + x (host_LxL holds L*L bytes). */
+int ising_get_spins(ising_t h, int8_t *host_LxL);
+int ising_set_spins(ising_t h, const int8_t *host_LxL);
+
+/* Generator state of the lattice's streams (see rng_get_state). */
+int ising_get_rng(ising_t h, rng_t *rng);
+
+int ising_destroy(ising_t h);
+
+/* ---------------------------------------------------------------- batched */
+
+/* n independent lattices of sizes L[b], inverse temperatures beta[b] and
+ * generator kinds rng_kind[b] (RNG_XORWOW or RNG_XS1024W or any per-thread
+ * kind), lattice b seeded with w_b of the master seed; int8 layout.
+ * Batching is not in the paper: it packs many application-test lattices
+ * into one persistent launch over a work list of (lattice, tile) items. */
+int ising_batch_create(ising_t *out, uint32_t n, const uint32_t *L, const double *beta,
+                       const int *rng_kind, uint64_t seed, uint32_t G, void *cuda_stream);
+
+/* All lattices advance n_sweeps sweeps in one persistent launch (captured in
+ * a CUDA graph and replayed when the same n_sweeps is requested again).
+ * Each lattice's result equals ising_sweep on that lattice alone. */
+int ising_batch_sweep(ising_t h, uint64_t n_sweeps, uint32_t measure_every, void *cuda_stream);
+
+/* Lattice `idx` of a batch: observables and spins as for single lattices. */
+int ising_batch_observables(ising_t h, uint32_t idx, int64_t *E, int64_t *M, int64_t acc[4],
+                            uint64_t *n_meas);
+int ising_batch_get_spins(ising_t h, uint32_t idx, int8_t *host_LxL);
+
+/* ----------------------------------------------------------------- errors */
+
+const char *rng_strerror(int status);
+const char *rng_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RNG_GB300_H */

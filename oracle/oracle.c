@@ -158,6 +158,10 @@ static uint64_t g_mwc_next_a = 0xffffffffULL; /* next candidate to test */
 static int mwc_extend(uint64_t count)
 {
     if (count <= g_mwc_count) return ORC_OK;
+    /* the table is a cache of a fixed list: grow it geometrically so that
+     * callers asking for one more entry at a time do not rescan */
+    if (count < 2 * g_mwc_count) count = 2 * g_mwc_count;
+    if (count < 4096) count = 4096;
     uint32_t *t = (uint32_t *)realloc(g_mwc_table, count * sizeof(uint32_t));
     if (!t) return ORC_ENOMEM;
     g_mwc_table = t;

@@ -1,0 +1,151 @@
+"""Python binding of librng_gb300.so (C ABI in include/rng_gb300.h).
+
+Argument marshalling only: every function calls the C entry point of the
+same name; device buffers are passed as integer addresses (for example
+``tensor.data_ptr()``) and CUDA streams as integer handles (for example
+``torch.cuda.current_stream().cuda_stream``).  A nonzero status raises
+:class:`RngError` carrying the library's own message.  There is no CPU
+fallback: without the built library the import fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librng_gb300.so")
+
+RNG_OK, RNG_EINVAL, RNG_ENOMEM, RNG_EUNSUPPORTED, RNG_ECUDA, RNG_ETIMEOUT, RNG_EBUSY = range(7)
+(RNG_LCG32, RNG_LCG64, RNG_MWC, RNG_XORWOW, RNG_PHILOX4X32_10, RNG_XS1024W,
+ RNG_MT19937_SHARED) = range(7)
+RNG_SEED_RANDOM, RNG_SEED_LEAPFROG, RNG_SEED_SUBSTREAM, RNG_MWC_SAME_A = 0, 1, 2, 4
+RNG_STEP_MAJOR, RNG_INSTANCE_MAJOR, RNG_XOR_REDUCE = 0, 1, 2
+ISING_INT8, ISING_MULTISPIN32 = 0, 1
+
+KIND_NAMES = {RNG_LCG32: "lcg32", RNG_LCG64: "lcg64", RNG_MWC: "mwc", RNG_XORWOW: "xorwow",
+              RNG_PHILOX4X32_10: "philox4x32_10", RNG_XS1024W: "xs1024w",
+              RNG_MT19937_SHARED: "mt19937_shared"}
+
+
+class RngError(RuntimeError):
+    def __init__(self, status: int, func: str, detail: str):
+        super().__init__(f"{func}: status {status}: {detail}")
+        self.status = status
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_1204_6193_gb300.build.build() "
+                      "(nvcc, sm_103a); there is no fallback implementation")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_u64, _u32, _i32, _f64, _p = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+_pp = ctypes.POINTER(ctypes.c_void_p)
+
+_SIGS = {
+    "rng_create": [_pp, _i32, _u64, _u32, _p],
+    "rng_create_shard": [_pp, _i32, _u64, _u64, _u64, _u32, _p],
+    "rng_destroy": [_p],
+    "rng_seed": [_p, _u64],
+    "rng_skipahead": [_p, _u64],
+    "rng_generate_u32": [_p, _p, _u64, _i32, _p],
+    "rng_generate_f32": [_p, _p, _u64, _i32, _p],
+    "rng_generate_normal": [_p, _p, _u64, _i32, _p],
+    "rng_get_state": [_p, _p, ctypes.POINTER(ctypes.c_size_t)],
+    "rng_set_state": [_p, _p, ctypes.c_size_t],
+    "rng_info": [_p, ctypes.POINTER(_i32), ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64)],
+    "rng_mwc_multipliers": [_u64, _u64, _p],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _i32
+_lib.rng_strerror.argtypes = [_i32]
+_lib.rng_strerror.restype = ctypes.c_char_p
+_lib.rng_last_error.argtypes = []
+_lib.rng_last_error.restype = ctypes.c_char_p
+
+
+def _call(name: str, *args) -> None:
+    st = getattr(_lib, name)(*args)
+    if st != RNG_OK:
+        raise RngError(st, name, _lib.rng_last_error().decode(errors="replace"))
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return None
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def library() -> ctypes.CDLL:
+    return _lib
+
+
+def rng_strerror(status: int) -> str:
+    return _lib.rng_strerror(status).decode()
+
+
+def rng_last_error() -> str:
+    return _lib.rng_last_error().decode(errors="replace")
+
+
+def rng_create(kind: int, n_instances: int, flags: int = 0, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _call("rng_create", ctypes.byref(h), kind, n_instances, flags, _stream(stream))
+    return h.value
+
+
+def rng_create_shard(kind: int, n_total: int, first: int, count: int, flags: int = 0, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _call("rng_create_shard", ctypes.byref(h), kind, n_total, first, count, flags, _stream(stream))
+    return h.value
+
+
+def rng_destroy(h: int) -> None:
+    _call("rng_destroy", h)
+
+
+def rng_seed(h: int, seed: int) -> None:
+    _call("rng_seed", h, seed & (2**64 - 1))
+
+
+def rng_skipahead(h: int, n: int) -> None:
+    _call("rng_skipahead", h, n)
+
+
+def rng_generate_u32(h: int, d_out: int, n_per_instance: int, layout: int = RNG_STEP_MAJOR, stream=None) -> None:
+    _call("rng_generate_u32", h, d_out, n_per_instance, layout, _stream(stream))
+
+
+def rng_generate_f32(h: int, d_out: int, n_per_instance: int, layout: int = RNG_STEP_MAJOR, stream=None) -> None:
+    _call("rng_generate_f32", h, d_out, n_per_instance, layout, _stream(stream))
+
+
+def rng_generate_normal(h: int, d_out: int, n_per_instance: int, layout: int = RNG_STEP_MAJOR, stream=None) -> None:
+    _call("rng_generate_normal", h, d_out, n_per_instance, layout, _stream(stream))
+
+
+def rng_get_state(h: int) -> bytes:
+    size = ctypes.c_size_t(0)
+    _call("rng_get_state", h, None, ctypes.byref(size))
+    buf = ctypes.create_string_buffer(size.value)
+    _call("rng_get_state", h, buf, ctypes.byref(size))
+    return buf.raw[: size.value]
+
+
+def rng_set_state(h: int, blob: bytes) -> None:
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _call("rng_set_state", h, buf, len(blob))
+
+
+def rng_info(h: int) -> dict:
+    k, n, f, p = _i32(), _u64(), _u64(), _u64()
+    _call("rng_info", h, ctypes.byref(k), ctypes.byref(n), ctypes.byref(f), ctypes.byref(p))
+    return {"kind": k.value, "n_instances": n.value, "first": f.value, "position": p.value}
+
+
+def rng_mwc_multipliers(first: int, count: int):
+    import numpy as np
+    out = np.zeros(count, dtype=np.uint32)
+    _call("rng_mwc_multipliers", first, count, out.ctypes.data)
+    return out

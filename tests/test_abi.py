@@ -1,0 +1,44 @@
+"""The C ABI library loads without a GPU and exports every function that
+include/*.h declares (no compute calls)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*([a-z_][a-z0-9_]*)\s*\(",
+                             text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ["rng_create", "rng_seed", "rng_skipahead", "rng_generate_u32", "rng_generate_f32",
+                 "rng_generate_normal", "ising_sweep", "ising_observables"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib_path = os.path.join(ROOT, "paper_1204_6193_gb300", "_build", "librng_gb300.so")
+    if not os.path.exists(lib_path):
+        pytest.fail("librng_gb300.so is not built (run __graft_entry__.build())")
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_without_gpu():
+    import paper_1204_6193_gb300 as R
+    assert R.rng_strerror(R.RNG_OK) == "ok"
+    assert "invalid" in R.rng_strerror(R.RNG_EINVAL)

@@ -1,0 +1,284 @@
+"""Parity of the CUDA generation path (through the C ABI) with the CPU
+oracle: bit-exact for integer draws and uniform floats, within 2e-6 for
+Box-Muller normals."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0x0123456789ABCDEF
+THREAD_KINDS = [O.LCG32, O.LCG64, O.MWC, O.XORWOW, O.PHILOX4X32_10, O.XS1024W]
+ALL_KINDS = THREAD_KINDS + [O.MT19937_SHARED]
+NORMAL_TOL = 2e-6  # absolute, for float32 Box-Muller against the double oracle
+
+
+@pytest.fixture(scope="module")
+def R():
+    import paper_1204_6193_gb300 as R
+    return R
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def run_gpu(R, torch, kind, n, Ks, *, flags=0, out="u32", layout=0, seed=SEED, skip=0, shard=None):
+    """Creates, seeds, optionally skips, then generates len(Ks) calls; returns list of numpy arrays."""
+    if shard is None:
+        h = R.rng_create(kind, n, flags)
+        n_local = n
+    else:
+        first, count = shard
+        h = R.rng_create_shard(kind, n, first, count, flags)
+        n_local = count
+    try:
+        R.rng_seed(h, seed)
+        if skip:
+            R.rng_skipahead(h, skip)
+        res = []
+        for K in Ks:
+            size = n_local if layout == R.RNG_XOR_REDUCE else n_local * K
+            dt = torch.int32 if out == "u32" else torch.float32
+            buf = torch.empty(size, dtype=dt, device="cuda")
+            fn = {"u32": R.rng_generate_u32, "f32": R.rng_generate_f32, "normal": R.rng_generate_normal}[out]
+            fn(h, buf.data_ptr(), K, layout)
+            torch.cuda.synchronize()
+            a = buf.cpu().numpy()
+            a = a.view(np.uint32) if out == "u32" else a
+            if layout == R.RNG_STEP_MAJOR:
+                a = a.reshape(K, n_local).T
+            elif layout == R.RNG_INSTANCE_MAJOR:
+                a = a.reshape(n_local, K)
+            res.append(a)
+        return res
+    finally:
+        R.rng_destroy(h)
+
+
+def as_f32_oracle(r):
+    return O.to_f32(r).astype(np.float32)
+
+
+# ---------------------------------------------------------------- config 1
+@pytest.mark.parametrize("kind", THREAD_KINDS)
+def test_plain_generation_16384x256_bit_exact(R, torch_cuda, kind):
+    n, K = 16384, 256
+    g = run_gpu(R, torch_cuda, kind, n, [K])[0]
+    o = O.generate(kind, SEED, n, K)
+    assert np.array_equal(g, o)
+
+
+def test_mt_64_generators_x_65536_bit_exact(R, torch_cuda):
+    n, K = 64, 65536
+    g = run_gpu(R, torch_cuda, O.MT19937_SHARED, n, [K], layout=1)[0]
+    o = O.generate(O.MT19937_SHARED, SEED, n, K)
+    assert np.array_equal(g, o)
+
+
+# ------------------------------------------------------ layouts and forms
+def ragged_n(kind):
+    if kind == O.XS1024W:
+        return 96
+    if kind == O.MT19937_SHARED:
+        return 5
+    return 1000  # not a multiple of 32: partial last warp
+
+
+@pytest.mark.parametrize("kind", ALL_KINDS)
+@pytest.mark.parametrize("layout", [0, 1])
+def test_u32_and_f32_layouts_ragged(R, torch_cuda, kind, layout):
+    n = ragged_n(kind)
+    K = 1501 if kind == O.MT19937_SHARED else 77
+    o = O.generate(kind, SEED, n, K)
+    g = run_gpu(R, torch_cuda, kind, n, [K], layout=layout)[0]
+    assert np.array_equal(g, o)
+    f = run_gpu(R, torch_cuda, kind, n, [K], layout=layout, out="f32")[0]
+    assert np.array_equal(f, as_f32_oracle(o))
+    assert f.min() >= 0.0 and f.max() < 1.0
+
+
+@pytest.mark.parametrize("kind", ALL_KINDS)
+@pytest.mark.parametrize("layout", [0, 1])
+def test_normals_within_2e6(R, torch_cuda, kind, layout):
+    n = ragged_n(kind)
+    K = 1250 if kind == O.MT19937_SHARED else 78
+    o = O.box_muller(O.generate(kind, SEED, n, K))
+    g = run_gpu(R, torch_cuda, kind, n, [K], layout=layout, out="normal")[0]
+    err = np.abs(g.astype(np.float64) - o).max()
+    assert err <= NORMAL_TOL, err
+
+
+@pytest.mark.parametrize("kind", ALL_KINDS)
+def test_consume_in_register_modes(R, torch_cuda, kind):
+    n = ragged_n(kind)
+    K = 1250 if kind == O.MT19937_SHARED else 78
+    o = O.generate(kind, SEED, n, K)
+    g = run_gpu(R, torch_cuda, kind, n, [K], layout=R.RNG_XOR_REDUCE)[0]
+    assert np.array_equal(g, np.bitwise_xor.reduce(o, axis=1))
+    gf = run_gpu(R, torch_cuda, kind, n, [K], layout=R.RNG_XOR_REDUCE, out="f32")[0].view(np.uint32)
+    assert np.array_equal(gf, np.bitwise_xor.reduce(as_f32_oracle(o).view(np.uint32), axis=1))
+    z = O.box_muller(o)
+    gz = run_gpu(R, torch_cuda, kind, n, [K], layout=R.RNG_XOR_REDUCE, out="normal")[0].astype(np.float64)
+    # per-term error <= 2e-6, plus float32 summation error gamma_(K-1) sum |z|
+    u = 2.0**-24
+    tol = K * NORMAL_TOL + (K - 1) * u / (1 - (K - 1) * u) * np.abs(z).sum(axis=1) * 2
+    assert np.all(np.abs(gz - z.sum(axis=1)) <= tol)
+
+
+# ------------------------------------------------- positions and seeding
+@pytest.mark.parametrize("kind", ALL_KINDS)
+def test_consecutive_calls_continue_the_streams(R, torch_cuda, kind):
+    n = ragged_n(kind)
+    Ks = [37, 91, 2] if kind != O.MT19937_SHARED else [37, 1300, 611]
+    o = O.generate(kind, SEED, n, sum(Ks))
+    g = run_gpu(R, torch_cuda, kind, n, Ks)
+    assert np.array_equal(np.concatenate(g, axis=1), o)
+
+
+@pytest.mark.parametrize("kind", [O.LCG32, O.LCG64, O.MWC, O.XORWOW, O.PHILOX4X32_10, O.XS1024W])
+@pytest.mark.parametrize("t", [1, 1003, 2**33 + 7])
+def test_skipahead(R, torch_cuda, kind, t):
+    n = 256 if kind != O.MWC else 64
+    g = run_gpu(R, torch_cuda, kind, n, [9], skip=t)[0]
+    o = O.generate(kind, SEED, n, 9, skip=t, jump=True)
+    assert np.array_equal(g, o)
+
+
+def test_skipahead_unsupported_for_mt(R, torch_cuda):
+    h = R.rng_create(R.RNG_MT19937_SHARED, 2)
+    try:
+        R.rng_seed(h, 1)
+        with pytest.raises(R.RngError) as e:
+            R.rng_skipahead(h, 5)
+        assert e.value.status == R.RNG_EUNSUPPORTED
+    finally:
+        R.rng_destroy(h)
+
+
+@pytest.mark.parametrize("kind", [O.LCG32, O.LCG64])
+def test_leapfrog_is_the_serial_sequence(R, torch_cuda, kind):
+    n, K = 1024, 64
+    g = run_gpu(R, torch_cuda, kind, n, [K], flags=O.SEED_LEAPFROG)[0]
+    o = O.generate(kind, SEED, n, K, flags=O.SEED_LEAPFROG)
+    assert np.array_equal(g, o)
+    serial = O.generate(kind, SEED, 1, n * K, flags=O.SEED_LEAPFROG)[0]
+    assert np.array_equal(g.T.ravel(), serial)
+
+
+def test_xs1024w_substream_seeding(R, torch_cuda):
+    n, K = 32 * 10, 40
+    g = run_gpu(R, torch_cuda, O.XS1024W, n, [K], flags=O.SEED_SUBSTREAM)[0]
+    o = O.generate(O.XS1024W, SEED, n, K, flags=O.SEED_SUBSTREAM)
+    assert np.array_equal(g, o)
+
+
+def test_mwc_same_a(R, torch_cuda):
+    g = run_gpu(R, torch_cuda, O.MWC, 500, [33], flags=O.MWC_SAME_A)[0]
+    assert np.array_equal(g, O.generate(O.MWC, SEED, 500, 33, flags=O.MWC_SAME_A))
+
+
+def test_mwc_multiplier_table_matches_oracle(R, torch_cuda):
+    n = 20000
+    assert np.array_equal(R.rng_mwc_multipliers(0, n), O.mwc_multipliers(n))
+    assert int(R.rng_mwc_multipliers(0, 1)[0]) == 4294967118
+
+
+@pytest.mark.parametrize("kind", ALL_KINDS)
+def test_shards_reproduce_the_whole(R, torch_cuda, kind):
+    n = 256 if kind != O.MT19937_SHARED else 6
+    K = 21
+    flags = O.SEED_LEAPFROG if kind == O.LCG32 else (O.SEED_SUBSTREAM if kind == O.XS1024W else 0)
+    whole = run_gpu(R, torch_cuda, kind, n, [K], flags=flags)[0]
+    cut = n // 2 if kind != O.XS1024W else 128
+    a = run_gpu(R, torch_cuda, kind, n, [K], flags=flags, shard=(0, cut))[0]
+    b = run_gpu(R, torch_cuda, kind, n, [K], flags=flags, shard=(cut, n - cut))[0]
+    assert np.array_equal(np.concatenate([a, b]), whole)
+    assert np.array_equal(whole, O.generate(kind, SEED, n, K, flags=flags))
+
+
+@pytest.mark.parametrize("kind", ALL_KINDS)
+def test_checkpoint_restore(R, torch_cuda, kind):
+    torch = torch_cuda
+    n = ragged_n(kind)
+    h = R.rng_create(kind, n)
+    try:
+        R.rng_seed(h, SEED)
+        buf = torch.empty(n * 50, dtype=torch.int32, device="cuda")
+        R.rng_generate_u32(h, buf.data_ptr(), 50, 1)
+        blob = R.rng_get_state(h)
+        R.rng_generate_u32(h, buf.data_ptr(), 50, 1)
+        a = buf.cpu().numpy().view(np.uint32).reshape(n, 50).copy()
+        R.rng_set_state(h, blob)
+        R.rng_generate_u32(h, buf.data_ptr(), 50, 1)
+        b = buf.cpu().numpy().view(np.uint32).reshape(n, 50)
+        assert np.array_equal(a, b)
+        assert np.array_equal(a, O.generate(kind, SEED, n, 50, skip=50))
+        assert R.rng_info(h)["position"] == 100
+    finally:
+        R.rng_destroy(h)
+
+
+def test_argument_errors(R, torch_cuda):
+    with pytest.raises(R.RngError) as e:
+        R.rng_create(R.RNG_XS1024W, 33)
+    assert e.value.status == R.RNG_EINVAL
+    with pytest.raises(R.RngError) as e:
+        R.rng_create(R.RNG_XORWOW, 64, R.RNG_SEED_LEAPFROG)
+    assert e.value.status == R.RNG_EUNSUPPORTED
+    with pytest.raises(R.RngError):
+        R.rng_create(99, 64)
+    with pytest.raises(R.RngError):
+        R.rng_create(R.RNG_LCG32, 0)
+    h = R.rng_create(R.RNG_LCG32, 64)
+    try:
+        with pytest.raises(R.RngError):
+            R.rng_generate_u32(h, 0, 4)  # unseeded
+        R.rng_seed(h, 1)
+        with pytest.raises(R.RngError):
+            R.rng_generate_normal(h, 1 << 20, 3)  # odd count of normals
+        with pytest.raises(R.RngError):
+            R.rng_generate_u32(h, 0, 4)  # null output
+    finally:
+        R.rng_destroy(h)
+
+
+# ------------------------------------------------ full size (config 2)
+@pytest.mark.parametrize("kind", ALL_KINDS)
+def test_full_size_sampled(R, torch_cuda, kind):
+    """2^30 outputs per call in the bench's launch configuration, checked on
+    sampled instances (every draw of each sampled instance)."""
+    torch = torch_cuda
+    if kind == O.MT19937_SHARED:
+        n, K, layout = 4096, 1 << 18, 1
+    else:
+        n, K, layout = 1 << 20, 1024, 0
+    flags = O.SEED_SUBSTREAM if kind == O.XS1024W else 0
+    h = R.rng_create(kind, n, flags)
+    try:
+        R.rng_seed(h, SEED)
+        buf = torch.empty(n * K, dtype=torch.int32, device="cuda")
+        R.rng_generate_u32(h, buf.data_ptr(), K, layout)
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(kind)
+        if kind == O.XS1024W:
+            samp = sorted({0, 31, 32, n - 1, *rng.integers(0, n, 6).tolist()})
+        else:
+            samp = sorted({0, 1, n - 1, *rng.integers(0, n, 24).tolist()})
+        view = buf.view(K, n) if layout == 0 else buf.view(n, K)
+        for i in samp:
+            g = (view[:, i] if layout == 0 else view[i]).cpu().numpy().view(np.uint32)
+            o = O.generate(kind, SEED, n, K, flags=flags, i_lo=i, i_hi=i + 1)[0]
+            assert np.array_equal(g, o), i
+        del buf
+    finally:
+        R.rng_destroy(h)
+
+
+def test_mwc_full_table_matches_oracle(R, torch_cuda):
+    n = 1 << 20
+    assert np.array_equal(R.rng_mwc_multipliers(0, n), O.mwc_multipliers(n))
