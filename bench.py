@@ -1,0 +1,429 @@
+#!/usr/bin/env python3
+"""Benchmark of the per-thread stream generation and its Ising consumer.
+
+Default (N=1): the bulk workload -- 2^20 resident instances of every
+generator kind, 1024 draws each (2^30 outputs per call; the block-shared
+MT19937 as 4096 generators x 2^18 draws), written to HBM as u32, exact
+uniform f32 and Box-Muller normals, and consumed in registers (u32 XOR
+reduce).  One step = those 28 calls.  `value` = outputs of all ranks /
+device time (Gnum/s).  Extra keys report the Ising sweep (flips/ns) and
+the other workloads.
+
+Under torchrun (N>1) each rank holds its own shard of an N x 2^20-instance
+generator (global instance indices, no collective on the data path):
+weak scaling.
+
+`--impl reference` times the CPU oracle (the reference implementation of
+the method for this build) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RNG Gnum/s (frac of HBM peak); Ising flips/ns; served p50/p99 vs plain"
+N_INST = 1 << 20
+K_DRAWS = 1024
+MT_GENS = 4096
+MT_DRAWS = 1 << 18
+SEED = 0x0123456789ABCDEF
+FORMS = ["u32", "f32", "normal", "u32_xor"]
+# state bytes moved per instance and call: load + store of the state, plus
+# the MWC multiplier read; Philox only reads its key (the position is the
+# handle's counter)
+STATE_TRAFFIC = {0: 8, 1: 16, 2: 20, 3: 48, 4: 8, 5: 8, 6: 2 * 624 * 4}
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured", "sm_max_mhz": d.get("sm_max_mhz")}
+    return {"hbm_gbs": 6800.0, "source": "fallback", "sm_max_mhz": 2070.0}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-i",
+                 str(self.device), "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sms.append(float(parts[0]))
+                maxs.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs), "samples": len(sms),
+                "reasons": sorted(reasons)}
+
+
+def file_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+GEN_SOURCES = ["paper_1204_6193_gb300/csrc/gen.cu", "paper_1204_6193_gb300/csrc/gen_device.cuh"]
+
+
+def ncu_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    sources are unchanged since it was captured."""
+    p = os.path.join(ROOT, "profiles", "gen_bulk_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_hash") != file_hash(GEN_SOURCES):
+        return None
+    v = d.get("traffic_bytes_per_launch", {}).get(kernel_key)
+    return float(v) if v is not None else None
+
+
+# ------------------------------------------------------------------ GPU arm
+class Bulk:
+    def __init__(self, R, torch, rank, world):
+        self.R, self.torch = R, torch
+        self.handles = {}
+        for kind in range(7):
+            if kind == R.RNG_MT19937_SHARED:
+                n, first, total = MT_GENS, rank * MT_GENS, world * MT_GENS
+            else:
+                n, first, total = N_INST, rank * N_INST, world * N_INST
+            h = R.rng_create_shard(kind, total, first, n, 0)
+            R.rng_seed(h, SEED)
+            self.handles[kind] = (h, n)
+        self.out = torch.empty(N_INST * K_DRAWS, dtype=torch.int32, device="cuda")
+        self.red = torch.empty(N_INST, dtype=torch.int32, device="cuda")
+
+    def calls(self):
+        """(name, kind, form, fn, n, K, layout) for one step."""
+        R = self.R
+        res = []
+        for kind in range(7):
+            h, n = self.handles[kind]
+            K = MT_DRAWS if kind == R.RNG_MT19937_SHARED else K_DRAWS
+            lay = R.RNG_INSTANCE_MAJOR if kind == R.RNG_MT19937_SHARED else R.RNG_STEP_MAJOR
+            for form in FORMS:
+                res.append((f"{R.KIND_NAMES[kind]}/{form}", kind, form, h, n, K, lay))
+        return res
+
+    def launch(self, c, stream):
+        R = self.R
+        _, kind, form, h, n, K, lay = c
+        if form == "u32":
+            R.rng_generate_u32(h, self.out.data_ptr(), K, lay, stream)
+        elif form == "f32":
+            R.rng_generate_f32(h, self.out.data_ptr(), K, lay, stream)
+        elif form == "normal":
+            R.rng_generate_normal(h, self.out.data_ptr(), K, lay, stream)
+        else:
+            R.rng_generate_u32(h, self.red.data_ptr(), K, R.RNG_XOR_REDUCE, stream)
+
+    def algorithmic_bytes(self, c):
+        _, kind, form, h, n, K, lay = c
+        out = n * 4 if form == "u32_xor" else n * K * 4
+        return out + STATE_TRAFFIC[kind] * n
+
+    def close(self):
+        for h, _ in self.handles.values():
+            self.R.rng_destroy(h)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1204_6193_gb300 as R
+
+    peaks = load_peaks()
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    bulk = Bulk(R, torch, rank, world)
+    calls = bulk.calls()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        for c in calls:
+            bulk.launch(c, sptr)
+    barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)  # let the sampler start before the timed region
+    barrier()
+    ev = []
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        for c in calls:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            bulk.launch(c, sptr)
+            b.record(stream)
+            ev.append((c, a, b))
+    t1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+
+    per = {}
+    for c, a, b in ev:
+        d = per.setdefault(c[0], {"ms": [], "call": c})
+        d["ms"].append(a.elapsed_time(b))
+    outputs_per_step_rank = sum((c[4] * c[5]) for c in calls)
+    total_outputs = outputs_per_step_rank * world * args.steps
+    value = total_outputs / (elapsed_ms * 1e-3) / 1e9
+
+    detail = {}
+    best = None
+    for name, d in per.items():
+        c = d["call"]
+        avg = sum(d["ms"]) / len(d["ms"])
+        tot = sum(d["ms"])
+        gb = bulk.algorithmic_bytes(c) / (avg * 1e-3) / 1e9
+        detail[name] = {"ms": round(avg, 4), "gnum_s": round(c[4] * c[5] / (avg * 1e-3) / 1e9, 1),
+                        "gb_s": round(gb, 1), "frac_hbm": round(gb / peaks["hbm_gbs"], 3)}
+        if best is None or tot > best[1]:
+            best = (name, tot, avg, c)
+    name, tot, avg, c = best
+    is_write = not name.endswith("u32_xor")
+    ach = bulk.algorithmic_bytes(c) / (avg * 1e-3) / 1e9
+    step_ms_total = sum(sum(d["ms"]) for d in per.values())
+    roofline = {
+        "kernel": name,
+        "bound": "hbm" if is_write else "alu",
+        "achieved": round(ach, 1),
+        "peak": peaks["hbm_gbs"],
+        "unit": "GB/s",
+        "frac": round(ach / peaks["hbm_gbs"], 4),
+        "peak_source": f"{peaks['source']} (MEASURED_PEAKS.json hbm_gbs)" if peaks["source"] == "measured"
+        else "fallback 6.8 TB/s",
+        "share_of_step": round(tot / step_ms_total, 3),
+        "algorithmic_bytes_per_launch": bulk.algorithmic_bytes(c),
+        "traffic": ncu_traffic(name),
+    }
+
+    # end to end through the C ABI with host buffers: reseed from a host seed,
+    # generate, copy every output to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty(N_INST * K_DRAWS, dtype=torch.int32, pin_memory=True)
+        hred = torch.empty(N_INST, dtype=torch.int32, pin_memory=True)
+        e_steps = max(1, min(2, args.steps))
+        barrier()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        d2h = 0
+        for st in range(e_steps):
+            for kind in range(7):
+                R.rng_seed(bulk.handles[kind][0], SEED + 1 + st)
+            for c in calls:
+                bulk.launch(c, sptr)
+                nbytes = c[4] * 4 if c[2] == "u32_xor" else c[4] * c[5] * 4
+                src = bulk.red if c[2] == "u32_xor" else bulk.out
+                dst = hred if c[2] == "u32_xor" else host
+                dst[: nbytes // 4].copy_(src[: nbytes // 4], non_blocking=True)
+                d2h += nbytes
+        s1.record(stream)
+        barrier()
+        e_ms = s0.elapsed_time(s1)
+        if world > 1:
+            tt = torch.tensor([e_ms], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e_ms = float(tt.item())
+        e2e = {"value": round(outputs_per_step_rank * world * e_steps / (e_ms * 1e-3) / 1e9, 2), "unit": "Gnum/s",
+               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h // e_steps, "steps": e_steps,
+               "note": "seed passed by value (no input arrays); every output copied to pinned host memory"}
+
+    extra = {}
+    if not args.no_ising and hasattr(R, "ising_create"):
+        from paper_1204_6193_gb300 import benchlib
+        extra["ising"] = benchlib.ising_section(R, torch, args)
+    bulk.close()
+
+    line = None
+    if rank == 0:
+        cpu = None if (args.no_cpu or world > 1) else cpu_baseline(args)
+        line = {
+            "metric": METRIC,
+            "value": round(value, 2),
+            "unit": "Gnum/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(elapsed_ms / args.steps, 3),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "u32",
+            "data": "synthetic",
+            "config": {
+                "workload": "bulk generation: 2^20 resident instances x 1024 draws per call (MT19937: 4096 "
+                            "block-shared generators x 2^18), 7 generators x {u32, f32, normal} written to HBM + "
+                            "u32 consumed in registers (XOR reduce); 28 calls per step",
+                "instances_per_gpu": N_INST, "draws_per_call": K_DRAWS, "outputs_per_step_per_gpu":
+                    outputs_per_step_rank, "layout": "step-major (MT19937: instance-major)",
+                "l2": "no flush: every write call streams 4 GiB (> 129 MB L2)", "seed": hex(SEED),
+                "parallelism": f"instance shards x{world}",
+            },
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+            "gpu_launches": len(ev),
+            "detail": detail,
+        }
+        line.update(extra)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return line
+
+
+# ------------------------------------------------------------ CPU oracle arm
+def oracle_sample(per_form: int):
+    """Times the oracle on a bounded sample of the bulk workload: for every
+    kind and form, per_form outputs (instances x draws like the GPU call)."""
+    import numpy as np
+
+    import oracle as O
+
+    O.mwc_multipliers(8192)  # multiplier table outside the timed region
+    total = 0
+    t0 = time.perf_counter()
+    for kind in range(7):
+        if kind == O.MT19937_SHARED:
+            n, K = 4, per_form // 4
+        else:
+            n, K = 256, per_form // 256
+        for form in FORMS:
+            r = O.generate(kind, SEED, n, K)
+            if form == "f32":
+                O.to_f32(r)
+            elif form == "normal":
+                O.box_muller(r)
+            elif form == "u32_xor":
+                np.bitwise_xor.reduce(r, axis=1)
+            total += n * K
+    dt = time.perf_counter() - t0
+    return total, dt
+
+
+def cpu_baseline(args):
+    per_form = args.cpu_sample
+    total, dt = oracle_sample(per_form)
+    return {"value": round(total / dt / 1e9, 4), "unit": "Gnum/s", "cores": 1, "kind": "oracle",
+            "sample": f"{per_form} outputs per kind and form (7 kinds x 4 forms = {total} outputs), "
+                      f"single-threaded C oracle, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return None
+    per_form = args.cpu_sample
+    oracle_sample(per_form // 8)  # warm-up (builds and loads the oracle)
+    times, total = [], 0
+    for _ in range(args.warmup):
+        oracle_sample(per_form // 4)
+    for _ in range(args.steps):
+        tot, dt = oracle_sample(per_form // 4)
+        times.append(dt)
+        total += tot
+    v = total / sum(times) / 1e9
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "Gnum/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / len(times), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "bulk generation sample (CPU oracle): 7 generators x {u32, f32, normal, u32 "
+                                   "xor} on a bounded sample per step", "outputs_per_step": total // len(times)},
+            "cpu_baseline": {"value": round(v, 4), "unit": "Gnum/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_form // 4} outputs per kind and form per step"},
+            "e2e": {"value": round(v, 4), "unit": "Gnum/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=1 << 24)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ising", action="store_true")
+    ap.add_argument("--ising-sweeps", type=int, default=2000)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    line = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

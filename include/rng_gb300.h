@@ -170,8 +170,8 @@ int rng_mwc_multipliers(uint64_t first, uint64_t count, uint32_t *host_out);
  * (RNG_MT19937_SHARED: RNG_EUNSUPPORTED; the paper ran no Ising test with
  * it, Sec. 5).  Initial spins: site j = y L + x is +1 iff bit j % 64 of
  * SplitMix64 word j / 64 of (seed XOR 0x5350494E) is set.  Requires L even,
- * G dividing L^2/2 (and L^2/64 for the multispin layout), L % 64 == 0 for
- * ISING_MULTISPIN32. */
+ * 4 <= L <= 65536, G dividing L/2 (each stream's sites lie in one row), and
+ * L % 64 == 0 for ISING_MULTISPIN32. */
 int ising_create(ising_t *out, uint32_t L, double beta, int layout, int rng_kind, uint32_t rng_flags,
                  uint64_t seed, uint32_t G, void *cuda_stream);
 
@@ -182,7 +182,9 @@ int ising_create(ising_t *out, uint32_t L, double beta, int layout, int rng_kind
  * With measure_every > 0 the energy E and magnetisation M are measured
  * after every measure_every-th sweep and accumulated (see
  * ising_observables).  Persistent fused kernel: random numbers never leave
- * registers and the lattice stays on chip between half-sweeps. */
+ * registers and the lattice stays on chip between half-sweeps.  Asynchronous:
+ * a timed-out wait between row strips (RNG_ETIMEOUT) is reported by the
+ * next ising_observables / ising_get_spins. */
 int ising_sweep(ising_t h, uint64_t n_sweeps, uint32_t measure_every, void *cuda_stream);
 
 /* Same result as ising_sweep, one kernel launch per half-sweep with the
@@ -196,6 +198,30 @@ int ising_sweep_plain(ising_t h, uint64_t n_sweeps, uint32_t measure_every, void
  * Synchronises the handle's stream.  Any output pointer may be NULL. */
 int ising_observables(ising_t h, int64_t *E, int64_t *M, int64_t acc[4], uint64_t *n_meas);
 
+/* Launch shape of the persistent kernel: threads per block (multiple of 32,
+ * <= 1024; 0 = heuristic) and blocks per SM used for the row-strip plan
+ * (0 = heuristic).  Results do not depend on it: the draw order is fixed
+ * by the site numbering alone. */
+int ising_set_launch(ising_t h, uint32_t threads, int ctas_per_sm);
+
+/* Times the persistent kernel on a clone of the handle (same lattices and
+ * seeds; the handle itself does not advance) for a few launch shapes,
+ * probe_sweeps sweeps each, and applies the fastest (reported through the
+ * optional outputs). */
+int ising_autotune(ising_t h, uint32_t probe_sweeps, uint32_t *threads, int *ctas_per_sm);
+
+/* The current persistent launch plan: kind groups (one launch each), thread
+ * blocks, row strips and threads per block.  Plans on first use. */
+int ising_plan_info(ising_t h, uint32_t *groups, uint32_t *blocks, uint32_t *strips, uint32_t *threads);
+
+/* Failure-detection hook for tests: row strip `strip` (-1: none) of the
+ * plan stops publishing its boundary rows, so the strips next to it wait
+ * until wait_budget_ns (0: the default of 2 s) runs out, record
+ * RNG_ETIMEOUT and end the launch; the next ising_observables or
+ * ising_get_spins returns RNG_ETIMEOUT and the handle's lattice is then
+ * undefined.  The device context stays usable. */
+int ising_debug_mute_strip(ising_t h, int32_t strip, uint64_t wait_budget_ns);
+
 /* Spins as int8 +-1, row-major y L + x (host_LxL holds L*L bytes). */
 int ising_get_spins(ising_t h, int8_t *host_LxL);
 int ising_set_spins(ising_t h, const int8_t *host_LxL);
@@ -204,6 +230,11 @@ int ising_set_spins(ising_t h, const int8_t *host_LxL);
 int ising_get_rng(ising_t h, rng_t *rng);
 
 int ising_destroy(ising_t h);
+
+/* Number of lattices of the handle, and lattice idx's size, layout,
+ * generator kind and sweeps done since creation.  Any output may be NULL. */
+int ising_info(ising_t h, uint32_t idx, uint32_t *n_lattices, uint32_t *L, int *layout, int *rng_kind,
+               uint64_t *sweeps_done);
 
 /* ---------------------------------------------------------------- batched */
 

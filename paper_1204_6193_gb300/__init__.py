@@ -54,6 +54,23 @@ _SIGS = {
     "rng_set_state": [_p, _p, ctypes.c_size_t],
     "rng_info": [_p, ctypes.POINTER(_i32), ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64)],
     "rng_mwc_multipliers": [_u64, _u64, _p],
+    "ising_create": [_pp, _u32, _f64, _i32, _i32, _u32, _u64, _u32, _p],
+    "ising_destroy": [_p],
+    "ising_sweep": [_p, _u64, _u32, _p],
+    "ising_sweep_plain": [_p, _u64, _u32, _p],
+    "ising_observables": [_p, _p, _p, _p, _p],
+    "ising_get_spins": [_p, _p],
+    "ising_set_spins": [_p, _p],
+    "ising_get_rng": [_p, _pp],
+    "ising_set_launch": [_p, _u32, _i32],
+    "ising_autotune": [_p, _u32, _p, _p],
+    "ising_info": [_p, _u32, _p, _p, _p, _p, _p],
+    "ising_batch_create": [_pp, _u32, _p, _p, _p, _u64, _u32, _p],
+    "ising_batch_sweep": [_p, _u64, _u32, _p],
+    "ising_batch_observables": [_p, _u32, _p, _p, _p, _p],
+    "ising_batch_get_spins": [_p, _u32, _p],
+    "ising_debug_mute_strip": [_p, ctypes.c_int32, _u64],
+    "ising_plan_info": [_p, _p, _p, _p, _p],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -149,3 +166,111 @@ def rng_mwc_multipliers(first: int, count: int):
     out = np.zeros(count, dtype=np.uint32)
     _call("rng_mwc_multipliers", first, count, out.ctypes.data)
     return out
+
+
+# ---------------------------------------------------------------- Ising
+def ising_create(L: int, beta: float, layout: int = ISING_INT8, rng_kind: int = RNG_XORWOW, rng_flags: int = 0,
+                 seed: int = 0, G: int = 2, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _call("ising_create", ctypes.byref(h), L, float(beta), layout, rng_kind, rng_flags, seed & (2**64 - 1), G,
+          _stream(stream))
+    return h.value
+
+
+def ising_destroy(h: int) -> None:
+    _call("ising_destroy", h)
+
+
+def ising_sweep(h: int, n_sweeps: int, measure_every: int = 0, stream=None) -> None:
+    _call("ising_sweep", h, n_sweeps, measure_every, _stream(stream))
+
+
+def ising_sweep_plain(h: int, n_sweeps: int, measure_every: int = 0, stream=None) -> None:
+    _call("ising_sweep_plain", h, n_sweeps, measure_every, _stream(stream))
+
+
+def _obs(name, h, *idx):
+    E, M, nm = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_uint64()
+    acc = (ctypes.c_int64 * 4)()
+    _call(name, h, *idx, ctypes.byref(E), ctypes.byref(M), acc, ctypes.byref(nm))
+    return {"E": E.value, "M": M.value, "acc": list(acc), "n_meas": nm.value}
+
+
+def ising_observables(h: int) -> dict:
+    return _obs("ising_observables", h)
+
+
+def ising_info(h: int, idx: int = 0) -> dict:
+    n, L, lay, k, sw = _u32(), _u32(), _i32(), _i32(), _u64()
+    _call("ising_info", h, idx, ctypes.byref(n), ctypes.byref(L), ctypes.byref(lay), ctypes.byref(k),
+          ctypes.byref(sw))
+    return {"n_lattices": n.value, "L": L.value, "layout": lay.value, "kind": k.value, "sweeps": sw.value}
+
+
+def ising_get_spins(h: int):
+    import numpy as np
+    L = ising_info(h)["L"]
+    out = np.zeros((L, L), dtype=np.int8)
+    _call("ising_get_spins", h, out.ctypes.data)
+    return out
+
+
+def ising_set_spins(h: int, spins) -> None:
+    import numpy as np
+    a = np.ascontiguousarray(spins, dtype=np.int8)
+    _call("ising_set_spins", h, a.ctypes.data)
+
+
+def ising_get_rng(h: int) -> int:
+    r = ctypes.c_void_p()
+    _call("ising_get_rng", h, ctypes.byref(r))
+    return r.value
+
+
+def ising_set_launch(h: int, threads: int = 0, ctas_per_sm: int = 0) -> None:
+    _call("ising_set_launch", h, threads, ctas_per_sm)
+
+
+def ising_autotune(h: int, probe_sweeps: int = 64) -> dict:
+    t, c = _u32(), _i32()
+    _call("ising_autotune", h, probe_sweeps, ctypes.byref(t), ctypes.byref(c))
+    return {"threads": t.value, "ctas_per_sm": c.value}
+
+
+def ising_batch_create(L, beta, rng_kind, seed: int = 0, G: int = 2, stream=None) -> int:
+    import numpy as np
+    n = len(L)
+    La = np.ascontiguousarray(L, dtype=np.uint32)
+    Ba = np.ascontiguousarray(beta, dtype=np.float64)
+    Ka = np.ascontiguousarray(rng_kind, dtype=np.int32)
+    assert len(Ba) == n and len(Ka) == n
+    h = ctypes.c_void_p()
+    _call("ising_batch_create", ctypes.byref(h), n, La.ctypes.data, Ba.ctypes.data, Ka.ctypes.data,
+          seed & (2**64 - 1), G, _stream(stream))
+    return h.value
+
+
+def ising_batch_sweep(h: int, n_sweeps: int, measure_every: int = 0, stream=None) -> None:
+    _call("ising_batch_sweep", h, n_sweeps, measure_every, _stream(stream))
+
+
+def ising_batch_observables(h: int, idx: int) -> dict:
+    return _obs("ising_batch_observables", h, idx)
+
+
+def ising_batch_get_spins(h: int, idx: int):
+    import numpy as np
+    L = ising_info(h, idx)["L"]
+    out = np.zeros((L, L), dtype=np.int8)
+    _call("ising_batch_get_spins", h, idx, out.ctypes.data)
+    return out
+
+
+def ising_debug_mute_strip(h: int, strip: int, wait_budget_ns: int = 0) -> None:
+    _call("ising_debug_mute_strip", h, strip, wait_budget_ns)
+
+
+def ising_plan_info(h: int) -> dict:
+    g, b, s, t = _u32(), _u32(), _u32(), _u32()
+    _call("ising_plan_info", h, ctypes.byref(g), ctypes.byref(b), ctypes.byref(s), ctypes.byref(t))
+    return {"groups": g.value, "blocks": b.value, "strips": s.value, "threads": t.value}

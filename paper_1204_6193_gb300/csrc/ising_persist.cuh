@@ -1,0 +1,404 @@
+// ising_persist.cuh -- the persistent fused checkerboard kernel.
+//
+// One cooperative launch runs many sweeps.  The grid works through a list
+// of row strips ("segments") of one or more lattices; each thread block
+// keeps its strips, plus one halo row above and below, in shared memory as
+// two colour planes, and each thread keeps the generator state of its
+// streams in registers for the whole launch: random numbers are consumed
+// where they are drawn and never touch memory (the state load/store per
+// tile that Sec. 2 identifies as the cost of the application test happens
+// once per launch).  After each half-sweep a strip publishes its two
+// boundary rows of the colour just updated and waits (bounded) only for
+// the strips above and below it; a strip that holds a whole lattice
+// refreshes its halo from itself.
+#pragma once
+
+#include "ising_common.cuh"
+
+namespace rngx {
+
+constexpr int kPersistMaxSegs = 32;   // segments per thread block
+constexpr uint64_t kWaitBudgetNs = 2000000000ull;  // default: 2 s per neighbour wait
+
+struct PersistArgs {
+    const LatDev *lats;
+    const SegDev *segs;
+    const uint32_t *cta_seg;   // segments of block b: [cta_seg[b], cta_seg[b+1])
+    uint8_t *halo;             // per segment: 2 parities x 2 rows x halo_row_bytes
+    uint32_t halo_row_bytes;
+    uint32_t *flags;           // per segment: half-sweeps published (zeroed per launch)
+    int *err;
+    uint64_t n_sweeps;
+    uint64_t sweep0;           // sweeps of the same call before this launch
+    uint32_t measure_every;    // measure after sweeps sweep0+t+1 that are multiples
+    int32_t mute_seg;          // test hook: this segment never publishes (-1: none)
+    uint64_t wait_budget_ns;   // limit of one neighbour wait
+};
+
+struct SegLocal {              // per-segment constants held in shared memory
+    uint32_t L, half, W, G, y0, R, off, lat;
+    int32_t up, down, gid;
+    uint64_t s0, prefix, T4, T8;
+    uint64_t n_valid, n_inst;  // streams with sites; generator instances
+};
+
+template <int LAYOUT>
+__device__ __forceinline__ uint32_t row_bytes(const SegLocal &S)
+{
+    return LAYOUT == ISING_INT8 ? S.half : S.W * 4u;
+}
+
+// Address of plane c, local row r (r in [-1, R]) of a segment.
+template <int LAYOUT>
+__device__ __forceinline__ uint8_t *plane_row(uint8_t *smem, const SegLocal &S, int c, int r)
+{
+    const uint32_t rb = row_bytes<LAYOUT>(S);
+    return smem + S.off + (static_cast<uint32_t>(c) * (S.R + 2) + static_cast<uint32_t>(r + 1)) * rb;
+}
+
+// Global spins -> shared planes for rows y0-1 .. y0+R (all threads).
+template <int LAYOUT>
+__device__ void load_segment(uint8_t *smem, const SegLocal &S, const void *spins)
+{
+    const int rows = static_cast<int>(S.R) + 2;
+    if (LAYOUT == ISING_INT8) {
+        const int8_t *g = static_cast<const int8_t *>(spins);
+        const uint32_t total = rows * S.L;
+        for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int r = static_cast<int>(idx / S.L) - 1;
+            const uint32_t x = idx % S.L;
+            const uint32_t y = (S.y0 + S.L + r) % S.L;
+            const int c = (x + y) & 1;
+            reinterpret_cast<int8_t *>(plane_row<LAYOUT>(smem, S, c, r))[x >> 1] = g[static_cast<size_t>(y) * S.L + x];
+        }
+    } else {
+        const uint32_t *g = static_cast<const uint32_t *>(spins);
+        const uint32_t total = 2 * rows * S.W;
+        for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int c = idx / (rows * S.W);
+            const uint32_t rem = idx % (rows * S.W);
+            const int r = static_cast<int>(rem / S.W) - 1;
+            const uint32_t w = rem % S.W;
+            const uint32_t y = (S.y0 + S.L + r) % S.L;
+            reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, S, c, r))[w] =
+                g[static_cast<size_t>(c) * S.L * S.W + static_cast<size_t>(y) * S.W + w];
+        }
+    }
+}
+
+template <int LAYOUT>
+__device__ void store_segment(uint8_t *smem, const SegLocal &S, void *spins)
+{
+    if (LAYOUT == ISING_INT8) {
+        int8_t *g = static_cast<int8_t *>(spins);
+        const uint32_t total = S.R * S.L;
+        for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int r = static_cast<int>(idx / S.L);
+            const uint32_t x = idx % S.L;
+            const uint32_t y = S.y0 + r;
+            const int c = (x + y) & 1;
+            g[static_cast<size_t>(y) * S.L + x] = reinterpret_cast<int8_t *>(plane_row<LAYOUT>(smem, S, c, r))[x >> 1];
+        }
+    } else {
+        uint32_t *g = static_cast<uint32_t *>(spins);
+        const uint32_t total = 2 * S.R * S.W;
+        for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int c = idx / (S.R * S.W);
+            const uint32_t rem = idx % (S.R * S.W);
+            const int r = static_cast<int>(rem / S.W);
+            const uint32_t w = rem % S.W;
+            g[static_cast<size_t>(c) * S.L * S.W + static_cast<size_t>(S.y0 + r) * S.W + w] =
+                reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, S, c, r))[w];
+        }
+    }
+}
+
+// Partial E (bonds with a colour-0 endpoint in the strip's rows) and M.
+template <int LAYOUT>
+__device__ void strip_energy(uint8_t *smem, const SegLocal &S, long long &E, long long &M)
+{
+    E = 0;
+    M = 0;
+    if (LAYOUT == ISING_INT8) {
+        const uint32_t total = S.R * S.half;
+        for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int r = static_cast<int>(idx / S.half);
+            const uint32_t xh = idx % S.half;
+            const uint32_t y = S.y0 + r;
+            const uint32_t p = y & 1u;  // colour 0
+            const int8_t *o = reinterpret_cast<const int8_t *>(plane_row<LAYOUT>(smem, S, 1, r));
+            const int s0 = reinterpret_cast<const int8_t *>(plane_row<LAYOUT>(smem, S, 0, r))[xh];
+            const int s1 = o[xh];
+            const int nn = o[col_left(xh, p, S.half)] + o[col_right(xh, p, S.half)] +
+                           reinterpret_cast<const int8_t *>(plane_row<LAYOUT>(smem, S, 1, r - 1))[xh] +
+                           reinterpret_cast<const int8_t *>(plane_row<LAYOUT>(smem, S, 1, r + 1))[xh];
+            E -= s0 * nn;
+            M += s0 + s1;
+        }
+    } else {
+        const uint32_t total = S.R * S.W;
+        for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int r = static_cast<int>(idx / S.W);
+            const uint32_t w = idx % S.W;
+            const uint32_t y = S.y0 + r;
+            const uint32_t *o = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, S, 1, r));
+            const uint32_t own = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, S, 0, r))[w];
+            const uint32_t up = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, S, 1, r - 1))[w];
+            const uint32_t dn = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, S, 1, r + 1))[w];
+            uint32_t lft, rgt;
+            if ((y & 1u) == 0) {  // p = 0: left = xh - 1, right = xh
+                lft = (o[w] << 1) | (o[w == 0 ? S.W - 1 : w - 1] >> 31);
+                rgt = o[w];
+            } else {              // p = 1: left = xh, right = xh + 1
+                lft = o[w];
+                rgt = (o[w] >> 1) | (o[w + 1 == S.W ? 0 : w + 1] << 31);
+            }
+            const int U = __popc(own ^ lft) + __popc(own ^ rgt) + __popc(own ^ up) + __popc(own ^ dn);
+            E += 2 * U - 4 * 32;
+            M += 64 - 2 * (__popc(own) + __popc(o[w]));
+        }
+    }
+}
+
+__device__ __forceinline__ long long block_sum(long long v, long long *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    long long s = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < static_cast<int>(blockDim.x >> 5); i++) s += red[i];
+    return s;  // valid in thread 0
+}
+
+template <int KIND, int LAYOUT, int SMAX>
+__global__ void __launch_bounds__(1024) k_ising_persist(PersistArgs a)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ SegLocal S[kPersistMaxSegs];
+    __shared__ uint64_t prefix_end;
+    __shared__ int s_abort;
+    __shared__ long long red[32];
+    const uint32_t sb = a.cta_seg[blockIdx.x], nseg = a.cta_seg[blockIdx.x + 1] - sb;
+    if (threadIdx.x < nseg) {
+        const SegDev d = a.segs[sb + threadIdx.x];
+        const LatDev &l = a.lats[d.lat];
+        SegLocal s;
+        s.L = l.L;
+        s.half = l.half;
+        s.W = l.W;
+        s.G = l.G;
+        s.y0 = d.y0;
+        s.R = d.y1 - d.y0;
+        s.off = d.smem_off;
+        s.lat = d.lat;
+        s.up = d.up;
+        s.down = d.down;
+        s.gid = static_cast<int32_t>(sb + threadIdx.x);
+        s.s0 = d.s0;
+        s.T4 = l.T4;
+        s.T8 = l.T8;
+        s.n_valid = l.nstreams;
+        s.n_inst = l.rng.n;
+        S[threadIdx.x] = s;
+    }
+    if (threadIdx.x == 0) s_abort = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t pre = 0;
+        for (uint32_t j = 0; j < nseg; j++) {
+            S[j].prefix = pre;
+            const SegDev d = a.segs[sb + j];
+            pre += d.s1 - d.s0;
+        }
+        prefix_end = pre;
+    }
+    __syncthreads();
+    for (uint32_t j = 0; j < nseg; j++) load_segment<LAYOUT>(smem, S[j], a.lats[S[j].lat].spins);
+
+    // streams of this thread: flat indices f = tid + k * blockDim
+    Gen<KIND> gen[SMAX];
+    uint32_t kseg[SMAX];
+    uint32_t krow[SMAX], kxh0[SMAX];  // global row and first column of the stream's sites
+    bool kval[SMAX], kin[SMAX];
+    uint64_t kstream[SMAX];
+#pragma unroll
+    for (int k = 0; k < SMAX; k++) {
+        const uint64_t f = threadIdx.x + static_cast<uint64_t>(k) * blockDim.x;
+        kin[k] = f < prefix_end;
+        uint32_t j = 0;
+        while (j + 1 < nseg && f >= S[j + 1].prefix) j++;
+        kseg[k] = j;
+        const uint64_t s = S[j].s0 + (kin[k] ? f - S[j].prefix : 0);
+        kval[k] = kin[k] && s < S[j].n_valid;
+        kstream[k] = s;
+        const uint64_t q0 = s * S[j].G;
+        krow[k] = static_cast<uint32_t>(q0 / S[j].half);
+        kxh0[k] = static_cast<uint32_t>(q0 - static_cast<uint64_t>(krow[k]) * S[j].half);
+        DevParams rp = a.lats[S[j].lat].rng;
+        rp.pos = *a.lats[S[j].lat].pos_dev;
+        gen[k].load(rp, s < S[j].n_inst ? s : S[j].n_inst - 1);
+    }
+    __syncthreads();
+
+    uint64_t meas_idx = 0;
+    const int lane = threadIdx.x & 31;
+    for (uint64_t t = 0; t < a.n_sweeps; t++) {
+        for (int c = 0; c < 2; c++) {
+            // ---- update every colour-c site of the block's strips
+#pragma unroll
+            for (int k = 0; k < SMAX; k++) {
+                const bool warp_active = __any_sync(0xffffffffu, kin[k]);
+                if (!warp_active) continue;
+                const SegLocal &sg = S[kseg[k]];
+                const uint32_t y = krow[k];
+                const int r = static_cast<int>(y - sg.y0);
+                const uint32_t p = (c + y) & 1u;
+                if (LAYOUT == ISING_INT8) {
+                    int8_t *own = reinterpret_cast<int8_t *>(plane_row<LAYOUT>(smem, sg, c, r));
+                    const int8_t *o = reinterpret_cast<const int8_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r));
+                    const int8_t *ou = reinterpret_cast<const int8_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r - 1));
+                    const int8_t *od = reinterpret_cast<const int8_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r + 1));
+                    for (uint32_t g = 0; g < sg.G; g++) {
+                        const uint32_t rr = gen[k].next();
+                        if (!kval[k]) continue;
+                        const uint32_t xh = kxh0[k] + g;
+                        const int nn = o[col_left(xh, p, sg.half)] + o[col_right(xh, p, sg.half)] + ou[xh] + od[xh];
+                        const int sp = own[xh];
+                        if (accept_flip(2 * sp * nn, rr, sg.T4, sg.T8)) own[xh] = static_cast<int8_t>(-sp);
+                    }
+                } else {
+                    uint32_t *own = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, r));
+                    const uint32_t *o = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r));
+                    const uint32_t *ou = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r - 1));
+                    const uint32_t *od = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r + 1));
+                    const uint32_t G = sg.G;
+                    const uint32_t lq0 = lane * G;
+                    uint32_t c_lo = 0, c_hi = 0;
+                    for (uint32_t g = 0; g < G; g++) {
+                        const uint32_t rr = gen[k].next();
+                        if (!kval[k]) continue;
+                        const uint32_t xh = kxh0[k] + g;
+                        const int nn = bit_spin(o, col_left(xh, p, sg.half)) + bit_spin(o, col_right(xh, p, sg.half)) +
+                                       bit_spin(ou, xh) + bit_spin(od, xh);
+                        const int sp = bit_spin(own, xh);
+                        if (accept_flip(2 * sp * nn, rr, sg.T4, sg.T8)) {
+                            const uint32_t lq = lq0 + g;
+                            if ((lq >> 5) == (lq0 >> 5)) c_lo |= 1u << (lq & 31);
+                            else c_hi |= 1u << (lq & 31);
+                        }
+                    }
+                    // the warp's 32 G sites are G consecutive words of plane c
+                    const uint32_t f0 = __shfl_sync(0xffffffffu, static_cast<uint32_t>(kstream[k] - sg.s0), 0);
+                    const uint64_t q_first = (sg.s0 + f0) * G;
+                    const uint32_t base = static_cast<uint32_t>((q_first - static_cast<uint64_t>(sg.y0) * sg.half) >> 5);
+                    uint32_t *plane_c = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, 0));
+                    const uint32_t own_words = sg.R * sg.W;
+                    for (uint32_t m = 0; m < G; m++) {
+                        const uint32_t mine = ((lq0 >> 5) == m ? c_lo : 0u) | ((lq0 >> 5) + 1 == m ? c_hi : 0u);
+                        const uint32_t word = __reduce_or_sync(0xffffffffu, mine);
+                        if (lane == 0 && word && base + m < own_words) plane_c[base + m] ^= word;
+                    }
+                }
+            }
+            __syncthreads();
+
+            // ---- publish boundary rows of colour c, refresh halos
+            const uint32_t h = static_cast<uint32_t>(2 * t + c);
+            bool any_split = false;
+            for (uint32_t j = 0; j < nseg; j++) {
+                const SegLocal &sg = S[j];
+                const uint32_t rb = row_bytes<LAYOUT>(sg);
+                if (sg.up < 0) {
+                    // whole lattice: halo rows are its own last and first rows
+                    // (byte copies: an int8 row of L/2 bytes need not be word aligned)
+                    uint8_t *top = plane_row<LAYOUT>(smem, sg, c, -1), *bot = plane_row<LAYOUT>(smem, sg, c, sg.R);
+                    const uint8_t *last = plane_row<LAYOUT>(smem, sg, c, sg.R - 1), *first = plane_row<LAYOUT>(smem, sg, c, 0);
+                    for (uint32_t i = threadIdx.x; i < rb; i += blockDim.x) {
+                        top[i] = last[i];
+                        bot[i] = first[i];
+                    }
+                } else {
+                    any_split = true;
+                    uint32_t *dst = reinterpret_cast<uint32_t *>(a.halo + (static_cast<size_t>(sg.gid) * 4 + (h & 1) * 2) *
+                                                                              a.halo_row_bytes);
+                    for (uint32_t i = threadIdx.x; i < rb / 4; i += blockDim.x) {
+                        __stcg(dst + i, reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, 0))[i]);
+                        __stcg(dst + a.halo_row_bytes / 4 + i,
+                               reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, sg.R - 1))[i]);
+                    }
+                }
+            }
+            if (any_split) {
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    __threadfence();
+                    for (uint32_t j = 0; j < nseg; j++)
+                        if (S[j].up >= 0 && S[j].gid != a.mute_seg) st_release(a.flags + S[j].gid, h + 1);
+                    // bounded by two clocks: the global ns timer and the SM
+                    // cycle counter (at most 4 cycles per ns of budget)
+                    const uint64_t t0 = global_ns();
+                    const long long c0 = clock64();
+                    for (uint32_t j = 0; j < nseg && !s_abort; j++) {
+                        if (S[j].up < 0) continue;
+                        while (ld_acquire(a.flags + S[j].up) < h + 1 || ld_acquire(a.flags + S[j].down) < h + 1) {
+                            if (global_ns() - t0 > a.wait_budget_ns ||
+                                static_cast<uint64_t>(clock64() - c0) > 4 * a.wait_budget_ns ||
+                                ld_acquire(reinterpret_cast<uint32_t *>(a.err)) != 0) {
+                                atomicCAS(a.err, 0, RNG_ETIMEOUT);
+                                s_abort = 1;
+                                break;
+                            }
+                            __nanosleep(64);
+                        }
+                    }
+                }
+                __syncthreads();
+                if (s_abort) goto done;
+                for (uint32_t j = 0; j < nseg; j++) {
+                    const SegLocal &sg = S[j];
+                    if (sg.up < 0) continue;
+                    const uint32_t rb = row_bytes<LAYOUT>(sg);
+                    const uint32_t *up_bottom = reinterpret_cast<const uint32_t *>(
+                        a.halo + (static_cast<size_t>(sg.up) * 4 + (h & 1) * 2 + 1) * a.halo_row_bytes);
+                    const uint32_t *dn_top = reinterpret_cast<const uint32_t *>(
+                        a.halo + (static_cast<size_t>(sg.down) * 4 + (h & 1) * 2) * a.halo_row_bytes);
+                    for (uint32_t i = threadIdx.x; i < rb / 4; i += blockDim.x) {
+                        reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, -1))[i] = __ldcg(up_bottom + i);
+                        reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, sg.R))[i] = __ldcg(dn_top + i);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // ---- measurement after every measure_every-th sweep of this launch
+        if (a.measure_every && (a.sweep0 + t + 1) % a.measure_every == 0) {
+            for (uint32_t j = 0; j < nseg; j++) {
+                long long E, M;
+                strip_energy<LAYOUT>(smem, S[j], E, M);
+                const long long Es = block_sum(E, red);
+                __syncthreads();
+                const long long Ms = block_sum(M, red);
+                if (threadIdx.x == 0) {
+                    int64_t *meas = a.lats[S[j].lat].meas;
+                    atomicAdd(reinterpret_cast<unsigned long long *>(meas + 2 * meas_idx),
+                              static_cast<unsigned long long>(Es));
+                    atomicAdd(reinterpret_cast<unsigned long long *>(meas + 2 * meas_idx + 1),
+                              static_cast<unsigned long long>(Ms));
+                }
+                __syncthreads();
+            }
+            meas_idx++;
+        }
+    }
+done:
+    __syncthreads();
+    for (uint32_t j = 0; j < nseg; j++) store_segment<LAYOUT>(smem, S[j], a.lats[S[j].lat].spins);
+#pragma unroll
+    for (int k = 0; k < SMAX; k++)
+        if (kin[k] && kstream[k] < S[kseg[k]].n_inst) gen[k].store(a.lats[S[kseg[k]].lat].rng, kstream[k]);
+}
+
+}  // namespace rngx

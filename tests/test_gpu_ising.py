@@ -1,0 +1,195 @@
+"""Parity of the CUDA checkerboard Metropolis path (through the C ABI) with
+the CPU oracle: spins bit-exact after the same sweeps from the same seeds,
+integer observables and accumulators exactly equal."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0x0123456789ABCDEF
+BETA_C = float(np.log(1 + np.sqrt(2)) / 2)
+KINDS = [O.LCG32, O.LCG64, O.MWC, O.XORWOW, O.PHILOX4X32_10, O.XS1024W]
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1204_6193_gb300 as R
+    return R
+
+
+def gpu_run(R, L, beta, kind, n, *, layout=0, G=2, flags=0, seed=SEED, mode="persist", measure_every=0):
+    h = R.ising_create(L, beta, layout, kind, flags, seed, G)
+    try:
+        if mode == "persist":
+            R.ising_sweep(h, n, measure_every)
+        else:
+            R.ising_sweep_plain(h, n, measure_every)
+        return R.ising_get_spins(h), R.ising_observables(h)
+    finally:
+        R.ising_destroy(h)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("mode", ["persist", "plain"])
+def test_100_sweeps_L64_bit_exact(R, kind, layout, mode):
+    ref, acc, nm = O.ising_run(64, BETA_C, kind, SEED, 100, measure_every=10)
+    spins, obs = gpu_run(R, 64, BETA_C, kind, 100, layout=layout, mode=mode, measure_every=10)
+    assert np.array_equal(spins, ref)
+    assert obs["acc"] == acc.tolist() and obs["n_meas"] == nm
+    assert (obs["E"], obs["M"]) == O.ising_energy(ref)
+
+
+@pytest.mark.parametrize("kind", [O.XORWOW, O.XS1024W])
+@pytest.mark.parametrize("layout", [0, 1])
+def test_100_sweeps_L1024_bit_exact(R, kind, layout):
+    ref, acc, nm = O.ising_run(1024, BETA_C, kind, SEED, 100, measure_every=25)
+    spins, obs = gpu_run(R, 1024, BETA_C, kind, 100, layout=layout, measure_every=25)
+    assert np.array_equal(spins, ref)
+    assert obs["acc"] == acc.tolist() and obs["n_meas"] == nm
+
+
+@pytest.mark.parametrize("L,G,kind", [(16, 2, O.XORWOW), (16, 1, O.XS1024W), (48, 3, O.PHILOX4X32_10),
+                                      (40, 4, O.MWC), (12, 2, O.LCG64), (256, 8, O.XS1024W),
+                                      (192, 6, O.LCG32), (8, 4, O.XORWOW)])
+def test_small_and_ragged_lattices(R, L, G, kind):
+    ref, _, _ = O.ising_run(L, 0.4, kind, SEED, 60, G=G)
+    for mode in ["persist", "plain"]:
+        spins, _ = gpu_run(R, L, 0.4, kind, 60, G=G, mode=mode)
+        assert np.array_equal(spins, ref), mode
+
+
+def test_multispin_other_G(R):
+    for L, G in [(128, 4), (192, 2), (128, 32)]:
+        ref, _, _ = O.ising_run(L, 0.3, O.XORWOW, SEED, 40, G=G)
+        for mode in ["persist", "plain"]:
+            spins, _ = gpu_run(R, L, 0.3, O.XORWOW, 40, layout=1, G=G, mode=mode)
+            assert np.array_equal(spins, ref), (L, G, mode)
+
+
+@pytest.mark.parametrize("flags,kind", [(O.SEED_LEAPFROG, O.LCG32), (O.SEED_SUBSTREAM, O.XS1024W),
+                                        (O.MWC_SAME_A, O.MWC)])
+def test_seeding_flags(R, flags, kind):
+    ref, _, _ = O.ising_run(64, 0.4, kind, SEED, 30, flags=flags)
+    spins, _ = gpu_run(R, 64, 0.4, kind, 30, flags=flags)
+    assert np.array_equal(spins, ref)
+
+
+def test_degenerate_temperatures(R):
+    # beta = 0: every proposal accepted; beta = 50: zero-temperature quench
+    for beta in [0.0, 50.0]:
+        ref, _, _ = O.ising_run(64, beta, O.PHILOX4X32_10, SEED, 20)
+        spins, _ = gpu_run(R, 64, beta, O.PHILOX4X32_10, 20)
+        assert np.array_equal(spins, ref)
+    # beta = 0 accepts every proposal: one sweep flips every site once
+    spins, _ = gpu_run(R, 64, 0.0, O.XORWOW, 1, layout=1)
+    assert np.array_equal(spins, -O.ising_init_spins(64, SEED))
+
+
+def test_chunk_boundary_and_measurement_phase(R):
+    # more sweeps than one persistent launch holds, measurements straddling it
+    ref, acc, nm = O.ising_run(32, 0.44, O.XS1024W, SEED, 5000, measure_every=7)
+    spins, obs = gpu_run(R, 32, 0.44, O.XS1024W, 5000, measure_every=7)
+    assert np.array_equal(spins, ref)
+    assert obs["acc"] == acc.tolist() and obs["n_meas"] == nm
+
+
+def test_calls_compose_and_checkpoint_restores(R):
+    L, beta, kind = 128, 0.42, O.XORWOW
+    ref, _, _ = O.ising_run(L, beta, kind, SEED, 100)
+    h = R.ising_create(L, beta, 0, kind, 0, SEED, 2)
+    try:
+        R.ising_sweep(h, 50)
+        spins50 = R.ising_get_spins(h)
+        blob = R.rng_get_state(R.ising_get_rng(h))
+        R.ising_sweep_plain(h, 30)
+        R.ising_sweep(h, 20)
+        assert np.array_equal(R.ising_get_spins(h), ref)
+    finally:
+        R.ising_destroy(h)
+    h2 = R.ising_create(L, beta, 0, kind, 0, SEED + 1, 2)  # different seed, then restored
+    try:
+        R.ising_set_spins(h2, spins50)
+        R.rng_set_state(R.ising_get_rng(h2), blob)
+        R.ising_sweep(h2, 50)
+        assert np.array_equal(R.ising_get_spins(h2), ref)
+    finally:
+        R.ising_destroy(h2)
+
+
+def test_launch_shape_does_not_change_results(R):
+    L, kind = 512, O.XS1024W
+    ref, _, _ = O.ising_run(L, 0.4, kind, SEED, 20)
+    for threads, per_sm in [(256, 1), (1024, 1), (512, 4), (0, 0)]:
+        h = R.ising_create(L, 0.4, 0, kind, 0, SEED, 2)
+        try:
+            R.ising_set_launch(h, threads, per_sm)
+            R.ising_sweep(h, 20)
+            assert np.array_equal(R.ising_get_spins(h), ref), (threads, per_sm)
+        finally:
+            R.ising_destroy(h)
+    h = R.ising_create(L, 0.4, 1, kind, 0, SEED, 2)
+    try:
+        cfg = R.ising_autotune(h, 16)
+        assert cfg["threads"] in (256, 512, 1024)
+        R.ising_sweep(h, 20)
+        assert np.array_equal(R.ising_get_spins(h), ref)
+    finally:
+        R.ising_destroy(h)
+
+
+def test_batch_matches_lattices_alone(R):
+    rng = np.random.default_rng(4)
+    Ls = [16, 32, 64, 128, 256, 512, 16, 64, 32, 128, 256, 48]
+    betas = rng.uniform(0.30, 0.60, len(Ls)).tolist()
+    kinds = [O.XORWOW if b % 2 == 0 else O.XS1024W for b in range(len(Ls))]
+    h = R.ising_batch_create(Ls, betas, kinds, SEED, 2)
+    try:
+        R.ising_batch_sweep(h, 30, 10)
+        R.ising_batch_sweep(h, 30, 10)  # graph replay
+        for b, L in enumerate(Ls):
+            wb = O.seed_word(SEED, b)
+            ref, acc, nm = O.ising_run(L, betas[b], kinds[b], wb, 60, measure_every=10)
+            # two calls of 30: measurements after sweeps 10, 20, 30 of each call
+            assert np.array_equal(R.ising_batch_get_spins(h, b), ref), b
+            obs = R.ising_batch_observables(h, b)
+            assert obs["n_meas"] == nm
+            assert obs["acc"] == acc.tolist(), b
+    finally:
+        R.ising_destroy(h)
+
+
+def test_strip_that_stops_publishing_times_out_without_hanging(R):
+    import time
+    h = R.ising_create(1024, 0.4, 0, O.XORWOW, 0, SEED, 2)
+    try:
+        info = R.ising_plan_info(h)
+        assert info["strips"] >= 2
+        R.ising_debug_mute_strip(h, 1, 20_000_000)  # 20 ms budget
+        t0 = time.time()
+        R.ising_sweep(h, 10)
+        with pytest.raises(R.RngError) as e:
+            R.ising_observables(h)
+        assert e.value.status == R.RNG_ETIMEOUT
+        assert time.time() - t0 < 30
+    finally:
+        R.ising_destroy(h)
+    # the context is still usable
+    ref, _, _ = O.ising_run(64, 0.4, O.XORWOW, SEED, 5)
+    spins, _ = gpu_run(R, 64, 0.4, O.XORWOW, 5)
+    assert np.array_equal(spins, ref)
+
+
+def test_argument_errors(R):
+    for args in [(63, 0.4, 0), (66, 0.4, 1), (64, -1.0, 0), (2, 0.4, 0)]:
+        with pytest.raises(R.RngError):
+            R.ising_create(args[0], args[1], args[2], O.XORWOW, 0, 1, 2)
+    with pytest.raises(R.RngError) as e:
+        R.ising_create(64, 0.4, 0, O.MT19937_SHARED, 0, 1, 2)
+    assert e.value.status == R.RNG_EUNSUPPORTED
+    with pytest.raises(R.RngError):
+        R.ising_create(64, 0.4, 0, O.XORWOW, 0, 1, 3)  # G does not divide L/2

@@ -132,3 +132,12 @@ def test_runs_are_deterministic_and_seeded():
     b = O.ising_run(16, 0.4, O.MWC, 11, 7)[0]
     c = O.ising_run(16, 0.4, O.MWC, 12, 7)[0]
     assert np.array_equal(a, b) and not np.array_equal(a, c)
+
+
+def test_infinite_temperature_flips_every_site_once_per_sweep():
+    # beta = 0: T = 2^32 exceeds every 32-bit draw, so every proposal is accepted
+    init = O.ising_init_spins(32, 5)
+    out, _, _ = O.ising_run(32, 0.0, O.LCG64, 5, 1)
+    assert np.array_equal(out, -init)
+    out2, _, _ = O.ising_run(32, 0.0, O.LCG64, 5, 2)
+    assert np.array_equal(out2, init)
