@@ -127,6 +127,29 @@ int rng_seed(rng_t h, uint64_t seed);
  * frees device scratch on the handle's stream for the matrix kinds. */
 int rng_skipahead(rng_t h, uint64_t n);
 
+/* Same advance as rng_skipahead for RNG_XORWOW and RNG_XS1024W, on a state
+ * array the caller owns, with no device allocation of any kind: for callers
+ * that cannot allocate device memory (code inside a framework that owns
+ * every device allocation, or that must not let an allocation synchronise
+ * the device mid-sequence).  The paper has no counterpart; it is an
+ * interface variant of the skip-ahead of Sec. 6.
+ *  d_state: device array in the library's state layout, advanced in place:
+ *    RNG_XORWOW   6 consecutive arrays of n_instances words (x, y, z, w, v, d);
+ *    RNG_XS1024W  n_instances words, 32 consecutive words per warp state
+ *                 (n_instances a multiple of 32); the Weyl step count is the
+ *                 caller's and is not touched.
+ *  Scratch: one file-scope device array of 384 KiB (three 1024 x 1024-bit
+ *  matrices), held by every GPU that loads the library until the process
+ *  exits.  States wider than 1024 bits (RNG_MT19937_SHARED) are rejected
+ *  with RNG_EINVAL; kinds that skip without matrices (LCGs, MWC, Philox)
+ *  with RNG_EUNSUPPORTED.  The first call on a device looks up the array's
+ *  device address with that device current (make it before any stream
+ *  capture).  Every call on a device shares the one array: calls whose work
+ *  overlaps on the GPU (different streams, no ordering) race and give wrong
+ *  results; order them on one stream or synchronise between them.
+ *  Asynchronous on cuda_stream. */
+int rng_skipahead_noalloc(int kind, void *d_state, uint64_t n_instances, uint64_t n, void *cuda_stream);
+
 /* Raw 32-bit draws.  d_out holds n * n_per_instance words (n for
  * RNG_XOR_REDUCE) in the chosen layout. */
 int rng_generate_u32(rng_t h, uint32_t *d_out, uint64_t n_per_instance, int layout, void *cuda_stream);

@@ -54,6 +54,7 @@ _SIGS = {
     "rng_set_state": [_p, _p, ctypes.c_size_t],
     "rng_info": [_p, ctypes.POINTER(_i32), ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64)],
     "rng_mwc_multipliers": [_u64, _u64, _p],
+    "rng_skipahead_noalloc": [_i32, _p, _u64, _u64, _p],
     "ising_create": [_pp, _u32, _f64, _i32, _i32, _u32, _u64, _u32, _p],
     "ising_destroy": [_p],
     "ising_sweep": [_p, _u64, _u32, _p],
@@ -159,6 +160,10 @@ def rng_info(h: int) -> dict:
     k, n, f, p = _i32(), _u64(), _u64(), _u64()
     _call("rng_info", h, ctypes.byref(k), ctypes.byref(n), ctypes.byref(f), ctypes.byref(p))
     return {"kind": k.value, "n_instances": n.value, "first": f.value, "position": p.value}
+
+
+def rng_skipahead_noalloc(kind: int, d_state: int, n_instances: int, n: int, stream=None) -> None:
+    _call("rng_skipahead_noalloc", kind, d_state, n_instances, n, _stream(stream))
 
 
 def rng_mwc_multipliers(first: int, count: int):

@@ -239,6 +239,17 @@ int launch_seed(GenState &g, uint64_t seed, cudaStream_t s)
     return RNG_OK;
 }
 
+// Applies a precomputed t-step GF(2) matrix to every instance of an
+// xorshift kind (and advances XORWOW's Weyl word by t steps).
+int launch_matrix_apply(int kind, const DevParams &p, const uint32_t *M, uint64_t t, cudaStream_t s)
+{
+    const unsigned nb = blocks_for(p.n);
+    if (kind == RNG_XS1024W) k_skip_xs<<<nb, kBlock, 0, s>>>(p, M);
+    else k_skip_xorwow<<<nb, kBlock, 0, s>>>(p, M, t);
+    RNGX_CHECK_CUDA(cudaGetLastError());
+    return RNG_OK;
+}
+
 int launch_skipahead(GenState &g, uint64_t t, cudaStream_t s)
 {
     if (t == 0) return RNG_OK;

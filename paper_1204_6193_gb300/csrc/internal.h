@@ -82,4 +82,7 @@ int gf2_mul(int n, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_c, cuda
 int gf2_pow(int kind, uint64_t t, uint32_t *d_out, uint32_t *d_tmp1, uint32_t *d_tmp2, cudaStream_t s);
 int xs_substream_matrices(int levels, const uint32_t **d_P, cudaStream_t s);  // P_k = M^(2^(137+k))
 
+struct DevParams;
+int launch_matrix_apply(int kind, const DevParams &p, const uint32_t *M, uint64_t t, cudaStream_t s);
+
 }  // namespace rngx
