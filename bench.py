@@ -300,11 +300,14 @@ def run_gpu(args):
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h // e_steps, "steps": e_steps,
                "note": "seed passed by value (no input arrays); every output copied to pinned host memory"}
 
-    extra = {}
-    if not args.no_ising and hasattr(R, "ising_create"):
-        from paper_1204_6193_gb300 import benchlib
-        extra["ising"] = benchlib.ising_section(R, torch, args)
     bulk.close()
+    extra = {}
+    if rank == 0 and not args.no_ising:
+        extra["ising"] = ising_section(R, torch, args)
+    if rank == 0 and not args.no_batch:
+        extra["batched"] = batch_section(R, torch, args)
+    if rank == 0 and not args.no_serve:
+        extra["served"] = serve_section(R, torch, args)
 
     line = None
     if rank == 0:
@@ -343,6 +346,242 @@ def run_gpu(args):
         dist.barrier()
         dist.destroy_process_group()
     return line
+
+
+# ------------------------------------------------------------ Ising (config 3)
+BETA_C = 0.44068679350977151
+
+
+def _time_sweeps(R, torch, h, n, plain=False):
+    stream = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    (R.ising_sweep_plain if plain else R.ising_sweep)(h, n, 0, stream.cuda_stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    R.ising_observables(h)  # surfaces a timed-out wait, if any
+    return a.elapsed_time(b)
+
+
+def ising_section(R, torch, args):
+    """flips/ns = L^2 sweeps / device time, persistent fused kernel vs one
+    launch per half-sweep, at beta_c with G = 2 and a random start."""
+    out = {"beta": BETA_C, "G": 2, "unit": "flips/ns"}
+    n = args.ising_sweeps
+    for L in (1024, 64):
+        for layout, lname in ((R.ISING_INT8, "int8"), (R.ISING_MULTISPIN32, "multispin32")):
+            for kind in (R.RNG_XS1024W, R.RNG_XORWOW, R.RNG_PHILOX4X32_10, R.RNG_LCG32):
+                if L == 64 and kind not in (R.RNG_XS1024W, R.RNG_XORWOW):
+                    continue
+                h = R.ising_create(L, BETA_C, layout, kind, 0, SEED, 2)
+                try:
+                    tuned = R.ising_autotune(h, 64)
+                    R.ising_sweep(h, 50)
+                    ms = _time_sweeps(R, torch, h, n)
+                    nplain = max(20, n // 10)
+                    ms_plain = _time_sweeps(R, torch, h, nplain, plain=True)
+                    key = f"L{L}/{lname}/{R.KIND_NAMES[kind]}"
+                    out[key] = {
+                        "flips_per_ns": round(L * L * n / (ms * 1e6), 2),
+                        "us_per_sweep": round(1e3 * ms / n, 3),
+                        "plain_flips_per_ns": round(L * L * nplain / (ms_plain * 1e6), 3),
+                        "sweeps_timed": n, "launch": tuned, "plan": R.ising_plan_info(h),
+                    }
+                finally:
+                    R.ising_destroy(h)
+    return out
+
+
+# --------------------------------------------------------- batched (config 4)
+def batch_workload(n=256, seed=7):
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    Ls = (2 ** rng.integers(4, 10, n)).tolist()  # 16 .. 512, uniform over exponents
+    betas = rng.uniform(0.30, 0.60, n).tolist()
+    kinds = [3 if b % 2 == 0 else 5 for b in range(n)]  # xorwow / the paper's generator
+    return Ls, betas, kinds
+
+
+def batch_section(R, torch, args):
+    Ls, betas, kinds = batch_workload()
+    sites = sum(L * L for L in Ls)
+    n = args.batch_sweeps
+    h = R.ising_batch_create(Ls, betas, kinds, SEED, 2)
+    try:
+        tuned = R.ising_autotune(h, 32)
+        R.ising_batch_sweep(h, n)  # captures the graph; also warm-up
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        R.ising_batch_sweep(h, n, 0, stream.cuda_stream)  # graph replay
+        b.record(stream)
+        torch.cuda.synchronize()
+        R.ising_batch_observables(h, 0)
+        ms = a.elapsed_time(b)
+        plan = R.ising_plan_info(h)
+    finally:
+        R.ising_destroy(h)
+    # one launch per lattice: each lattice alone through ising_sweep
+    nb = max(10, n // 10)
+    hs = [R.ising_create(L, bt, 0, k, 0, int(O_seed_word(SEED, i)), 2) for i, (L, bt, k) in
+          enumerate(zip(Ls, betas, kinds))]
+    try:
+        for hh in hs:
+            R.ising_sweep(hh, 2)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream()
+        a.record(stream)
+        for hh in hs:
+            R.ising_sweep(hh, nb, 0, stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms_alone = a.elapsed_time(b)
+    finally:
+        for hh in hs:
+            R.ising_destroy(hh)
+    fl = sites * n / (ms * 1e6)
+    fl_alone = sites * nb / (ms_alone * 1e6)
+    return {"lattices": len(Ls), "sites": sites, "sweeps": n, "ms": round(ms, 2), "flips_per_ns": round(fl, 2),
+            "one_launch_per_lattice": {"sweeps": nb, "ms": round(ms_alone, 2), "flips_per_ns": round(fl_alone, 3)},
+            "speedup": round(fl / fl_alone, 2), "launch": tuned, "plan": plan,
+            "workload": "L log-uniform over {16..512}, beta U[0.30,0.60], xorwow/xs1024w alternating, G=2, "
+                        "one persistent launch per kind group, replayed from a CUDA graph"}
+
+
+def O_seed_word(seed, k):
+    """SplitMix64 word w_k of the master seed (the batch seeds lattice b
+    with w_b); computed here only to build the one-lattice-per-launch
+    baseline with the same seeds."""
+    m = (1 << 64) - 1
+    z = (seed + (k + 1) * 0x9E3779B97F4A7C15) & m
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+    return z ^ (z >> 31)
+
+
+# ---------------------------------------------------------- served (config 5)
+def serve_requests(R, n, seed=3):
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        r = R.rng_request_t()
+        if rng.random() < 0.8:
+            r.type = R.RNG_REQ_DRAW
+            r.kind = int(rng.integers(0, 6))
+            r.out = int(rng.integers(0, 3))
+            r.count = int(2 ** rng.uniform(10, 26)) // 2 * 2
+            r.seed = int(rng.integers(0, 64))
+            r.offset = int(rng.integers(0, 4096)) << 20
+        else:
+            r.type = R.RNG_REQ_SWEEP
+            r.kind = int(rng.choice([3, 5]))
+            r.L = int(rng.choice([64, 128, 256, 512, 1024]))
+            r.beta = float(rng.uniform(0.3, 0.6))
+            r.sweeps = int(10 ** rng.uniform(1, 3))
+            r.seed = int(rng.integers(0, 1 << 62))
+        reqs.append(r)
+    return reqs
+
+
+def _serve_run(R, srv, reqs, rate):
+    """Submits reqs with Poisson arrivals at `rate` per second (rate None: all
+    at once); returns (latencies in ms, wall seconds)."""
+    import threading
+    import numpy as np
+    rng = np.random.default_rng(1)
+    gaps = rng.exponential(1.0 / rate, len(reqs)) if rate else np.zeros(len(reqs))
+    tickets = [None] * len(reqs)
+    lat = [None] * len(reqs)
+    ready = threading.Semaphore(0)
+
+    def collector():
+        for i in range(len(reqs)):
+            ready.acquire()
+            res = R.rng_server_wait(srv, tickets[i], 600.0)
+            lat[i] = (res.t_done_ns - res.t_submit_ns) / 1e6
+            R.rng_server_fetch(srv, tickets[i], None, 0)
+
+    th = threading.Thread(target=collector)
+    th.start()
+    t0 = time.perf_counter()
+    due = t0
+    for i, r in enumerate(reqs):
+        due += gaps[i]
+        while True:
+            now = time.perf_counter()
+            if now >= due:
+                break
+            time.sleep(min(due - now, 0.0005))
+        tickets[i] = R.rng_server_submit(srv, r)
+        ready.release()
+    th.join()
+    return lat, time.perf_counter() - t0
+
+
+def _plain_run(R, torch, reqs, n_set):
+    """The same requests as sequential plain calls (no resident states)."""
+    buf = torch.empty(1 << 26, dtype=torch.int32, device="cuda")
+    lat = []
+    t0 = time.perf_counter()
+    for r in reqs:
+        ts = time.perf_counter()
+        if r.type == R.RNG_REQ_DRAW:
+            h = R.rng_create(r.kind, n_set)
+            R.rng_seed(h, r.seed)
+            if r.offset:
+                R.rng_skipahead(h, r.offset)
+            K = -(-r.count // n_set)
+            if r.out == R.RNG_OUT_NORMAL:
+                K += K % 2
+            fn = {0: R.rng_generate_u32, 1: R.rng_generate_f32, 2: R.rng_generate_normal}[r.out]
+            fn(h, buf.data_ptr(), K, R.RNG_STEP_MAJOR)
+            torch.cuda.synchronize()
+            R.rng_destroy(h)
+        else:
+            h = R.ising_create(r.L, r.beta, 0, r.kind, 0, r.seed, 2)
+            R.ising_sweep(h, r.sweeps)
+            R.ising_observables(h)
+            R.ising_destroy(h)
+        lat.append((time.perf_counter() - ts) * 1e3)
+    return lat, time.perf_counter() - t0
+
+
+def serve_section(R, torch, args):
+    import numpy as np
+    n_set = 4096
+    reqs = serve_requests(R, args.serve_requests)
+    numbers = sum(r.count for r in reqs if r.type == R.RNG_REQ_DRAW)
+    srv = R.rng_server_create(512, n_set, 8, 16 << 30)
+    try:
+        _serve_run(R, srv, reqs[: min(40, len(reqs))], None)  # warm-up: sets, plans, ladders
+        lat_cap, wall_cap = _serve_run(R, srv, reqs, None)  # closed loop: capacity
+        cap = len(reqs) / wall_cap
+        rates = {}
+        for f in (0.5, 0.8, 1.0):
+            lat, wall = _serve_run(R, srv, reqs, f * cap)
+            rates[str(f)] = {"rate_req_s": round(f * cap, 1), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                             "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                             "gnum_s": round(numbers / wall / 1e9, 2)}
+        stats = R.rng_server_stats(srv)
+    finally:
+        R.rng_server_destroy(srv)
+    lat_p, wall_p = _plain_run(R, torch, reqs, n_set)
+    return {"requests": len(reqs), "draw_numbers": numbers, "capacity_req_s": round(cap, 1),
+            "capacity_gnum_s": round(numbers / wall_cap / 1e9, 2), "rates": rates,
+            "plain_sequential": {"p50_ms": round(float(np.percentile(lat_p, 50)), 3),
+                                 "p99_ms": round(float(np.percentile(lat_p, 99)), 3),
+                                 "gnum_s": round(numbers / wall_p / 1e9, 2), "wall_s": round(wall_p, 2)},
+            "speedup_vs_plain": round(wall_p / wall_cap, 2), "max_concurrent": stats["max_concurrent"],
+            "workload": "80% draws (2^U(10,26) numbers, u32/f32/normal, 6 kinds, 64 seeds, offsets k 2^20), "
+                        "20% sweeps (L in 64..1024, 10..1000 sweeps); 512 resident stream sets of 4096 "
+                        "instances; 8 draw slots + 1 sweep slot; latency = submit to GPU completion"}
 
 
 # ------------------------------------------------------------ CPU oracle arm
@@ -417,6 +656,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ising", action="store_true")
     ap.add_argument("--ising-sweeps", type=int, default=2000)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-sweeps", type=int, default=10000)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=400)
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

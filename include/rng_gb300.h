@@ -279,6 +279,62 @@ int ising_batch_observables(ising_t h, uint32_t idx, int64_t *E, int64_t *M, int
                             uint64_t *n_meas);
 int ising_batch_get_spins(ising_t h, uint32_t idx, int8_t *host_LxL);
 
+/* ---------------------------------------------------------------- serving */
+
+/* A request loop with continuous batching (not in the paper): generator
+ * states stay resident on the device as "stream sets", and requests that
+ * arrive while others run are admitted as soon as a slot (one of n_slots
+ * CUDA streams for draws, plus one for sweeps) and device memory (a byte
+ * budget for outputs and lattices) are free, in arrival order; their GPU
+ * work overlaps.  A host worker thread owns all of the server's CUDA calls;
+ * submit, wait and fetch may be called from any host thread. */
+typedef struct rng_server_s *rng_server_t;
+
+enum { RNG_REQ_DRAW = 0, RNG_REQ_SWEEP = 1 };
+enum { RNG_OUT_U32 = 0, RNG_OUT_F32 = 1, RNG_OUT_NORMAL = 2 };
+
+typedef struct {
+    int32_t type;      /* RNG_REQ_DRAW or RNG_REQ_SWEEP */
+    int32_t kind;      /* generator kind, any but RNG_MT19937_SHARED */
+    uint64_t seed;     /* draw: stream-set seed; sweep: lattice seed */
+    uint64_t offset;   /* draw: draws skipped in every instance of the set */
+    uint64_t count;    /* draw: numbers returned (even for normals) */
+    int32_t out;       /* draw: RNG_OUT_U32, RNG_OUT_F32 or RNG_OUT_NORMAL */
+    uint32_t L;        /* sweep: lattice size (even, 4..16384) */
+    double beta;       /* sweep: inverse temperature */
+    uint64_t sweeps;   /* sweep: number of sweeps */
+} rng_request_t;
+
+typedef struct {
+    int32_t status;    /* RNG_OK or the request's error */
+    int32_t done;
+    uint64_t bytes;    /* result size: draw count*4, sweep L*L */
+    uint64_t t_submit_ns, t_start_ns, t_done_ns;  /* host steady clock */
+    int64_t E, M;      /* sweep: energy and magnetisation after the sweeps */
+} rng_result_t;
+
+/* A draw request returns, in step-major order, the first `count` numbers of
+ * the n = instances_per_set instances of stream set (kind, seed) -- seeded
+ * as rng_seed(seed) -- advanced by `offset` draws:
+ * result[j] = s_(j mod n)[offset + j div n].  A sweep request returns the
+ * int8 spins of ising_create(L, beta, ISING_INT8, kind, 0, seed, 2) after
+ * `sweeps` sweeps, with E and M.  Each result is a pure function of its
+ * request, whatever else is in flight.  Up to n_sets stream sets stay
+ * resident (least recently used evicted). */
+int rng_server_create(rng_server_t *out, uint32_t n_sets, uint32_t instances_per_set, uint32_t n_slots,
+                      uint64_t mem_budget_bytes);
+/* Queues a request; RNG_EBUSY if the queue is full, RNG_ENOMEM if the
+ * request alone exceeds the memory budget. */
+int rng_server_submit(rng_server_t s, const rng_request_t *req, uint64_t *ticket);
+/* Waits (timeout_s < 0: forever) until the request is done; fills *res. */
+int rng_server_wait(rng_server_t s, uint64_t ticket, double timeout_s, rng_result_t *res);
+/* Copies a finished request's result to host memory (host_dst may be NULL
+ * to discard it) and releases the request and its device memory. */
+int rng_server_fetch(rng_server_t s, uint64_t ticket, void *host_dst, uint64_t bytes);
+int rng_server_stats(rng_server_t s, uint64_t *submitted, uint64_t *completed, uint64_t *mem_in_use,
+                     uint32_t *max_concurrent);
+int rng_server_destroy(rng_server_t s);
+
 /* ----------------------------------------------------------------- errors */
 
 const char *rng_strerror(int status);

@@ -72,6 +72,12 @@ _SIGS = {
     "ising_batch_get_spins": [_p, _u32, _p],
     "ising_debug_mute_strip": [_p, ctypes.c_int32, _u64],
     "ising_plan_info": [_p, _p, _p, _p, _p],
+    "rng_server_create": [_pp, _u32, _u32, _u32, _u64],
+    "rng_server_submit": [_p, _p, ctypes.POINTER(_u64)],
+    "rng_server_wait": [_p, _u64, _f64, _p],
+    "rng_server_fetch": [_p, _u64, _p, _u64],
+    "rng_server_stats": [_p, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u32)],
+    "rng_server_destroy": [_p],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -279,3 +285,53 @@ def ising_plan_info(h: int) -> dict:
     g, b, s, t = _u32(), _u32(), _u32(), _u32()
     _call("ising_plan_info", h, ctypes.byref(g), ctypes.byref(b), ctypes.byref(s), ctypes.byref(t))
     return {"groups": g.value, "blocks": b.value, "strips": s.value, "threads": t.value}
+
+
+# -------------------------------------------------------------- serving
+RNG_REQ_DRAW, RNG_REQ_SWEEP = 0, 1
+RNG_OUT_U32, RNG_OUT_F32, RNG_OUT_NORMAL = 0, 1, 2
+
+
+class rng_request_t(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("kind", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("offset", ctypes.c_uint64), ("count", ctypes.c_uint64), ("out", ctypes.c_int32),
+                ("L", ctypes.c_uint32), ("beta", ctypes.c_double), ("sweeps", ctypes.c_uint64)]
+
+
+class rng_result_t(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("done", ctypes.c_int32), ("bytes", ctypes.c_uint64),
+                ("t_submit_ns", ctypes.c_uint64), ("t_start_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64),
+                ("E", ctypes.c_int64), ("M", ctypes.c_int64)]
+
+
+def rng_server_create(n_sets: int = 512, instances_per_set: int = 4096, n_slots: int = 8,
+                      mem_budget_bytes: int = 8 << 30) -> int:
+    h = ctypes.c_void_p()
+    _call("rng_server_create", ctypes.byref(h), n_sets, instances_per_set, n_slots, mem_budget_bytes)
+    return h.value
+
+
+def rng_server_submit(srv: int, req: rng_request_t) -> int:
+    t = _u64()
+    _call("rng_server_submit", srv, ctypes.byref(req), ctypes.byref(t))
+    return t.value
+
+
+def rng_server_wait(srv: int, ticket: int, timeout_s: float = -1.0) -> rng_result_t:
+    res = rng_result_t()
+    _call("rng_server_wait", srv, ticket, timeout_s, ctypes.byref(res))
+    return res
+
+
+def rng_server_fetch(srv: int, ticket: int, host_dst: int | None, nbytes: int) -> None:
+    _call("rng_server_fetch", srv, ticket, host_dst, nbytes)
+
+
+def rng_server_stats(srv: int) -> dict:
+    a, b, c, d = _u64(), _u64(), _u64(), _u32()
+    _call("rng_server_stats", srv, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d))
+    return {"submitted": a.value, "completed": b.value, "mem_in_use": c.value, "max_concurrent": d.value}
+
+
+def rng_server_destroy(srv: int) -> None:
+    _call("rng_server_destroy", srv)
