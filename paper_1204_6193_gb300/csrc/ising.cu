@@ -479,14 +479,15 @@ int build_plan(ising_t h, int kind, int layout, const std::vector<uint32_t> &ids
             segs[ls[i]].down = static_cast<int32_t>(ls[(i + 1) % n]);
         }
     }
-    // block shape: up to 4 streams per thread
+    // block shape: up to 4 streams per thread keep their state in registers;
+    // beyond that the kernel streams the states through L2 each half-sweep
     unsigned threads = h->cfg_threads ? h->cfg_threads : 256;
-    while (threads < 1024 && (max_streams + threads - 1) / threads > 4) threads *= 2;
-    if ((max_streams + threads - 1) / threads > 4) {
-        set_error("Ising: a block would need more than 4 streams per thread");
-        return RNG_EUNSUPPORTED;
+    while (!h->cfg_threads && threads < 1024 && (max_streams + threads - 1) / threads > 4) threads *= 2;
+    uint64_t spt = std::min<uint64_t>(4, std::max<uint64_t>(1, (max_streams + threads - 1) / threads));
+    if (spt >= 2 && threads > 512) {  // multi-slot kernels are built for at most 512 threads
+        threads = 512;
+        spt = std::min<uint64_t>(4, (max_streams + threads - 1) / threads);
     }
-    const uint64_t spt = std::max<uint64_t>(1, (max_streams + threads - 1) / threads);
     P.kind = kind;
     P.layout = layout;
     P.smax = spt <= 1 ? 1 : (spt <= 2 ? 2 : 4);

@@ -173,8 +173,86 @@ __device__ __forceinline__ long long block_sum(long long v, long long *red)
     return s;  // valid in thread 0
 }
 
+// One stream slot of a thread: which strip, which stream, where its sites are.
+struct StreamSlot {
+    uint32_t seg, row, xh0;  // strip index in the block, global row, first column of its sites
+    bool in, val;            // inside the block's stream range; owns sites
+    uint64_t s;              // stream (instance) index in its lattice
+};
+
+__device__ __forceinline__ void setup_slot(const SegLocal *S, uint32_t nseg, uint64_t prefix_end, uint64_t f,
+                                           StreamSlot &o)
+{
+    o.in = f < prefix_end;
+    uint32_t j = 0;
+    while (j + 1 < nseg && f >= S[j + 1].prefix) j++;
+    o.seg = j;
+    o.s = S[j].s0 + (o.in ? f - S[j].prefix : 0);
+    o.val = o.in && o.s < S[j].n_valid;
+    const uint64_t q0 = o.s * S[j].G;
+    o.row = static_cast<uint32_t>(q0 / S[j].half);
+    o.xh0 = static_cast<uint32_t>(q0 - static_cast<uint64_t>(o.row) * S[j].half);
+}
+
+// Draws G numbers from the slot's generator and updates its G colour-c
+// sites in shared memory (all 32 lanes of the warp call this together).
+template <int KIND, int LAYOUT>
+__device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, const StreamSlot &sl, Gen<KIND> &gen,
+                                            int c, int lane)
+{
+    const uint32_t y = sl.row;
+    const int r = static_cast<int>(y - sg.y0);
+    const uint32_t p = (c + y) & 1u;
+    if (LAYOUT == ISING_INT8) {
+        int8_t *own = reinterpret_cast<int8_t *>(plane_row<LAYOUT>(smem, sg, c, r));
+        const int8_t *o = reinterpret_cast<const int8_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r));
+        const int8_t *ou = reinterpret_cast<const int8_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r - 1));
+        const int8_t *od = reinterpret_cast<const int8_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r + 1));
+        for (uint32_t g = 0; g < sg.G; g++) {
+            const uint32_t rr = gen.next();
+            if (!sl.val) continue;
+            const uint32_t xh = sl.xh0 + g;
+            const int nn = o[col_left(xh, p, sg.half)] + o[col_right(xh, p, sg.half)] + ou[xh] + od[xh];
+            const int sp = own[xh];
+            if (accept_flip(2 * sp * nn, rr, sg.T4, sg.T8)) own[xh] = static_cast<int8_t>(-sp);
+        }
+    } else {
+        const uint32_t *own = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, c, r));
+        const uint32_t *o = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r));
+        const uint32_t *ou = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r - 1));
+        const uint32_t *od = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r + 1));
+        const uint32_t G = sg.G;
+        const uint32_t lq0 = lane * G;
+        uint32_t c_lo = 0, c_hi = 0;
+        for (uint32_t g = 0; g < G; g++) {
+            const uint32_t rr = gen.next();
+            if (!sl.val) continue;
+            const uint32_t xh = sl.xh0 + g;
+            const int nn = bit_spin(o, col_left(xh, p, sg.half)) + bit_spin(o, col_right(xh, p, sg.half)) +
+                           bit_spin(ou, xh) + bit_spin(od, xh);
+            const int sp = bit_spin(own, xh);
+            if (accept_flip(2 * sp * nn, rr, sg.T4, sg.T8)) {
+                const uint32_t lq = lq0 + g;
+                if ((lq >> 5) == (lq0 >> 5)) c_lo |= 1u << (lq & 31);
+                else c_hi |= 1u << (lq & 31);
+            }
+        }
+        // the warp's 32 G sites are G consecutive words of plane c
+        const uint32_t f0 = __shfl_sync(0xffffffffu, static_cast<uint32_t>(sl.s - sg.s0), 0);
+        const uint64_t q_first = (sg.s0 + f0) * G;
+        const uint32_t base = static_cast<uint32_t>((q_first - static_cast<uint64_t>(sg.y0) * sg.half) >> 5);
+        uint32_t *plane_c = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, 0));
+        const uint32_t own_words = sg.R * sg.W;
+        for (uint32_t m = 0; m < G; m++) {
+            const uint32_t mine = ((lq0 >> 5) == m ? c_lo : 0u) | ((lq0 >> 5) + 1 == m ? c_hi : 0u);
+            const uint32_t word = __reduce_or_sync(0xffffffffu, mine);
+            if (lane == 0 && word && base + m < own_words) plane_c[base + m] ^= word;
+        }
+    }
+}
+
 template <int KIND, int LAYOUT, int SMAX>
-__global__ void __launch_bounds__(1024) k_ising_persist(PersistArgs a)
+__global__ void __launch_bounds__(SMAX >= 2 ? 512 : 1024) k_ising_persist(PersistArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ SegLocal S[kPersistMaxSegs];
@@ -218,28 +296,23 @@ __global__ void __launch_bounds__(1024) k_ising_persist(PersistArgs a)
     __syncthreads();
     for (uint32_t j = 0; j < nseg; j++) load_segment<LAYOUT>(smem, S[j], a.lats[S[j].lat].spins);
 
-    // streams of this thread: flat indices f = tid + k * blockDim
+    // Streams of this thread: flat indices f = tid + k * blockDim over the
+    // block's strips.  When they all fit (k < SMAX), the generator states
+    // stay in registers for the whole launch; otherwise each half-sweep
+    // walks the streams in passes of SMAX * blockDim, loading and storing
+    // the states (L2-resident) around their draws.
+    const bool resident = prefix_end <= static_cast<uint64_t>(SMAX) * blockDim.x;
     Gen<KIND> gen[SMAX];
-    uint32_t kseg[SMAX];
-    uint32_t krow[SMAX], kxh0[SMAX];  // global row and first column of the stream's sites
-    bool kval[SMAX], kin[SMAX];
-    uint64_t kstream[SMAX];
+    StreamSlot slot[SMAX];
+    if (resident) {
 #pragma unroll
-    for (int k = 0; k < SMAX; k++) {
-        const uint64_t f = threadIdx.x + static_cast<uint64_t>(k) * blockDim.x;
-        kin[k] = f < prefix_end;
-        uint32_t j = 0;
-        while (j + 1 < nseg && f >= S[j + 1].prefix) j++;
-        kseg[k] = j;
-        const uint64_t s = S[j].s0 + (kin[k] ? f - S[j].prefix : 0);
-        kval[k] = kin[k] && s < S[j].n_valid;
-        kstream[k] = s;
-        const uint64_t q0 = s * S[j].G;
-        krow[k] = static_cast<uint32_t>(q0 / S[j].half);
-        kxh0[k] = static_cast<uint32_t>(q0 - static_cast<uint64_t>(krow[k]) * S[j].half);
-        DevParams rp = a.lats[S[j].lat].rng;
-        rp.pos = *a.lats[S[j].lat].pos_dev;
-        gen[k].load(rp, s < S[j].n_inst ? s : S[j].n_inst - 1);
+        for (int k = 0; k < SMAX; k++) {
+            setup_slot(S, nseg, prefix_end, threadIdx.x + static_cast<uint64_t>(k) * blockDim.x, slot[k]);
+            const SegLocal &sg = S[slot[k].seg];
+            DevParams rp = a.lats[sg.lat].rng;
+            rp.pos = *a.lats[sg.lat].pos_dev;
+            gen[k].load(rp, slot[k].s < sg.n_inst ? slot[k].s : sg.n_inst - 1);
+        }
     }
     __syncthreads();
 
@@ -248,58 +321,28 @@ __global__ void __launch_bounds__(1024) k_ising_persist(PersistArgs a)
     for (uint64_t t = 0; t < a.n_sweeps; t++) {
         for (int c = 0; c < 2; c++) {
             // ---- update every colour-c site of the block's strips
+            if (resident) {
 #pragma unroll
-            for (int k = 0; k < SMAX; k++) {
-                const bool warp_active = __any_sync(0xffffffffu, kin[k]);
-                if (!warp_active) continue;
-                const SegLocal &sg = S[kseg[k]];
-                const uint32_t y = krow[k];
-                const int r = static_cast<int>(y - sg.y0);
-                const uint32_t p = (c + y) & 1u;
-                if (LAYOUT == ISING_INT8) {
-                    int8_t *own = reinterpret_cast<int8_t *>(plane_row<LAYOUT>(smem, sg, c, r));
-                    const int8_t *o = reinterpret_cast<const int8_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r));
-                    const int8_t *ou = reinterpret_cast<const int8_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r - 1));
-                    const int8_t *od = reinterpret_cast<const int8_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r + 1));
-                    for (uint32_t g = 0; g < sg.G; g++) {
-                        const uint32_t rr = gen[k].next();
-                        if (!kval[k]) continue;
-                        const uint32_t xh = kxh0[k] + g;
-                        const int nn = o[col_left(xh, p, sg.half)] + o[col_right(xh, p, sg.half)] + ou[xh] + od[xh];
-                        const int sp = own[xh];
-                        if (accept_flip(2 * sp * nn, rr, sg.T4, sg.T8)) own[xh] = static_cast<int8_t>(-sp);
-                    }
-                } else {
-                    uint32_t *own = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, r));
-                    const uint32_t *o = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r));
-                    const uint32_t *ou = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r - 1));
-                    const uint32_t *od = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r + 1));
-                    const uint32_t G = sg.G;
-                    const uint32_t lq0 = lane * G;
-                    uint32_t c_lo = 0, c_hi = 0;
-                    for (uint32_t g = 0; g < G; g++) {
-                        const uint32_t rr = gen[k].next();
-                        if (!kval[k]) continue;
-                        const uint32_t xh = kxh0[k] + g;
-                        const int nn = bit_spin(o, col_left(xh, p, sg.half)) + bit_spin(o, col_right(xh, p, sg.half)) +
-                                       bit_spin(ou, xh) + bit_spin(od, xh);
-                        const int sp = bit_spin(own, xh);
-                        if (accept_flip(2 * sp * nn, rr, sg.T4, sg.T8)) {
-                            const uint32_t lq = lq0 + g;
-                            if ((lq >> 5) == (lq0 >> 5)) c_lo |= 1u << (lq & 31);
-                            else c_hi |= 1u << (lq & 31);
-                        }
-                    }
-                    // the warp's 32 G sites are G consecutive words of plane c
-                    const uint32_t f0 = __shfl_sync(0xffffffffu, static_cast<uint32_t>(kstream[k] - sg.s0), 0);
-                    const uint64_t q_first = (sg.s0 + f0) * G;
-                    const uint32_t base = static_cast<uint32_t>((q_first - static_cast<uint64_t>(sg.y0) * sg.half) >> 5);
-                    uint32_t *plane_c = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, 0));
-                    const uint32_t own_words = sg.R * sg.W;
-                    for (uint32_t m = 0; m < G; m++) {
-                        const uint32_t mine = ((lq0 >> 5) == m ? c_lo : 0u) | ((lq0 >> 5) + 1 == m ? c_hi : 0u);
-                        const uint32_t word = __reduce_or_sync(0xffffffffu, mine);
-                        if (lane == 0 && word && base + m < own_words) plane_c[base + m] ^= word;
+                for (int k = 0; k < SMAX; k++) {
+                    if (!__any_sync(0xffffffffu, slot[k].in)) continue;
+                    update_slot<KIND, LAYOUT>(smem, S[slot[k].seg], slot[k], gen[k], c, lane);
+                }
+            } else {
+                const uint64_t pass = static_cast<uint64_t>(SMAX) * blockDim.x;
+                for (uint64_t base = 0; base < prefix_end; base += pass) {
+#pragma unroll
+                    for (int k = 0; k < SMAX; k++) {
+                        StreamSlot sl;
+                        setup_slot(S, nseg, prefix_end, base + threadIdx.x + static_cast<uint64_t>(k) * blockDim.x, sl);
+                        if (!__any_sync(0xffffffffu, sl.in)) continue;
+                        const SegLocal &sg = S[sl.seg];
+                        DevParams rp = a.lats[sg.lat].rng;
+                        rp.pos = *a.lats[sg.lat].pos_dev + (2 * t + c) * sg.G;
+                        const uint64_t si = sl.s < sg.n_inst ? sl.s : sg.n_inst - 1;
+                        Gen<KIND> g;
+                        g.load(rp, si);
+                        update_slot<KIND, LAYOUT>(smem, sg, sl, g, c, lane);
+                        if (sl.in && sl.s < sg.n_inst) g.store(rp, sl.s);
                     }
                 }
             }
@@ -396,9 +439,11 @@ __global__ void __launch_bounds__(1024) k_ising_persist(PersistArgs a)
 done:
     __syncthreads();
     for (uint32_t j = 0; j < nseg; j++) store_segment<LAYOUT>(smem, S[j], a.lats[S[j].lat].spins);
+    if (resident) {
 #pragma unroll
-    for (int k = 0; k < SMAX; k++)
-        if (kin[k] && kstream[k] < S[kseg[k]].n_inst) gen[k].store(a.lats[S[kseg[k]].lat].rng, kstream[k]);
+        for (int k = 0; k < SMAX; k++)
+            if (slot[k].in && slot[k].s < S[slot[k].seg].n_inst) gen[k].store(a.lats[S[slot[k].seg].lat].rng, slot[k].s);
+    }
 }
 
 }  // namespace rngx

@@ -142,6 +142,37 @@ def test_launch_shape_does_not_change_results(R):
         R.ising_destroy(h)
 
 
+@pytest.mark.parametrize("layout", [0, 1])
+def test_streamed_generator_state(R, layout):
+    # 256 threads x 4 slots per block cannot hold a 1024^2 strip's streams:
+    # the kernel streams generator states through L2 every half-sweep
+    L, kind = 1024, O.PHILOX4X32_10
+    ref, acc, nm = O.ising_run(L, 0.42, kind, SEED, 12, measure_every=4)
+    h = R.ising_create(L, 0.42, layout, kind, 0, SEED, 2)
+    try:
+        R.ising_set_launch(h, 256, 1)
+        R.ising_sweep(h, 12, 4)
+        assert np.array_equal(R.ising_get_spins(h), ref)
+        assert R.ising_observables(h)["acc"] == acc.tolist()
+    finally:
+        R.ising_destroy(h)
+
+
+def test_batch_streamed_state_matches_alone(R):
+    Ls = [512, 256, 128, 64, 32, 16] * 2
+    betas = [0.3 + 0.025 * b for b in range(len(Ls))]
+    kinds = [O.XS1024W if b % 2 else O.XORWOW for b in range(len(Ls))]
+    h = R.ising_batch_create(Ls, betas, kinds, SEED + 5, 2)
+    try:
+        R.ising_set_launch(h, 128, 1)
+        R.ising_batch_sweep(h, 15)
+        for b, L in enumerate(Ls):
+            ref, _, _ = O.ising_run(L, betas[b], kinds[b], O.seed_word(SEED + 5, b), 15)
+            assert np.array_equal(R.ising_batch_get_spins(h, b), ref), b
+    finally:
+        R.ising_destroy(h)
+
+
 def test_batch_matches_lattices_alone(R):
     rng = np.random.default_rng(4)
     Ls = [16, 32, 64, 128, 256, 512, 16, 64, 32, 128, 256, 48]
