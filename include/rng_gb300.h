@@ -222,10 +222,11 @@ int ising_sweep_plain(ising_t h, uint64_t n_sweeps, uint32_t measure_every, void
 int ising_observables(ising_t h, int64_t *E, int64_t *M, int64_t acc[4], uint64_t *n_meas);
 
 /* Launch shape of the persistent kernel: threads per block (multiple of 32,
- * <= 1024; 0 = heuristic) and blocks per SM used for the row-strip plan
- * (0 = heuristic).  Results do not depend on it: the draw order is fixed
- * by the site numbering alone. */
-int ising_set_launch(ising_t h, uint32_t threads, int ctas_per_sm);
+ * <= 1024; 0 = heuristic), blocks per SM the row-strip plan aims for (0 =
+ * heuristic), and the fewest sites a block takes before lattices are split
+ * into more strips (0 = 1024).  Results do not depend on it: the draw
+ * order is fixed by the site numbering alone. */
+int ising_set_launch(ising_t h, uint32_t threads, int ctas_per_sm, uint32_t min_sites_per_block);
 
 /* Times the persistent kernel on a clone of the handle (same lattices and
  * seeds; the handle itself does not advance) for a few launch shapes,

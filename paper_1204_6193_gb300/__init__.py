@@ -63,7 +63,7 @@ _SIGS = {
     "ising_get_spins": [_p, _p],
     "ising_set_spins": [_p, _p],
     "ising_get_rng": [_p, _pp],
-    "ising_set_launch": [_p, _u32, _i32],
+    "ising_set_launch": [_p, _u32, _i32, _u32],
     "ising_autotune": [_p, _u32, _p, _p],
     "ising_info": [_p, _u32, _p, _p, _p, _p, _p],
     "ising_batch_create": [_pp, _u32, _p, _p, _p, _u64, _u32, _p],
@@ -238,8 +238,8 @@ def ising_get_rng(h: int) -> int:
     return r.value
 
 
-def ising_set_launch(h: int, threads: int = 0, ctas_per_sm: int = 0) -> None:
-    _call("ising_set_launch", h, threads, ctas_per_sm)
+def ising_set_launch(h: int, threads: int = 0, ctas_per_sm: int = 0, min_sites_per_block: int = 0) -> None:
+    _call("ising_set_launch", h, threads, ctas_per_sm, min_sites_per_block)
 
 
 def ising_autotune(h: int, probe_sweeps: int = 64) -> dict:

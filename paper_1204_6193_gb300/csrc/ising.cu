@@ -228,6 +228,7 @@ struct ising_s {
     bool planned = false;
     unsigned cfg_threads = 0;    // 0: heuristic
     int cfg_ctas_per_sm = 0;     // 0: heuristic
+    uint32_t cfg_min_sites = 0;  // 0: heuristic (1024)
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
     int32_t mute_seg = -1;                  // test hook (see ising_debug_mute_strip)
@@ -388,7 +389,8 @@ int build_plan(ising_t h, int kind, int layout, const std::vector<uint32_t> &ids
     for (uint32_t id : ids) total_sites += static_cast<uint64_t>(h->lats[id].L) * h->lats[id].L;
     // about one block per SM (or per_sm), but no fewer than 1024 sites per
     // block: smaller strips spend their time waiting on their neighbours
-    const double target = std::max(1024.0, static_cast<double>(total_sites) / target_blocks);
+    const double min_sites = h->cfg_min_sites ? static_cast<double>(h->cfg_min_sites) : 1024.0;
+    const double target = std::max(min_sites, static_cast<double>(total_sites) / target_blocks);
 
     std::vector<std::vector<SegPlan>> blocks;
     std::vector<std::pair<uint64_t, uint32_t>> whole;  // (sites, lattice) packed later
@@ -495,7 +497,7 @@ int build_plan(ising_t h, int kind, int layout, const std::vector<uint32_t> &ids
     P.nblocks = static_cast<unsigned>(blocks.size());
     P.smem = std::max<size_t>(smem_max, 16);
     P.nsegs = static_cast<uint32_t>(segs.size());
-    P.halo_row_bytes = (halo_rb + 15) / 16 * 16;
+    P.halo_row_bytes = (2 * halo_rb + 15) / 16 * 16;  // one 64-bit (tag, data) word per 32 data bits
     RNGX_CHECK(dalloc(reinterpret_cast<void **>(&P.d_segs), segs.size() * sizeof(SegDev), h->stream));
     RNGX_CHECK(dalloc(reinterpret_cast<void **>(&P.d_cta), cta.size() * sizeof(uint32_t), h->stream));
     RNGX_CHECK(dalloc(reinterpret_cast<void **>(&P.d_halo), static_cast<size_t>(P.nsegs) * 4 * P.halo_row_bytes,
@@ -564,7 +566,8 @@ int enqueue_persistent(ising_t h, uint64_t n_sweeps, uint32_t measure_every, cud
         for (auto &t : h->lats)
             if (n_meas) RNGX_CHECK_CUDA(cudaMemsetAsync(t.meas, 0, 2 * n_meas * sizeof(int64_t), s));
         for (auto &P : h->plans) {
-            RNGX_CHECK_CUDA(cudaMemsetAsync(P.d_flags, 0, P.nsegs * sizeof(uint32_t), s));
+            // halo words carry half-sweep tags that restart at every launch
+            RNGX_CHECK_CUDA(cudaMemsetAsync(P.d_halo, 0, static_cast<size_t>(P.nsegs) * 4 * P.halo_row_bytes, s));
             PersistArgs a;
             a.lats = h->d_lats;
             a.segs = P.d_segs;
@@ -834,7 +837,7 @@ int ising_get_rng(ising_t h, rng_t *rng)
     return RNG_OK;
 }
 
-int ising_set_launch(ising_t h, uint32_t threads, int ctas_per_sm)
+int ising_set_launch(ising_t h, uint32_t threads, int ctas_per_sm, uint32_t min_sites_per_block)
 {
     RNGX_CHECK(valid(h));
     if (threads && (threads % 32 || threads > 1024)) {
@@ -849,6 +852,7 @@ int ising_set_launch(ising_t h, uint32_t threads, int ctas_per_sm)
     free_plans(h);
     h->cfg_threads = threads;
     h->cfg_ctas_per_sm = ctas_per_sm;
+    h->cfg_min_sites = min_sites_per_block;
     return RNG_OK;
 }
 
@@ -898,51 +902,59 @@ extern "C" int ising_autotune(ising_t h, uint32_t probe_sweeps, uint32_t *thread
     if (probe_sweeps == 0) probe_sweeps = 64;
     static const uint32_t kThreads[] = {256, 512, 1024};
     static const int kPerSm[] = {1, 2, 4};
+    static const uint32_t kMinSites[] = {1024, 8192, 65536};
     float best = -1.0f;
-    uint32_t best_t = 0;
+    uint32_t best_t = 0, best_m = 0;
     int best_c = 0;
     cudaEvent_t e0, e1;
     RNGX_CHECK_CUDA(cudaEventCreate(&e0));
     RNGX_CHECK_CUDA(cudaEventCreate(&e1));
-    for (uint32_t th : kThreads) {
-        for (int pc : kPerSm) {
-            // probe a clone: the launch shape never changes results, and the
-            // handle itself must not advance
-            ising_t c = nullptr;
-            int st;
-            if (h->batch) {
-                std::vector<uint32_t> L;
-                std::vector<double> beta;
-                std::vector<int> kind;
-                for (auto &t : h->lats) {
-                    L.push_back(t.L);
-                    beta.push_back(t.beta);
-                    kind.push_back(t.kind);
+    uint64_t total_sites = 0;
+    for (auto &t : h->lats) total_sites += static_cast<uint64_t>(t.L) * t.L;
+    for (uint32_t ms : kMinSites) {
+        if (ms > 1024 && ms / 8 > total_sites) continue;  // same plan as a smaller minimum
+        for (uint32_t th : kThreads) {
+            for (int pc : kPerSm) {
+                // probe a clone: the launch shape never changes results, and
+                // the handle itself must not advance
+                ising_t c = nullptr;
+                int st;
+                if (h->batch) {
+                    std::vector<uint32_t> L;
+                    std::vector<double> beta;
+                    std::vector<int> kind;
+                    for (auto &t : h->lats) {
+                        L.push_back(t.L);
+                        beta.push_back(t.beta);
+                        kind.push_back(t.kind);
+                    }
+                    st = ising_batch_create(&c, static_cast<uint32_t>(L.size()), L.data(), beta.data(), kind.data(),
+                                            h->master_seed, h->lats[0].G, h->stream);
+                } else {
+                    const IsingLat &t = h->lats[0];
+                    st = ising_create(&c, t.L, t.beta, t.layout, t.kind, t.flags, t.seed, t.G, h->stream);
                 }
-                st = ising_batch_create(&c, static_cast<uint32_t>(L.size()), L.data(), beta.data(), kind.data(),
-                                        h->master_seed, h->lats[0].G, h->stream);
-            } else {
-                const IsingLat &t = h->lats[0];
-                st = ising_create(&c, t.L, t.beta, t.layout, t.kind, t.flags, t.seed, t.G, h->stream);
-            }
-            if (st != RNG_OK) continue;
-            c->cfg_threads = th;
-            c->cfg_ctas_per_sm = pc;
-            st = ising_sweep(c, std::max<uint32_t>(1, probe_sweeps / 4), 0, h->stream);
-            float ms = 0.0f;
-            if (st == RNG_OK) {
-                cudaEventRecord(e0, h->stream);
-                st = ising_sweep(c, probe_sweeps, 0, h->stream);
-                cudaEventRecord(e1, h->stream);
-                if (st == RNG_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-                if (st == RNG_OK) st = check_err(c);
-            }
-            cudaGetLastError();
-            ising_destroy(c);
-            if (st == RNG_OK && ms > 0.0f && (best < 0.0f || ms < best)) {
-                best = ms;
-                best_t = th;
-                best_c = pc;
+                if (st != RNG_OK) continue;
+                c->cfg_threads = th;
+                c->cfg_ctas_per_sm = pc;
+                c->cfg_min_sites = ms;
+                st = ising_sweep(c, std::max<uint32_t>(1, probe_sweeps / 4), 0, h->stream);
+                float msec = 0.0f;
+                if (st == RNG_OK) {
+                    cudaEventRecord(e0, h->stream);
+                    st = ising_sweep(c, probe_sweeps, 0, h->stream);
+                    cudaEventRecord(e1, h->stream);
+                    if (st == RNG_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&msec, e0, e1);
+                    if (st == RNG_OK) st = check_err(c);
+                }
+                cudaGetLastError();
+                ising_destroy(c);
+                if (st == RNG_OK && msec > 0.0f && (best < 0.0f || msec < best)) {
+                    best = msec;
+                    best_t = th;
+                    best_c = pc;
+                    best_m = ms;
+                }
             }
         }
     }
@@ -952,12 +964,11 @@ extern "C" int ising_autotune(ising_t h, uint32_t probe_sweeps, uint32_t *thread
         set_error("ising_autotune: no launch shape ran");
         return RNG_EUNSUPPORTED;
     }
-    RNGX_CHECK(ising_set_launch(h, best_t, best_c));
+    RNGX_CHECK(ising_set_launch(h, best_t, best_c, best_m));
     if (threads_out) *threads_out = best_t;
     if (ctas_per_sm_out) *ctas_per_sm_out = best_c;
     return RNG_OK;
 }
-
 extern "C" int ising_info(ising_t h, uint32_t idx, uint32_t *n_lattices, uint32_t *L, int *layout, int *rng_kind,
                           uint64_t *sweeps_position)
 {

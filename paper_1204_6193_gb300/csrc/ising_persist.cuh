@@ -40,6 +40,7 @@ struct SegLocal {              // per-segment constants held in shared memory
     int32_t up, down, gid;
     uint64_t s0, prefix, T4, T8;
     uint64_t n_valid, n_inst;  // streams with sites; generator instances
+    DevParams rng;             // the lattice's generator (position at launch start)
 };
 
 template <int LAYOUT>
@@ -189,9 +190,10 @@ __device__ __forceinline__ void setup_slot(const SegLocal *S, uint32_t nseg, uin
     o.seg = j;
     o.s = S[j].s0 + (o.in ? f - S[j].prefix : 0);
     o.val = o.in && o.s < S[j].n_valid;
-    const uint64_t q0 = o.s * S[j].G;
-    o.row = static_cast<uint32_t>(q0 / S[j].half);
-    o.xh0 = static_cast<uint32_t>(q0 - static_cast<uint64_t>(o.row) * S[j].half);
+    // s G < L^2 / 2 <= 2^31: 32-bit arithmetic suffices
+    const uint32_t q0 = static_cast<uint32_t>(o.s) * S[j].G;
+    o.row = q0 / S[j].half;
+    o.xh0 = q0 - o.row * S[j].half;
 }
 
 // Draws G numbers from the slot's generator and updates its G colour-c
@@ -251,6 +253,68 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
     }
 }
 
+__device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p)
+{
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool slot_on_boundary(const SegLocal *S, const StreamSlot &sl)
+{
+    const SegLocal &sg = S[sl.seg];
+    return sl.in && (sl.row == sg.y0 || sl.row + 1 == sg.y0 + sg.R);
+}
+
+// Updates the warps that hold a first or last row of their strip
+// (boundary = true) or the other warps (boundary = false).  A warp is
+// classified as a whole, so warp-wide steps see all 32 lanes.
+template <int KIND, int LAYOUT, int SMAX>
+__device__ __forceinline__ void update_pass(uint8_t *smem, const SegLocal *S, uint32_t nseg, uint64_t prefix_end,
+                                            const PersistArgs &a, bool resident, Gen<KIND> (&gen)[SMAX],
+                                            const StreamSlot (&slot)[SMAX], uint64_t t, int c, int lane, bool boundary)
+{
+    if (resident) {
+#pragma unroll
+        for (int k = 0; k < SMAX; k++) {
+            if (!__any_sync(0xffffffffu, slot[k].in)) continue;
+            if (__any_sync(0xffffffffu, slot_on_boundary(S, slot[k])) != boundary) continue;
+            update_slot<KIND, LAYOUT>(smem, S[slot[k].seg], slot[k], gen[k], c, lane);
+        }
+        return;
+    }
+    // streamed states: strip by strip, one stream per thread per step (the
+    // strips' stream counts are multiples of 32, so warps never straddle two)
+    for (uint32_t j = 0; j < nseg; j++) {
+        const SegLocal &sg = S[j];
+        const uint64_t count = (j + 1 < nseg ? S[j + 1].prefix : prefix_end) - sg.prefix;
+        for (uint64_t base = 0; base < count; base += blockDim.x) {
+            const uint64_t f = base + threadIdx.x;
+            StreamSlot sl;
+            sl.seg = j;
+            sl.in = f < count;
+            sl.s = sg.s0 + (sl.in ? f : 0);
+            sl.val = sl.in && sl.s < sg.n_valid;
+            const uint32_t q0 = static_cast<uint32_t>(sl.s) * sg.G;
+            sl.row = q0 / sg.half;
+            sl.xh0 = q0 - sl.row * sg.half;
+            if (!__any_sync(0xffffffffu, sl.in)) continue;
+            if (__any_sync(0xffffffffu, slot_on_boundary(S, sl)) != boundary) continue;
+            DevParams rp = sg.rng;
+            rp.pos += (2 * t + c) * sg.G;
+            Gen<KIND> g;
+            g.load(rp, sl.s < sg.n_inst ? sl.s : sg.n_inst - 1);
+            update_slot<KIND, LAYOUT>(smem, sg, sl, g, c, lane);
+            if (sl.in && sl.s < sg.n_inst) g.store(rp, sl.s);
+        }
+    }
+}
+
 template <int KIND, int LAYOUT, int SMAX>
 __global__ void __launch_bounds__(SMAX >= 2 ? 512 : 1024) k_ising_persist(PersistArgs a)
 {
@@ -280,6 +344,8 @@ __global__ void __launch_bounds__(SMAX >= 2 ? 512 : 1024) k_ising_persist(Persis
         s.T8 = l.T8;
         s.n_valid = l.nstreams;
         s.n_inst = l.rng.n;
+        s.rng = l.rng;
+        s.rng.pos = *l.pos_dev;
         S[threadIdx.x] = s;
     }
     if (threadIdx.x == 0) s_abort = 0;
@@ -309,9 +375,7 @@ __global__ void __launch_bounds__(SMAX >= 2 ? 512 : 1024) k_ising_persist(Persis
         for (int k = 0; k < SMAX; k++) {
             setup_slot(S, nseg, prefix_end, threadIdx.x + static_cast<uint64_t>(k) * blockDim.x, slot[k]);
             const SegLocal &sg = S[slot[k].seg];
-            DevParams rp = a.lats[sg.lat].rng;
-            rp.pos = *a.lats[sg.lat].pos_dev;
-            gen[k].load(rp, slot[k].s < sg.n_inst ? slot[k].s : sg.n_inst - 1);
+            gen[k].load(sg.rng, slot[k].s < sg.n_inst ? slot[k].s : sg.n_inst - 1);
         }
     }
     __syncthreads();
@@ -320,43 +384,18 @@ __global__ void __launch_bounds__(SMAX >= 2 ? 512 : 1024) k_ising_persist(Persis
     const int lane = threadIdx.x & 31;
     for (uint64_t t = 0; t < a.n_sweeps; t++) {
         for (int c = 0; c < 2; c++) {
-            // ---- update every colour-c site of the block's strips
-            if (resident) {
-#pragma unroll
-                for (int k = 0; k < SMAX; k++) {
-                    if (!__any_sync(0xffffffffu, slot[k].in)) continue;
-                    update_slot<KIND, LAYOUT>(smem, S[slot[k].seg], slot[k], gen[k], c, lane);
-                }
-            } else {
-                const uint64_t pass = static_cast<uint64_t>(SMAX) * blockDim.x;
-                for (uint64_t base = 0; base < prefix_end; base += pass) {
-#pragma unroll
-                    for (int k = 0; k < SMAX; k++) {
-                        StreamSlot sl;
-                        setup_slot(S, nseg, prefix_end, base + threadIdx.x + static_cast<uint64_t>(k) * blockDim.x, sl);
-                        if (!__any_sync(0xffffffffu, sl.in)) continue;
-                        const SegLocal &sg = S[sl.seg];
-                        DevParams rp = a.lats[sg.lat].rng;
-                        rp.pos = *a.lats[sg.lat].pos_dev + (2 * t + c) * sg.G;
-                        const uint64_t si = sl.s < sg.n_inst ? sl.s : sg.n_inst - 1;
-                        Gen<KIND> g;
-                        g.load(rp, si);
-                        update_slot<KIND, LAYOUT>(smem, sg, sl, g, c, lane);
-                        if (sl.in && sl.s < sg.n_inst) g.store(rp, sl.s);
-                    }
-                }
-            }
-            __syncthreads();
-
-            // ---- publish boundary rows of colour c, refresh halos
+            // ---- warps that hold a strip's first or last row go first ...
             const uint32_t h = static_cast<uint32_t>(2 * t + c);
+            update_pass<KIND, LAYOUT, SMAX>(smem, S, nseg, prefix_end, a, resident, gen, slot, t, c, lane, true);
+            __syncthreads();
+            // ---- ... their rows are published (a whole lattice copies them
+            // into its own halo rows) ...
             bool any_split = false;
             for (uint32_t j = 0; j < nseg; j++) {
                 const SegLocal &sg = S[j];
                 const uint32_t rb = row_bytes<LAYOUT>(sg);
                 if (sg.up < 0) {
-                    // whole lattice: halo rows are its own last and first rows
-                    // (byte copies: an int8 row of L/2 bytes need not be word aligned)
+                    // byte copies: an int8 row of L/2 bytes need not be word aligned
                     uint8_t *top = plane_row<LAYOUT>(smem, sg, c, -1), *bot = plane_row<LAYOUT>(smem, sg, c, sg.R);
                     const uint8_t *last = plane_row<LAYOUT>(smem, sg, c, sg.R - 1), *first = plane_row<LAYOUT>(smem, sg, c, 0);
                     for (uint32_t i = threadIdx.x; i < rb; i += blockDim.x) {
@@ -365,56 +404,59 @@ __global__ void __launch_bounds__(SMAX >= 2 ? 512 : 1024) k_ising_persist(Persis
                     }
                 } else {
                     any_split = true;
-                    uint32_t *dst = reinterpret_cast<uint32_t *>(a.halo + (static_cast<size_t>(sg.gid) * 4 + (h & 1) * 2) *
+                    if (sg.gid == a.mute_seg) continue;  // test hook: a strip that never publishes
+                    // each 64-bit word carries (half-sweep number + 1, 32 bits of
+                    // the row): one relaxed atomic store, no fence, no flag
+                    uint64_t *dst = reinterpret_cast<uint64_t *>(a.halo + (static_cast<size_t>(sg.gid) * 4 + (h & 1) * 2) *
                                                                               a.halo_row_bytes);
+                    const uint32_t *row0 = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, c, 0));
+                    const uint32_t *rowl = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, c, sg.R - 1));
+                    const uint64_t tag = static_cast<uint64_t>(h + 1) << 32;
                     for (uint32_t i = threadIdx.x; i < rb / 4; i += blockDim.x) {
-                        __stcg(dst + i, reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, 0))[i]);
-                        __stcg(dst + a.halo_row_bytes / 4 + i,
-                               reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, sg.R - 1))[i]);
+                        st_relaxed_u64(dst + i, tag | row0[i]);
+                        st_relaxed_u64(dst + a.halo_row_bytes / 8 + i, tag | rowl[i]);
                     }
                 }
             }
+            // ---- ... the interior rows are updated while those words travel ...
+            update_pass<KIND, LAYOUT, SMAX>(smem, S, nseg, prefix_end, a, resident, gen, slot, t, c, lane, false);
+            // ---- ... and the neighbours' rows are polled into the halo rows
             if (any_split) {
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    __threadfence();
-                    for (uint32_t j = 0; j < nseg; j++)
-                        if (S[j].up >= 0 && S[j].gid != a.mute_seg) st_release(a.flags + S[j].gid, h + 1);
-                    // bounded by two clocks: the global ns timer and the SM
-                    // cycle counter (at most 4 cycles per ns of budget)
-                    const uint64_t t0 = global_ns();
-                    const long long c0 = clock64();
-                    for (uint32_t j = 0; j < nseg && !s_abort; j++) {
-                        if (S[j].up < 0) continue;
-                        while (ld_acquire(a.flags + S[j].up) < h + 1 || ld_acquire(a.flags + S[j].down) < h + 1) {
+                const uint64_t t0 = global_ns();
+                const long long c0 = clock64();
+                bool failed = false;
+                for (uint32_t j = 0; j < nseg && !failed; j++) {
+                    const SegLocal &sg = S[j];
+                    if (sg.up < 0) continue;
+                    const uint32_t words = row_bytes<LAYOUT>(sg) / 4;
+                    const uint64_t *up_bottom = reinterpret_cast<const uint64_t *>(
+                        a.halo + (static_cast<size_t>(sg.up) * 4 + (h & 1) * 2 + 1) * a.halo_row_bytes);
+                    const uint64_t *dn_top = reinterpret_cast<const uint64_t *>(
+                        a.halo + (static_cast<size_t>(sg.down) * 4 + (h & 1) * 2) * a.halo_row_bytes);
+                    uint32_t *top = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, -1));
+                    uint32_t *bot = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, sg.R));
+                    for (uint32_t i = threadIdx.x; i < 2 * words && !failed; i += blockDim.x) {
+                        const uint64_t *src = i < words ? up_bottom + i : dn_top + (i - words);
+                        uint64_t v;
+                        // bounded by two clocks: the global ns timer and the SM
+                        // cycle counter (at most 4 cycles per ns of budget)
+                        while (((v = ld_relaxed_u64(src)) >> 32) != h + 1) {
+                            __nanosleep(20);  // light backoff: many blocks poll the L2 at once
                             if (global_ns() - t0 > a.wait_budget_ns ||
                                 static_cast<uint64_t>(clock64() - c0) > 4 * a.wait_budget_ns ||
                                 ld_acquire(reinterpret_cast<uint32_t *>(a.err)) != 0) {
                                 atomicCAS(a.err, 0, RNG_ETIMEOUT);
-                                s_abort = 1;
+                                failed = true;
                                 break;
                             }
-                            __nanosleep(64);
                         }
+                        if (!failed) (i < words ? top[i] : bot[i - words]) = static_cast<uint32_t>(v);
                     }
                 }
-                __syncthreads();
-                if (s_abort) goto done;
-                for (uint32_t j = 0; j < nseg; j++) {
-                    const SegLocal &sg = S[j];
-                    if (sg.up < 0) continue;
-                    const uint32_t rb = row_bytes<LAYOUT>(sg);
-                    const uint32_t *up_bottom = reinterpret_cast<const uint32_t *>(
-                        a.halo + (static_cast<size_t>(sg.up) * 4 + (h & 1) * 2 + 1) * a.halo_row_bytes);
-                    const uint32_t *dn_top = reinterpret_cast<const uint32_t *>(
-                        a.halo + (static_cast<size_t>(sg.down) * 4 + (h & 1) * 2) * a.halo_row_bytes);
-                    for (uint32_t i = threadIdx.x; i < rb / 4; i += blockDim.x) {
-                        reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, -1))[i] = __ldcg(up_bottom + i);
-                        reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, sg.R))[i] = __ldcg(dn_top + i);
-                    }
-                }
+                if (failed) s_abort = 1;
             }
             __syncthreads();
+            if (s_abort) goto done;
         }
         // ---- measurement after every measure_every-th sweep of this launch
         if (a.measure_every && (a.sweep0 + t + 1) % a.measure_every == 0) {

@@ -98,6 +98,18 @@ def test_chunk_boundary_and_measurement_phase(R):
     assert obs["acc"] == acc.tolist() and obs["n_meas"] == nm
 
 
+def test_many_short_launches(R):
+    # one-sweep launches back to back: each launch restarts its halo tags
+    ref, _, _ = O.ising_run(1024, 0.44, O.XORWOW, SEED, 6)
+    h = R.ising_create(1024, 0.44, 1, O.XORWOW, 0, SEED, 2)
+    try:
+        for n in (1, 1, 1, 3):
+            R.ising_sweep(h, n)
+        assert np.array_equal(R.ising_get_spins(h), ref)
+    finally:
+        R.ising_destroy(h)
+
+
 def test_calls_compose_and_checkpoint_restores(R):
     L, beta, kind = 128, 0.42, O.XORWOW
     ref, _, _ = O.ising_run(L, beta, kind, SEED, 100)
@@ -124,10 +136,10 @@ def test_calls_compose_and_checkpoint_restores(R):
 def test_launch_shape_does_not_change_results(R):
     L, kind = 512, O.XS1024W
     ref, _, _ = O.ising_run(L, 0.4, kind, SEED, 20)
-    for threads, per_sm in [(256, 1), (1024, 1), (512, 4), (0, 0)]:
+    for threads, per_sm, mins in [(256, 1, 0), (1024, 1, 0), (512, 4, 0), (0, 0, 0), (256, 1, 1 << 20)]:
         h = R.ising_create(L, 0.4, 0, kind, 0, SEED, 2)
         try:
-            R.ising_set_launch(h, threads, per_sm)
+            R.ising_set_launch(h, threads, per_sm, mins)
             R.ising_sweep(h, 20)
             assert np.array_equal(R.ising_get_spins(h), ref), (threads, per_sm)
         finally:
