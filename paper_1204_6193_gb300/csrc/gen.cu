@@ -30,6 +30,45 @@ __global__ void __launch_bounds__(kBlock) k_generate(DevParams p, void *out_, ui
     if (active) g.load(p, i);
     else g.load(p, n - 1);  // dummy state, output discarded
 
+    if constexpr (KIND == RNG_PHILOX4X32_10) {
+        // block-aligned calls: one block evaluation yields draws k..k+3
+        if (LAYOUT != RNG_INSTANCE_MAJOR && (p.pos & 3) == 0 && (K & 3) == 0) {
+            const uint64_t blk0 = p.pos >> 2;
+            uint32_t xacc = 0;
+            float facc = 0.0f;
+            for (uint64_t k = 0; k < K; k += 4) {
+                const uint64_t blk = blk0 + (k >> 2);
+                uint32_t o[4];
+                philox_block<10>(static_cast<uint32_t>(blk), static_cast<uint32_t>(blk >> 32), 0u, 0u, g.k0, g.k1,
+                                 o[0], o[1], o[2], o[3]);
+                if (OUT == OUT_NORMAL) {
+                    float z[4];
+                    box_muller(o[0], o[1], z[0], z[1]);
+                    box_muller(o[2], o[3], z[2], z[3]);
+                    if (LAYOUT == RNG_XOR_REDUCE) {
+#pragma unroll
+                        for (int j = 0; j < 4; j++) facc += z[j];
+                    } else if (active) {
+#pragma unroll
+                        for (int j = 0; j < 4; j++) st_stream(static_cast<float *>(out_) + (k + j) * n + i, z[j]);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        const uint32_t bits = OUT == OUT_U32 ? o[j] : __float_as_uint(u32_to_unit(o[j]));
+                        if (LAYOUT == RNG_XOR_REDUCE) xacc ^= bits;
+                        else if (active) __stcs(static_cast<uint32_t *>(out_) + (k + j) * n + i, bits);
+                    }
+                }
+            }
+            if (LAYOUT == RNG_XOR_REDUCE && active) {
+                if (OUT == OUT_NORMAL) static_cast<float *>(out_)[i] = facc;
+                else static_cast<uint32_t *>(out_)[i] = xacc;
+            }
+            return;  // Philox keeps no state beyond the handle's position
+        }
+    }
+
     if (LAYOUT == RNG_STEP_MAJOR) {
         if (OUT == OUT_NORMAL) {
             float *out = static_cast<float *>(out_);
@@ -103,12 +142,17 @@ __global__ void __launch_bounds__(kBlock) k_generate(DevParams p, void *out_, ui
 }
 
 // ------------------------------------------------------------- MT19937
-// One generator per thread block: the 624-word state lives in shared
-// memory and is refilled cooperatively in three barrier-separated phases
-// whose ranges [0,227), [227,454), [454,624) only read words that are
-// either not yet rewritten or rewritten by an earlier phase (Sec. 5; the
-// block-wise vectorisation of the paper's GPU Mersenne twister variants).
-constexpr int kMtBlock = 256;
+// One generator per warp: its 624-word state is staged in shared memory
+// (Sec. 5: the state is shared by the threads that refill it) and the warp
+// refills it in 20 chunks of 32 consecutive words.  In the sequential
+// recurrence word i reads word i+1 (not yet rewritten) and word i+397 mod
+// 624, which for i < 227 is not yet rewritten and for i >= 227 was
+// rewritten 227 positions earlier, i.e. in an earlier chunk; so a chunk
+// reads its inputs into registers, syncs the warp and writes -- no block
+// barriers.  The refilled words are tempered into a per-warp buffer from
+// which the outputs (pairs, for normals) are written.
+constexpr int kMtWarps = 8;
+constexpr int kMtBlock = 32 * kMtWarps;
 
 __device__ __forceinline__ uint32_t mt_mix(uint32_t cur, uint32_t nxt, uint32_t far)
 {
@@ -116,47 +160,32 @@ __device__ __forceinline__ uint32_t mt_mix(uint32_t cur, uint32_t nxt, uint32_t 
     return far ^ (y >> 1) ^ ((y & 1u) ? 0x9908B0DFu : 0u);
 }
 
-__device__ void mt_twist(uint32_t *mt)
+__device__ __forceinline__ void mt_twist_warp(uint32_t *mt, int lane)
 {
-    const int t = threadIdx.x;
-    uint32_t v = 0;
-    // phase 1: i in [0, 227), far word i + 397 not yet rewritten
-    if (t < MT_N - MT_M) v = mt_mix(mt[t], mt[t + 1], mt[t + MT_M]);
-    __syncthreads();
-    if (t < MT_N - MT_M) mt[t] = v;
-    __syncthreads();
-    // phase 2: i in [227, 454), far word i - 227 rewritten in phase 1
-    if (t < MT_N - MT_M) {
-        const int i = t + (MT_N - MT_M);
-        v = mt_mix(mt[i], mt[i + 1], mt[i - (MT_N - MT_M)]);
+    for (int b = 0; b < MT_N; b += 32) {
+        const int i = b + lane;
+        uint32_t v = 0;
+        if (i < MT_N) v = mt_mix(mt[i], mt[i + 1 == MT_N ? 0 : i + 1], mt[i + MT_M < MT_N ? i + MT_M : i + MT_M - MT_N]);
+        __syncwarp();
+        if (i < MT_N) mt[i] = v;
+        __syncwarp();
     }
-    __syncthreads();
-    if (t < MT_N - MT_M) mt[t + (MT_N - MT_M)] = v;
-    __syncthreads();
-    // phase 3: i in [454, 624), far word i - 227 rewritten in phase 2; the
-    // last word pairs with the new word 0
-    const int base = 2 * (MT_N - MT_M);
-    if (t < MT_N - base) {
-        const int i = t + base;
-        v = mt_mix(mt[i], mt[(i + 1) % MT_N], mt[i - (MT_N - MT_M)]);
-    }
-    __syncthreads();
-    if (t < MT_N - base) mt[t + base] = v;
-    __syncthreads();
 }
 
 template <int OUT, int LAYOUT>
 __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out_, uint64_t K)
 {
-    __shared__ uint32_t mt[MT_N];
-    __shared__ uint32_t buf[MT_N + 1];
-    __shared__ uint32_t red[kMtBlock];
-    const uint64_t gidx = blockIdx.x;
+    __shared__ uint32_t mt_s[kMtWarps][MT_N];
+    __shared__ uint32_t buf_s[kMtWarps][MT_N + 2];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t gidx = static_cast<uint64_t>(blockIdx.x) * kMtWarps + w;
     const uint64_t n = p.n;
+    if (gidx >= n) return;  // whole warps only: no block-wide barriers below
+    uint32_t *mt = mt_s[w], *buf = buf_s[w];
     uint32_t *st = static_cast<uint32_t *>(p.s[0]) + gidx * MT_N;
-    for (int t = threadIdx.x; t < MT_N; t += kMtBlock) mt[t] = st[t];
+    for (int t = lane; t < MT_N; t += 32) mt[t] = st[t];
     int mti = p.pos == 0 ? MT_N : static_cast<int>((p.pos - 1) % MT_N) + 1;
-    __syncthreads();
+    __syncwarp();
 
     auto out_index = [&](uint64_t d) -> uint64_t {
         return LAYOUT == RNG_INSTANCE_MAJOR ? gidx * K + d : d * n + gidx;
@@ -168,13 +197,13 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
     uint64_t k = 0;
     while (k < K) {
         if (mti == MT_N) {
-            mt_twist(mt);
+            mt_twist_warp(mt, lane);
             mti = 0;
             twisted = true;
         }
         const int cnt = static_cast<int>(K - k < static_cast<uint64_t>(MT_N - mti) ? K - k : MT_N - mti);
         if (OUT != OUT_NORMAL) {
-            for (int t = threadIdx.x; t < cnt; t += kMtBlock) {
+            for (int t = lane; t < cnt; t += 32) {
                 const uint32_t r = mt_temper(mt[mti + t]);
                 const uint32_t bits = OUT == OUT_U32 ? r : __float_as_uint(u32_to_unit(r));
                 if (LAYOUT == RNG_XOR_REDUCE) xacc ^= bits;
@@ -183,13 +212,13 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
         } else {
             // buf[0] = pending word when k is odd, then the chunk
             const int off = static_cast<int>(k & 1);
-            for (int t = threadIdx.x; t < cnt; t += kMtBlock) buf[off + t] = mt_temper(mt[mti + t]);
-            if (threadIdx.x == 0 && off) buf[0] = pending;
-            __syncthreads();
-            const uint64_t d0 = k - off;           // draw index of buf[0], even
+            for (int t = lane; t < cnt; t += 32) buf[off + t] = mt_temper(mt[mti + t]);
+            if (lane == 0 && off) buf[0] = pending;
+            __syncwarp();
+            const uint64_t d0 = k - off;  // draw index of buf[0], even
             const int avail = cnt + off;
             const int pairs = avail / 2;
-            for (int t = threadIdx.x; t < pairs; t += kMtBlock) {
+            for (int t = lane; t < pairs; t += 32) {
                 float z0, z1;
                 box_muller(buf[2 * t], buf[2 * t + 1], z0, z1);
                 if (LAYOUT == RNG_XOR_REDUCE) {
@@ -201,29 +230,165 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
                     __stcs(out + out_index(d0 + 2 * t + 1), z1);
                 }
             }
-            if (avail & 1) pending = buf[avail - 1];  // uniform across threads
+            if (avail & 1) pending = buf[avail - 1];  // same value in every lane
+            __syncwarp();
         }
         k += cnt;
         mti += cnt;
-        __syncthreads();
     }
     if (LAYOUT == RNG_XOR_REDUCE) {
-        if (OUT == OUT_NORMAL) red[threadIdx.x] = __float_as_uint(facc);
-        else red[threadIdx.x] = xacc;
-        __syncthreads();
-        for (int s = kMtBlock / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) {
-                if (OUT == OUT_NORMAL)
-                    red[threadIdx.x] = __float_as_uint(__uint_as_float(red[threadIdx.x]) +
-                                                       __uint_as_float(red[threadIdx.x + s]));
-                else red[threadIdx.x] ^= red[threadIdx.x + s];
-            }
-            __syncthreads();
+        if (OUT == OUT_NORMAL) {
+            for (int o = 16; o > 0; o >>= 1) facc += __shfl_down_sync(0xffffffffu, facc, o);
+            if (lane == 0) static_cast<float *>(out_)[gidx] = facc;
+        } else {
+            for (int o = 16; o > 0; o >>= 1) xacc ^= __shfl_down_sync(0xffffffffu, xacc, o);
+            if (lane == 0) static_cast<uint32_t *>(out_)[gidx] = xacc;
         }
-        if (threadIdx.x == 0) static_cast<uint32_t *>(out_)[gidx] = red[0];
     }
-    if (twisted)
-        for (int t = threadIdx.x; t < MT_N; t += kMtBlock) st[t] = mt[t];
+    if (twisted) {
+        __syncwarp();
+        for (int t = lane; t < MT_N; t += 32) st[t] = mt[t];
+    }
+}
+
+// ------------------------------------------- the 1024-bit generator, by thread
+// For step-major and consume-in-register output one thread holds a whole
+// 1024-bit state (its 32 lanes' words) in registers and applies the three
+// shifts with funnel shifts: identical draws to the warp-shuffle form, at
+// about seven instructions per output instead of six shuffles and a dozen
+// selects per lane.  Step-major output is then 32 consecutive words per
+// thread and step (eight 16-byte stores).
+template <int OUT, int LAYOUT>
+__global__ void __launch_bounds__(64) k_generate_xs_reg(DevParams p, void *out_, uint64_t K)
+{
+    const uint64_t j = static_cast<uint64_t>(blockIdx.x) * 64 + threadIdx.x;
+    const uint64_t n = p.n;
+    if (j >= n / 32) return;
+    uint32_t *state = static_cast<uint32_t *>(p.s[0]) + 32 * j;
+    uint32_t x[32];
+#pragma unroll
+    for (int m = 0; m < 8; m++) {
+        const uint4 v = reinterpret_cast<const uint4 *>(state)[m];
+        x[4 * m] = v.x;
+        x[4 * m + 1] = v.y;
+        x[4 * m + 2] = v.z;
+        x[4 * m + 3] = v.w;
+    }
+    uint64_t step = p.pos;
+    auto shift_step = [&]() {
+#pragma unroll
+        for (int i = 0; i <= 21; i++)  // X ^= X << 329: words i+10, i+11 (zero past the end)
+            x[i] ^= __funnelshift_l(i + 11 < 32 ? x[i + 11 < 32 ? i + 11 : 31] : 0u, x[i + 10], 9);
+#pragma unroll
+        for (int i = 31; i >= 10; i--)  // X ^= X >> 347: words i-10, i-11 (zero before the start)
+            x[i] ^= __funnelshift_r(x[i - 10], i - 11 >= 0 ? x[i - 11 >= 0 ? i - 11 : 0] : 0u, 27);
+#pragma unroll
+        for (int i = 0; i <= 21; i++)  // X ^= X << 344
+            x[i] ^= __funnelshift_l(i + 11 < 32 ? x[i + 11 < 32 ? i + 11 : 31] : 0u, x[i + 10], 24);
+    };
+    auto weyl = [&]() -> uint32_t {
+        step++;
+        const uint32_t y = static_cast<uint32_t>(step) * 362437u;
+        return y ^ (y >> 16);
+    };
+    if (LAYOUT == RNG_XOR_REDUCE) {
+        uint32_t acc[32];
+        float facc[32];
+#pragma unroll
+        for (int l = 0; l < 32; l++) {
+            acc[l] = 0;
+            facc[l] = 0.0f;
+        }
+        if (OUT == OUT_NORMAL) {
+            for (uint64_t k = 0; k < K; k += 2) {
+                shift_step();
+                const uint32_t y0 = weyl();
+                uint32_t a[32];
+#pragma unroll
+                for (int l = 0; l < 32; l++) a[l] = x[l] + y0;
+                shift_step();
+                const uint32_t y1 = weyl();
+#pragma unroll
+                for (int l = 0; l < 32; l++) {
+                    float z0, z1;
+                    box_muller(a[l], x[l] + y1, z0, z1);
+                    facc[l] += z0;
+                    facc[l] += z1;
+                }
+            }
+        } else {
+            for (uint64_t k = 0; k < K; k++) {
+                shift_step();
+                const uint32_t yy = weyl();
+#pragma unroll
+                for (int l = 0; l < 32; l++) {
+                    const uint32_t r = x[l] + yy;
+                    acc[l] ^= OUT == OUT_U32 ? r : __float_as_uint(u32_to_unit(r));
+                }
+            }
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(out_) + 32 * j);
+#pragma unroll
+        for (int m = 0; m < 8; m++) {
+            uint4 v;
+            if (OUT == OUT_NORMAL) {
+                v.x = __float_as_uint(facc[4 * m]);
+                v.y = __float_as_uint(facc[4 * m + 1]);
+                v.z = __float_as_uint(facc[4 * m + 2]);
+                v.w = __float_as_uint(facc[4 * m + 3]);
+            } else {
+                v.x = acc[4 * m];
+                v.y = acc[4 * m + 1];
+                v.z = acc[4 * m + 2];
+                v.w = acc[4 * m + 3];
+            }
+            dst[m] = v;
+        }
+    } else {  // RNG_STEP_MAJOR
+        uint32_t *out = static_cast<uint32_t *>(out_);
+        if (OUT == OUT_NORMAL) {
+            for (uint64_t k = 0; k < K; k += 2) {
+                shift_step();
+                const uint32_t y0 = weyl();
+                uint32_t a[32];
+#pragma unroll
+                for (int l = 0; l < 32; l++) a[l] = x[l] + y0;
+                shift_step();
+                const uint32_t y1 = weyl();
+                uint4 *row0 = reinterpret_cast<uint4 *>(out + k * n + 32 * j);
+                uint4 *row1 = reinterpret_cast<uint4 *>(out + (k + 1) * n + 32 * j);
+#pragma unroll
+                for (int m = 0; m < 8; m++) {
+                    float z0[4], z1[4];
+#pragma unroll
+                    for (int q = 0; q < 4; q++) box_muller(a[4 * m + q], x[4 * m + q] + y1, z0[q], z1[q]);
+                    __stcs(row0 + m, make_uint4(__float_as_uint(z0[0]), __float_as_uint(z0[1]),
+                                                 __float_as_uint(z0[2]), __float_as_uint(z0[3])));
+                    __stcs(row1 + m, make_uint4(__float_as_uint(z1[0]), __float_as_uint(z1[1]),
+                                                 __float_as_uint(z1[2]), __float_as_uint(z1[3])));
+                }
+            }
+        } else {
+            for (uint64_t k = 0; k < K; k++) {
+                shift_step();
+                const uint32_t yy = weyl();
+                uint4 *row = reinterpret_cast<uint4 *>(out + k * n + 32 * j);
+#pragma unroll
+                for (int m = 0; m < 8; m++) {
+                    uint32_t v[4];
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const uint32_t r = x[4 * m + q] + yy;
+                        v[q] = OUT == OUT_U32 ? r : __float_as_uint(u32_to_unit(r));
+                    }
+                    __stcs(row + m, make_uint4(v[0], v[1], v[2], v[3]));
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 8; m++)
+        reinterpret_cast<uint4 *>(state)[m] = make_uint4(x[4 * m], x[4 * m + 1], x[4 * m + 2], x[4 * m + 3]);
 }
 
 template <int KIND, int OUT>
@@ -231,12 +396,16 @@ int launch_kind_out(const GenState &g, void *out, uint64_t K, int layout, cudaSt
 {
     const DevParams p = dev_params(g);
     if constexpr (KIND == RNG_MT19937_SHARED) {
-        const dim3 grid(static_cast<unsigned>(g.n));
+        const dim3 grid(static_cast<unsigned>((g.n + kMtWarps - 1) / kMtWarps));
         switch (layout) {
         case RNG_STEP_MAJOR: k_generate_mt<OUT, RNG_STEP_MAJOR><<<grid, kMtBlock, 0, s>>>(p, out, K); break;
         case RNG_INSTANCE_MAJOR: k_generate_mt<OUT, RNG_INSTANCE_MAJOR><<<grid, kMtBlock, 0, s>>>(p, out, K); break;
         default: k_generate_mt<OUT, RNG_XOR_REDUCE><<<grid, kMtBlock, 0, s>>>(p, out, K); break;
         }
+    } else if (KIND == RNG_XS1024W && layout != RNG_INSTANCE_MAJOR && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+        const dim3 grid(static_cast<unsigned>((g.n / 32 + 63) / 64));
+        if (layout == RNG_STEP_MAJOR) k_generate_xs_reg<OUT, RNG_STEP_MAJOR><<<grid, 64, 0, s>>>(p, out, K);
+        else k_generate_xs_reg<OUT, RNG_XOR_REDUCE><<<grid, 64, 0, s>>>(p, out, K);
     } else {
         const dim3 grid(static_cast<unsigned>((g.n + kBlock - 1) / kBlock));
         switch (layout) {

@@ -130,6 +130,49 @@ def test_consume_in_register_modes(R, torch_cuda, kind):
     assert np.all(np.abs(gz - z.sum(axis=1)) <= tol)
 
 
+@pytest.mark.parametrize("layout", [0, 2])
+@pytest.mark.parametrize("out", ["u32", "f32", "normal"])
+def test_philox_block_aligned_and_misaligned(R, torch_cuda, layout, out):
+    n = 300
+    o = O.generate(O.PHILOX4X32_10, SEED, n, 2 + 96 + 96)
+    for Ks in ([96, 96], [2, 96, 96]):  # block-aligned calls, then misaligned ones
+        g = run_gpu(R, torch_cuda, O.PHILOX4X32_10, n, Ks, layout=layout, out=out)
+        start = 0
+        for K, a in zip(Ks, g):
+            ref = o[:, start:start + K]
+            start += K
+            if layout == R.RNG_XOR_REDUCE:
+                if out == "u32":
+                    assert np.array_equal(a, np.bitwise_xor.reduce(ref, axis=1))
+                elif out == "f32":
+                    assert np.array_equal(a.view(np.uint32),
+                                          np.bitwise_xor.reduce(as_f32_oracle(ref).view(np.uint32), axis=1))
+                else:
+                    z = O.box_muller(ref)
+                    assert np.all(np.abs(a - z.sum(axis=1)) <= K * NORMAL_TOL + 1e-4 * np.abs(z).sum(axis=1))
+            elif out == "u32":
+                assert np.array_equal(a, ref)
+            elif out == "f32":
+                assert np.array_equal(a, as_f32_oracle(ref))
+            else:
+                assert np.abs(a - O.box_muller(ref)).max() <= NORMAL_TOL
+
+
+def test_xs1024w_unaligned_output_pointer(R, torch_cuda):
+    torch = torch_cuda
+    n, K = 64, 10
+    h = R.rng_create(R.RNG_XS1024W, n)
+    try:
+        R.rng_seed(h, SEED)
+        buf = torch.empty(n * K + 1, dtype=torch.int32, device="cuda")
+        R.rng_generate_u32(h, buf.data_ptr() + 4, K, R.RNG_STEP_MAJOR)  # 4-byte aligned only
+        torch.cuda.synchronize()
+        g = buf[1:].cpu().numpy().view(np.uint32).reshape(K, n).T
+        assert np.array_equal(g, O.generate(O.XS1024W, SEED, n, K))
+    finally:
+        R.rng_destroy(h)
+
+
 # ------------------------------------------------- positions and seeding
 @pytest.mark.parametrize("kind", ALL_KINDS)
 def test_consecutive_calls_continue_the_streams(R, torch_cuda, kind):
