@@ -30,7 +30,15 @@ __device__ __forceinline__ Mont mont_setup(uint64_t p)
     uint64_t inv = p;  // p * p = 1 (mod 8): 3 bits correct; Newton doubles
     for (int i = 0; i < 5; i++) inv *= 2 - p * inv;
     m.pinv = 0 - inv;
-    m.r1 = (0 - p) % p;  // 2^64 mod p
+    // 2^64 mod p: for p > 2^61, 2^64 - p is below 8p, so a few subtractions
+    // replace the (slow, emulated) 64-bit remainder
+    uint64_t r1 = 0 - p;
+    if (p > (1ull << 61)) {
+        while (r1 >= p) r1 -= p;
+    } else {
+        r1 %= p;
+    }
+    m.r1 = r1;
     uint64_t r = m.r1;
     for (int i = 0; i < 64; i++) r = add_mod(r, r, p);  // r1 * 2^64 mod p
     m.r2 = r;
@@ -52,7 +60,10 @@ __device__ __forceinline__ uint64_t mont_mul(uint64_t a, uint64_t b, const Mont 
     return (ovf || s2 >= m.p) ? s2 - m.p : s2;
 }
 
-__device__ __forceinline__ uint64_t to_mont(uint64_t a, const Mont &m) { return mont_mul(a % m.p, m.r2, m); }
+__device__ __forceinline__ uint64_t to_mont(uint64_t a, const Mont &m)
+{
+    return mont_mul(a < m.p ? a : a % m.p, m.r2, m);
+}
 __device__ __forceinline__ uint64_t from_mont(uint64_t a, const Mont &m) { return mont_mul(a, 1, m); }
 
 // base^e in Montgomery form (base given in Montgomery form)
