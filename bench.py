@@ -3,7 +3,7 @@
 
 Default (N=1): the bulk workload -- 2^20 resident instances of every
 generator kind, 1024 draws each (2^30 outputs per call; the block-shared
-MT19937 as 4096 generators x 2^18 draws), written to HBM as u32, exact
+MT19937 as 32768 warp-shared generators x 2^15 draws), written to HBM as u32, exact
 uniform f32 and Box-Muller normals, and consumed in registers (u32 XOR
 reduce).  One step = those 28 calls.  `value` = outputs of all ranks /
 device time (Gnum/s).  Extra keys report the Ising sweep (flips/ns) and
@@ -33,8 +33,8 @@ sys.path.insert(0, ROOT)
 METRIC = "RNG Gnum/s (frac of HBM peak); Ising flips/ns; served p50/p99 vs plain"
 N_INST = 1 << 20
 K_DRAWS = 1024
-MT_GENS = 4096
-MT_DRAWS = 1 << 18
+MT_GENS = 1 << 15   # one generator per warp: 2^20 threads
+MT_DRAWS = 1 << 15
 SEED = 0x0123456789ABCDEF
 FORMS = ["u32", "f32", "normal", "u32_xor"]
 # state bytes moved per instance and call: load + store of the state, plus
@@ -326,8 +326,8 @@ def run_gpu(args):
             "dtype": "u32",
             "data": "synthetic",
             "config": {
-                "workload": "bulk generation: 2^20 resident instances x 1024 draws per call (MT19937: 4096 "
-                            "block-shared generators x 2^18), 7 generators x {u32, f32, normal} written to HBM + "
+                "workload": "bulk generation: 2^20 resident instances x 1024 draws per call (MT19937: 32768 "
+                            "warp-shared generators x 2^15), 7 generators x {u32, f32, normal} written to HBM + "
                             "u32 consumed in registers (XOR reduce); 28 calls per step",
                 "instances_per_gpu": N_INST, "draws_per_call": K_DRAWS, "outputs_per_step_per_gpu":
                     outputs_per_step_rank, "layout": "step-major (MT19937: instance-major)",

@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(kBlock) k_generate(DevParams p, void *out_, ui
             const uint64_t blk0 = p.pos >> 2;
             uint32_t xacc = 0;
             float facc = 0.0f;
+#pragma unroll 2
             for (uint64_t k = 0; k < K; k += 4) {
                 const uint64_t blk = blk0 + (k >> 2);
                 uint32_t o[4];
@@ -160,14 +161,47 @@ __device__ __forceinline__ uint32_t mt_mix(uint32_t cur, uint32_t nxt, uint32_t 
     return far ^ (y >> 1) ^ ((y & 1u) ? 0x9908B0DFu : 0u);
 }
 
-__device__ __forceinline__ void mt_twist_warp(uint32_t *mt, int lane)
+// Refills the state and hands each new word i (in order) to emit(i, word).
+template <typename Emit>
+__device__ __forceinline__ void mt_twist_warp(uint32_t *mt, int lane, Emit emit)
 {
-    for (int b = 0; b < MT_N; b += 32) {
+    // chunks with i + 397 < 624 (far word not yet rewritten)
+#pragma unroll 1
+    for (int b = 0; b < 224; b += 32) {
         const int i = b + lane;
-        uint32_t v = 0;
-        if (i < MT_N) v = mt_mix(mt[i], mt[i + 1 == MT_N ? 0 : i + 1], mt[i + MT_M < MT_N ? i + MT_M : i + MT_M - MT_N]);
+        const uint32_t v = mt_mix(mt[i], mt[i + 1], mt[i + MT_M]);
         __syncwarp();
-        if (i < MT_N) mt[i] = v;
+        mt[i] = v;
+        emit(i, v);
+        __syncwarp();
+    }
+    {  // the chunk that crosses i = 227
+        const int i = 224 + lane;
+        const uint32_t v = mt_mix(mt[i], mt[i + 1], mt[i < MT_N - MT_M ? i + MT_M : i - (MT_N - MT_M)]);
+        __syncwarp();
+        mt[i] = v;
+        emit(i, v);
+        __syncwarp();
+    }
+    // chunks whose far word i - 227 was rewritten in an earlier chunk
+#pragma unroll 1
+    for (int b = 256; b < 608; b += 32) {
+        const int i = b + lane;
+        const uint32_t v = mt_mix(mt[i], mt[i + 1], mt[i - (MT_N - MT_M)]);
+        __syncwarp();
+        mt[i] = v;
+        emit(i, v);
+        __syncwarp();
+    }
+    {  // the last 16 words; word 623 pairs with the new word 0
+        const int i = 608 + lane;
+        uint32_t v = 0;
+        if (i < MT_N) v = mt_mix(mt[i], mt[i + 1 == MT_N ? 0 : i + 1], mt[i - (MT_N - MT_M)]);
+        __syncwarp();
+        if (i < MT_N) {
+            mt[i] = v;
+            emit(i, v);
+        }
         __syncwarp();
     }
 }
@@ -196,23 +230,38 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
     bool twisted = false;
     uint64_t k = 0;
     while (k < K) {
-        if (mti == MT_N) {
-            mt_twist_warp(mt, lane);
-            mti = 0;
-            twisted = true;
-        }
-        const int cnt = static_cast<int>(K - k < static_cast<uint64_t>(MT_N - mti) ? K - k : MT_N - mti);
+        const bool refill = mti == MT_N;
+        const int cnt = static_cast<int>(K - k < static_cast<uint64_t>(MT_N - (refill ? 0 : mti))
+                                             ? K - k
+                                             : MT_N - (refill ? 0 : mti));
         if (OUT != OUT_NORMAL) {
-            for (int t = lane; t < cnt; t += 32) {
-                const uint32_t r = mt_temper(mt[mti + t]);
+            auto put = [&](int t, uint32_t word) {
+                const uint32_t r = mt_temper(word);
                 const uint32_t bits = OUT == OUT_U32 ? r : __float_as_uint(u32_to_unit(r));
                 if (LAYOUT == RNG_XOR_REDUCE) xacc ^= bits;
                 else __stcs(static_cast<uint32_t *>(out_) + out_index(k + t), bits);
+            };
+            if (refill) {  // the refill emits its new words as they are made
+                mt_twist_warp(mt, lane, [&](int i, uint32_t v) {
+                    if (i < cnt) put(i, v);
+                });
+                mti = 0;
+                twisted = true;
+            } else {
+                for (int t = lane; t < cnt; t += 32) put(t, mt[mti + t]);
             }
         } else {
             // buf[0] = pending word when k is odd, then the chunk
             const int off = static_cast<int>(k & 1);
-            for (int t = lane; t < cnt; t += 32) buf[off + t] = mt_temper(mt[mti + t]);
+            if (refill) {
+                mt_twist_warp(mt, lane, [&](int i, uint32_t v) {
+                    if (i < cnt) buf[off + i] = mt_temper(v);
+                });
+                mti = 0;
+                twisted = true;
+            } else {
+                for (int t = lane; t < cnt; t += 32) buf[off + t] = mt_temper(mt[mti + t]);
+            }
             if (lane == 0 && off) buf[0] = pending;
             __syncwarp();
             const uint64_t d0 = k - off;  // draw index of buf[0], even
@@ -258,13 +307,41 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
 // about seven instructions per output instead of six shuffles and a dozen
 // selects per lane.  Step-major output is then 32 consecutive words per
 // thread and step (eight 16-byte stores).
-template <int OUT, int LAYOUT>
-__global__ void __launch_bounds__(64) k_generate_xs_reg(DevParams p, void *out_, uint64_t K)
+constexpr int kXsBlock = 64;
+
+// Writes the 32 x 32 words a warp produced for one step (lane o holds the
+// words of state j0 + o) as 4 KiB of contiguous output: staged through
+// shared memory so that each 16-byte store instruction covers 512
+// consecutive bytes.
+__device__ __forceinline__ void xs_store_step(uint32_t (*tile)[33], const uint32_t (&v)[32], uint32_t *row,
+                                              uint64_t j0, uint64_t nstates, int lane)
 {
-    const uint64_t j = static_cast<uint64_t>(blockIdx.x) * 64 + threadIdx.x;
-    const uint64_t n = p.n;
-    if (j >= n / 32) return;
-    uint32_t *state = static_cast<uint32_t *>(p.s[0]) + 32 * j;
+#pragma unroll
+    for (int l = 0; l < 32; l++) tile[lane][l] = v[l];
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < 8; m++) {
+        const int c = m * 32 + lane;  // 16-byte chunk of the warp's 4 KiB
+        const int o = c >> 3, wo = (c & 7) * 4;
+        if (j0 + o < nstates)
+            __stcs(reinterpret_cast<uint4 *>(row + 32 * j0) + c,
+                   make_uint4(tile[o][wo], tile[o][wo + 1], tile[o][wo + 2], tile[o][wo + 3]));
+    }
+    __syncwarp();
+}
+
+template <int OUT, int LAYOUT>
+__global__ void __launch_bounds__(kXsBlock) k_generate_xs_reg(DevParams p, void *out_, uint64_t K)
+{
+    __shared__ uint32_t tile_s[kXsBlock / 32][32][33];
+    const uint64_t n = p.n, nstates = n / 32;
+    const uint64_t j = static_cast<uint64_t>(blockIdx.x) * kXsBlock + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const uint64_t j0 = j - lane;
+    if (j0 >= nstates) return;  // whole warps leave together
+    const bool active = j < nstates;
+    uint32_t(*tile)[33] = tile_s[threadIdx.x >> 5];
+    uint32_t *state = static_cast<uint32_t *>(p.s[0]) + 32 * (active ? j : j0);
     uint32_t x[32];
 #pragma unroll
     for (int m = 0; m < 8; m++) {
@@ -327,22 +404,19 @@ __global__ void __launch_bounds__(64) k_generate_xs_reg(DevParams p, void *out_,
                 }
             }
         }
-        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(out_) + 32 * j);
+        if (active) {
+            uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(out_) + 32 * j);
 #pragma unroll
-        for (int m = 0; m < 8; m++) {
-            uint4 v;
-            if (OUT == OUT_NORMAL) {
-                v.x = __float_as_uint(facc[4 * m]);
-                v.y = __float_as_uint(facc[4 * m + 1]);
-                v.z = __float_as_uint(facc[4 * m + 2]);
-                v.w = __float_as_uint(facc[4 * m + 3]);
-            } else {
-                v.x = acc[4 * m];
-                v.y = acc[4 * m + 1];
-                v.z = acc[4 * m + 2];
-                v.w = acc[4 * m + 3];
+            for (int m = 0; m < 8; m++) {
+                uint4 v;
+                if (OUT == OUT_NORMAL) {
+                    v = make_uint4(__float_as_uint(facc[4 * m]), __float_as_uint(facc[4 * m + 1]),
+                                   __float_as_uint(facc[4 * m + 2]), __float_as_uint(facc[4 * m + 3]));
+                } else {
+                    v = make_uint4(acc[4 * m], acc[4 * m + 1], acc[4 * m + 2], acc[4 * m + 3]);
+                }
+                dst[m] = v;
             }
-            dst[m] = v;
         }
     } else {  // RNG_STEP_MAJOR
         uint32_t *out = static_cast<uint32_t *>(out_);
@@ -355,40 +429,36 @@ __global__ void __launch_bounds__(64) k_generate_xs_reg(DevParams p, void *out_,
                 for (int l = 0; l < 32; l++) a[l] = x[l] + y0;
                 shift_step();
                 const uint32_t y1 = weyl();
-                uint4 *row0 = reinterpret_cast<uint4 *>(out + k * n + 32 * j);
-                uint4 *row1 = reinterpret_cast<uint4 *>(out + (k + 1) * n + 32 * j);
+                uint32_t z1b[32];
 #pragma unroll
-                for (int m = 0; m < 8; m++) {
-                    float z0[4], z1[4];
-#pragma unroll
-                    for (int q = 0; q < 4; q++) box_muller(a[4 * m + q], x[4 * m + q] + y1, z0[q], z1[q]);
-                    __stcs(row0 + m, make_uint4(__float_as_uint(z0[0]), __float_as_uint(z0[1]),
-                                                 __float_as_uint(z0[2]), __float_as_uint(z0[3])));
-                    __stcs(row1 + m, make_uint4(__float_as_uint(z1[0]), __float_as_uint(z1[1]),
-                                                 __float_as_uint(z1[2]), __float_as_uint(z1[3])));
+                for (int l = 0; l < 32; l++) {
+                    float z0, z1;
+                    box_muller(a[l], x[l] + y1, z0, z1);
+                    a[l] = __float_as_uint(z0);
+                    z1b[l] = __float_as_uint(z1);
                 }
+                xs_store_step(tile, a, out + k * n, j0, nstates, lane);
+                xs_store_step(tile, z1b, out + (k + 1) * n, j0, nstates, lane);
             }
         } else {
             for (uint64_t k = 0; k < K; k++) {
                 shift_step();
                 const uint32_t yy = weyl();
-                uint4 *row = reinterpret_cast<uint4 *>(out + k * n + 32 * j);
+                uint32_t v[32];
 #pragma unroll
-                for (int m = 0; m < 8; m++) {
-                    uint32_t v[4];
-#pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        const uint32_t r = x[4 * m + q] + yy;
-                        v[q] = OUT == OUT_U32 ? r : __float_as_uint(u32_to_unit(r));
-                    }
-                    __stcs(row + m, make_uint4(v[0], v[1], v[2], v[3]));
+                for (int l = 0; l < 32; l++) {
+                    const uint32_t r = x[l] + yy;
+                    v[l] = OUT == OUT_U32 ? r : __float_as_uint(u32_to_unit(r));
                 }
+                xs_store_step(tile, v, out + k * n, j0, nstates, lane);
             }
         }
     }
+    if (active) {
 #pragma unroll
-    for (int m = 0; m < 8; m++)
-        reinterpret_cast<uint4 *>(state)[m] = make_uint4(x[4 * m], x[4 * m + 1], x[4 * m + 2], x[4 * m + 3]);
+        for (int m = 0; m < 8; m++)
+            reinterpret_cast<uint4 *>(state)[m] = make_uint4(x[4 * m], x[4 * m + 1], x[4 * m + 2], x[4 * m + 3]);
+    }
 }
 
 template <int KIND, int OUT>
@@ -403,9 +473,9 @@ int launch_kind_out(const GenState &g, void *out, uint64_t K, int layout, cudaSt
         default: k_generate_mt<OUT, RNG_XOR_REDUCE><<<grid, kMtBlock, 0, s>>>(p, out, K); break;
         }
     } else if (KIND == RNG_XS1024W && layout != RNG_INSTANCE_MAJOR && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
-        const dim3 grid(static_cast<unsigned>((g.n / 32 + 63) / 64));
-        if (layout == RNG_STEP_MAJOR) k_generate_xs_reg<OUT, RNG_STEP_MAJOR><<<grid, 64, 0, s>>>(p, out, K);
-        else k_generate_xs_reg<OUT, RNG_XOR_REDUCE><<<grid, 64, 0, s>>>(p, out, K);
+        const dim3 grid(static_cast<unsigned>((g.n / 32 + kXsBlock - 1) / kXsBlock));
+        if (layout == RNG_STEP_MAJOR) k_generate_xs_reg<OUT, RNG_STEP_MAJOR><<<grid, kXsBlock, 0, s>>>(p, out, K);
+        else k_generate_xs_reg<OUT, RNG_XOR_REDUCE><<<grid, kXsBlock, 0, s>>>(p, out, K);
     } else {
         const dim3 grid(static_cast<unsigned>((g.n + kBlock - 1) / kBlock));
         switch (layout) {

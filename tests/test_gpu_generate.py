@@ -297,7 +297,7 @@ def test_full_size_sampled(R, torch_cuda, kind):
     sampled instances (every draw of each sampled instance)."""
     torch = torch_cuda
     if kind == O.MT19937_SHARED:
-        n, K, layout = 4096, 1 << 18, 1
+        n, K, layout = 1 << 15, 1 << 15, 1  # one generator per warp, 2^20 threads
     else:
         n, K, layout = 1 << 20, 1024, 0
     flags = O.SEED_SUBSTREAM if kind == O.XS1024W else 0
