@@ -472,7 +472,10 @@ int launch_kind_out(const GenState &g, void *out, uint64_t K, int layout, cudaSt
         case RNG_INSTANCE_MAJOR: k_generate_mt<OUT, RNG_INSTANCE_MAJOR><<<grid, kMtBlock, 0, s>>>(p, out, K); break;
         default: k_generate_mt<OUT, RNG_XOR_REDUCE><<<grid, kMtBlock, 0, s>>>(p, out, K); break;
         }
-    } else if (KIND == RNG_XS1024W && layout != RNG_INSTANCE_MAJOR && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+    } else if (KIND == RNG_XS1024W && OUT != OUT_NORMAL && layout != RNG_INSTANCE_MAJOR &&
+               (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+        // (normals stay on the lane-per-instance form: 32 Box-Muller pairs per
+        // thread and step leave too few threads to hide their latency)
         const dim3 grid(static_cast<unsigned>((g.n / 32 + kXsBlock - 1) / kXsBlock));
         if (layout == RNG_STEP_MAJOR) k_generate_xs_reg<OUT, RNG_STEP_MAJOR><<<grid, kXsBlock, 0, s>>>(p, out, K);
         else k_generate_xs_reg<OUT, RNG_XOR_REDUCE><<<grid, kXsBlock, 0, s>>>(p, out, K);
