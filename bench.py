@@ -43,6 +43,22 @@ FORMS = ["u32", "f32", "normal", "u32_xor"]
 STATE_TRAFFIC = {0: 8, 1: 16, 2: 20, 3: 48, 4: 8, 5: 8, 6: 2 * 624 * 4}
 
 
+def shard_range(rank: int, world: int, per_rank: int):
+    """Instances [first, first + count) of an (world * per_rank)-instance
+    generator held by `rank` (weak scaling: per-rank work is fixed)."""
+    return rank * per_rank, per_rank, world * per_rank
+
+
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """The slowest rank's time: every rank contributes its elapsed time."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -135,10 +151,8 @@ class Bulk:
         self.R, self.torch = R, torch
         self.handles = {}
         for kind in range(7):
-            if kind == R.RNG_MT19937_SHARED:
-                n, first, total = MT_GENS, rank * MT_GENS, world * MT_GENS
-            else:
-                n, first, total = N_INST, rank * N_INST, world * N_INST
+            per = MT_GENS if kind == R.RNG_MT19937_SHARED else N_INST
+            first, n, total = shard_range(rank, world, per)
             h = R.rng_create_shard(kind, total, first, n, 0)
             R.rng_seed(h, SEED)
             self.handles[kind] = (h, n)
@@ -224,11 +238,7 @@ def run_gpu(args):
     t1.record(stream)
     barrier()
     clk = clocks.stop()
-    elapsed_ms = t0.elapsed_time(t1)
-    if world > 1:
-        tt = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
+    elapsed_ms = max_over_ranks(t0.elapsed_time(t1), dist if world > 1 else None, "cuda")
 
     per = {}
     for c, a, b in ev:
@@ -291,11 +301,7 @@ def run_gpu(args):
                 d2h += nbytes
         s1.record(stream)
         barrier()
-        e_ms = s0.elapsed_time(s1)
-        if world > 1:
-            tt = torch.tensor([e_ms], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e_ms = float(tt.item())
+        e_ms = max_over_ranks(s0.elapsed_time(s1), dist if world > 1 else None, "cuda")
         e2e = {"value": round(outputs_per_step_rank * world * e_steps / (e_ms * 1e-3) / 1e9, 2), "unit": "Gnum/s",
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h // e_steps, "steps": e_steps,
                "note": "seed passed by value (no input arrays); every output copied to pinned host memory"}

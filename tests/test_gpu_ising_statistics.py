@@ -1,0 +1,100 @@
+"""The application test of Sec. 2 on the GPU: internal energy e = -<E>/N
+and specific heat C_V = beta^2 var(E)/N from the persistent kernel against
+the exact finite-lattice values (tests/golden/exact_ising.json, written by a
+script that calls only the oracle), as the deviation in units of the
+estimated standard error (the Delta_rel of Table 1).  The 32-bit LCG in
+skip-ahead (leapfrog) order is the paper's negative control."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SEED = 0x0123456789ABCDEF
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1204_6193_gb300 as R
+    return R
+
+
+def exact(L, beta):
+    with open(os.path.join(HERE, "golden", "exact_ising.json")) as f:
+        for c in json.load(f)["cases"]:
+            if c["L"] == L and abs(c["beta"] - beta) < 1e-12:
+                return c["e"], c["C_V"]
+    raise KeyError((L, beta))
+
+
+def measure(R, L, beta, kind, flags=0, layout=0, equil=2000, bins=40, per_bin=2500):
+    """Bin averages of e and C_V from the accumulators (one measurement per sweep)."""
+    N = L * L
+    h = R.ising_create(L, beta, layout, kind, flags, SEED, 2)
+    try:
+        R.ising_sweep(h, equil)
+        prev = R.ising_observables(h)
+        e_b, c_b = [], []
+        for _ in range(bins):
+            R.ising_sweep(h, per_bin, 1)
+            cur = R.ising_observables(h)
+            n = cur["n_meas"] - prev["n_meas"]
+            sE = cur["acc"][0] - prev["acc"][0]
+            sE2 = cur["acc"][1] - prev["acc"][1]
+            mE, mE2 = sE / n, sE2 / n
+            e_b.append(-mE / N)
+            c_b.append(beta * beta * (mE2 - mE * mE) / N)
+            prev = cur
+    finally:
+        R.ising_destroy(h)
+    e_b, c_b = np.array(e_b), np.array(c_b)
+    return (e_b.mean(), e_b.std(ddof=1) / np.sqrt(bins)), (c_b.mean(), c_b.std(ddof=1) / np.sqrt(bins))
+
+
+@pytest.mark.parametrize("kind", [3, 5, 4])  # xorwow, the paper's generator, Philox
+@pytest.mark.parametrize("L,beta", [(64, 0.4), (128, 0.4)])
+def test_energy_and_specific_heat_match_exact(R, kind, L, beta):
+    (e, de), (cv, dcv) = measure(R, L, beta, kind)
+    e_ex, cv_ex = exact(L, beta)
+    print(f"L={L} beta={beta} kind={kind}: e={e:.6f}({de:.1e}) exact {e_ex:.6f} "
+          f"Delta_rel={(e - e_ex) / de:+.2f}; C_V={cv:.5f}({dcv:.1e}) exact {cv_ex:.5f} "
+          f"Delta_rel={(cv - cv_ex) / dcv:+.2f}")
+    assert abs(e - e_ex) < 4.5 * de
+    # each bin's variance estimate is biased low by O(tau / per_bin)
+    assert abs(cv - cv_ex) < 4.5 * dcv + 0.01 * cv_ex
+
+
+def test_critical_point_L64_multispin(R):
+    (e, de), (cv, dcv) = measure(R, 64, float(np.log(1 + np.sqrt(2)) / 2), 5, layout=1, equil=20000,
+                                 bins=40, per_bin=10000)
+    e_ex, cv_ex = exact(64, float(np.log(1 + np.sqrt(2)) / 2))
+    print(f"beta_c L=64: e={e:.5f}({de:.1e}) exact {e_ex:.5f}; C_V={cv:.4f}({dcv:.1e}) exact {cv_ex:.4f}")
+    assert abs(e - e_ex) < 4.5 * de
+    assert abs(cv - cv_ex) < 4.5 * dcv + 0.03 * cv_ex
+
+
+def test_table_1_lattice_beta_04_energy(R):
+    # the paper's lattice (1024^2, beta = 0.4) with the paper's generator;
+    # e only: 4e4 sweeps resolve it to about 3e-5
+    (e, de), (cv, dcv) = measure(R, 1024, 0.4, 5, equil=1000, bins=20, per_bin=2000)
+    e_ex, cv_ex = exact(1024, 0.4)
+    print(f"L=1024 beta=0.4: e={e:.7f}({de:.1e}) exact {e_ex:.7f} Delta_rel={(e - e_ex) / de:+.2f}; "
+          f"C_V={cv:.4f}({dcv:.1e}) exact {cv_ex:.4f}")
+    assert abs(e - e_ex) < 4.5 * de
+
+
+def test_lcg32_leapfrog_deviates_as_in_table_1(R):
+    # Table 1: the 32-bit LCG consumed in skip-ahead order on the GPU gives
+    # a highly significant deviation of e (Delta_rel = -8259 after 1e7
+    # sweeps).  With all instances interleaving one power-of-two-strided
+    # sequence the deviation is large already after a few thousand sweeps.
+    (e, de), _ = measure(R, 64, 0.4, 0, flags=1, bins=20, per_bin=1000)
+    e_ex, _ = exact(64, 0.4)
+    dr = (e - e_ex) / de
+    print(f"LCG32 leapfrog L=64 beta=0.4: e={e:.6f}({de:.1e}) exact {e_ex:.6f} Delta_rel={dr:+.1f}")
+    assert abs(dr) > 10
