@@ -34,14 +34,15 @@ __global__ void __launch_bounds__(kBlock) k_generate(DevParams p, void *out_, ui
         // block-aligned calls: one block evaluation yields draws k..k+3
         if (LAYOUT != RNG_INSTANCE_MAJOR && (p.pos & 3) == 0 && (K & 3) == 0) {
             const uint64_t blk0 = p.pos >> 2;
+            const PhiloxKeys keys(g.k0, g.k1);
             uint32_t xacc = 0;
             float facc = 0.0f;
 #pragma unroll 2
             for (uint64_t k = 0; k < K; k += 4) {
                 const uint64_t blk = blk0 + (k >> 2);
                 uint32_t o[4];
-                philox_block<10>(static_cast<uint32_t>(blk), static_cast<uint32_t>(blk >> 32), 0u, 0u, g.k0, g.k1,
-                                 o[0], o[1], o[2], o[3]);
+                philox10_keys(static_cast<uint32_t>(blk), static_cast<uint32_t>(blk >> 32), 0u, 0u, keys, o[0], o[1],
+                              o[2], o[3]);
                 if (OUT == OUT_NORMAL) {
                     float z[4];
                     box_muller(o[0], o[1], z[0], z[1]);
