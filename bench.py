@@ -277,34 +277,77 @@ def run_gpu(args):
         "traffic": ncu_traffic(name),
     }
 
-    # end to end through the C ABI with host buffers: reseed from a host seed,
-    # generate, copy every output to pinned host memory
+    # end to end through the C ABI with host buffers: each step reseeds from a
+    # host seed and every output ends in pinned host memory, either written
+    # there directly by the kernels (host memory is device-addressable over
+    # NVLink-C2C) or generated into device memory and copied on a second
+    # stream while the next call generates; the faster is reported
     e2e = None
     if not args.no_e2e:
+        e_steps = max(1, min(2, args.steps))
         host = torch.empty(N_INST * K_DRAWS, dtype=torch.int32, pin_memory=True)
         hred = torch.empty(N_INST, dtype=torch.int32, pin_memory=True)
-        e_steps = max(1, min(2, args.steps))
-        barrier()
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        d2h = 0
-        for st in range(e_steps):
-            for kind in range(7):
-                R.rng_seed(bulk.handles[kind][0], SEED + 1 + st)
-            for c in calls:
-                bulk.launch(c, sptr)
-                nbytes = c[4] * 4 if c[2] == "u32_xor" else c[4] * c[5] * 4
-                src = bulk.red if c[2] == "u32_xor" else bulk.out
-                dst = hred if c[2] == "u32_xor" else host
-                dst[: nbytes // 4].copy_(src[: nbytes // 4], non_blocking=True)
-                d2h += nbytes
-        s1.record(stream)
-        barrier()
-        e_ms = max_over_ranks(s0.elapsed_time(s1), dist if world > 1 else None, "cuda")
-        e2e = {"value": round(outputs_per_step_rank * world * e_steps / (e_ms * 1e-3) / 1e9, 2), "unit": "Gnum/s",
-               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h // e_steps, "steps": e_steps,
-               "note": "seed passed by value (no input arrays); every output copied to pinned host memory"}
+        out_bytes = [c[4] * 4 if c[2] == "u32_xor" else c[4] * c[5] * 4 for c in calls]
+
+        def run_direct():
+            for st in range(e_steps):
+                for kind in range(7):
+                    R.rng_seed(bulk.handles[kind][0], SEED + 1 + st)
+                for c in calls:
+                    launch_into(c, hred.data_ptr() if c[2] == "u32_xor" else host.data_ptr())
+
+        def launch_into(c, ptr):
+            _, kind, form, h, n, K, lay = c
+            if form == "u32":
+                R.rng_generate_u32(h, ptr, K, lay, sptr)
+            elif form == "f32":
+                R.rng_generate_f32(h, ptr, K, lay, sptr)
+            elif form == "normal":
+                R.rng_generate_normal(h, ptr, K, lay, sptr)
+            else:
+                R.rng_generate_u32(h, ptr, K, R.RNG_XOR_REDUCE, sptr)
+
+        copy_stream = torch.cuda.Stream()
+        dev2 = torch.empty(N_INST * K_DRAWS, dtype=torch.int32, device="cuda")
+        bufs = [bulk.out, dev2]
+        done_ev = [torch.cuda.Event(), torch.cuda.Event()]
+
+        def run_copy():
+            i = 0
+            for st in range(e_steps):
+                for kind in range(7):
+                    R.rng_seed(bulk.handles[kind][0], SEED + 1 + st)
+                for c in calls:
+                    b = bufs[i % 2]
+                    stream.wait_event(done_ev[i % 2])  # copy from two calls ago has drained
+                    src = bulk.red if c[2] == "u32_xor" else b
+                    launch_into(c, src.data_ptr())
+                    gen_ev = torch.cuda.Event()
+                    gen_ev.record(stream)
+                    copy_stream.wait_event(gen_ev)
+                    nb = out_bytes[calls.index(c)] // 4
+                    with torch.cuda.stream(copy_stream):
+                        (hred if c[2] == "u32_xor" else host)[:nb].copy_(src[:nb], non_blocking=True)
+                    done_ev[i % 2].record(copy_stream)
+                    i += 1
+            stream.wait_stream(copy_stream)
+
+        variants = {}
+        for name, fn in (("direct", run_direct), ("copy_overlapped", run_copy)):
+            barrier()
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            fn()
+            s1.record(stream)
+            barrier()
+            e_ms = max_over_ranks(s0.elapsed_time(s1), dist if world > 1 else None, "cuda")
+            variants[name] = round(outputs_per_step_rank * world * e_steps / (e_ms * 1e-3) / 1e9, 2)
+        best = max(variants, key=variants.get)
+        e2e = {"value": variants[best], "unit": "Gnum/s", "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": sum(out_bytes), "steps": e_steps, "variant": best, "variants": variants,
+               "note": "seed passed by value (no input arrays); every output lands in pinned host memory"}
+        del dev2
 
     bulk.close()
     extra = {}
