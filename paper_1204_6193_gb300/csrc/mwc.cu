@@ -1,8 +1,9 @@
 // mwc.cu -- the multiply-with-carry multiplier table (Sec. 3): the
 // descending list of a < 2^32 for which p = a 2^32 - 1 and q = (p - 1)/2 =
 // a 2^31 - 1 are both prime (p a safe prime), starting from 4294967118.
-// Candidates are tested in parallel on the device (trial division by small
-// primes, then Miller-Rabin on q and p) and compacted in descending order.
+// Candidates are sieved in shared memory by the odd primes below 2^16, the
+// survivors tested by Miller-Rabin on q and p, and the hits compacted in
+// descending order of a.
 #include <mutex>
 #include <vector>
 
@@ -13,57 +14,109 @@ namespace rngx {
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kNumSmall = 96;  // odd primes 3 .. 503
+constexpr int kSeg = 1 << 16;           // candidates sieved by one block
+constexpr uint32_t kSieveLimit = 1 << 16;  // odd primes below this sieve the candidates
+constexpr uint32_t kSmall = 1024;          // primes below this are marked by the whole block
 
-// For each small odd prime l: the residues of a that make l divide p or q,
-// i.e. a = (2^32)^(-1) and a = (2^31)^(-1) (mod l); computed on the host.
-struct SmallPrimes {
-    uint32_t l[kNumSmall], rp[kNumSmall], rq[kNumSmall];
-};
-__constant__ SmallPrimes c_small;
-
-__global__ void k_flags(uint64_t a_hi, uint64_t count, uint32_t *flags, uint32_t *block_counts)
+// One block sieves kSeg consecutive candidates c (multiplier a = a_hi - c):
+// a candidate is composite when an odd prime l < 2^16 divides p = a 2^32 - 1
+// or q = a 2^31 - 1, i.e. when a = (2^32)^(-1) or (2^31)^(-1) (mod l).  The
+// survivors (about 1%) then go through Miller-Rabin for q and p; flags get
+// one bit per candidate, block_counts the hits of the block.
+__global__ void __launch_bounds__(kBlock) k_flags(uint64_t a_hi, uint64_t count, const uint32_t *primes,
+                                                  const uint32_t *rp, const uint32_t *rq, int nprimes,
+                                                  uint32_t *flags, uint32_t *block_counts)
 {
-    const uint64_t c = static_cast<uint64_t>(blockIdx.x) * kBlock + threadIdx.x;
-    bool hit = false;
-    if (c < count && a_hi >= c + 2) {
-        const uint32_t a = static_cast<uint32_t>(a_hi - c);
-        bool ok = true;
-        for (int k = 0; k < kNumSmall && ok; k++) {
-            const uint32_t r = a % c_small.l[k];
-            ok = r != c_small.rp[k] && r != c_small.rq[k];
+    __shared__ uint32_t comp[kSeg / 32];
+    __shared__ uint32_t warp_hits[kBlock / 32];
+    const uint64_t c0 = static_cast<uint64_t>(blockIdx.x) * kSeg;
+    for (int w = threadIdx.x; w < kSeg / 32; w += kBlock) {
+        uint32_t m = 0;
+        for (int b = 0; b < 32; b++) {
+            const uint64_t c = c0 + 32 * w + b;
+            if (c >= count || a_hi < c + 2) m |= 1u << b;  // past the chunk, or a < 2
         }
-        if (ok) {
-            const uint64_t p = (static_cast<uint64_t>(a) << 32) - 1, q = (static_cast<uint64_t>(a) << 31) - 1;
-            hit = is_prime_odd64(q) && is_prime_odd64(p);
-        }
-    }
-    const unsigned ballot = __ballot_sync(0xffffffffu, hit);
-    __shared__ uint32_t warp_counts[kBlock / 32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) {
-        flags[blockIdx.x * (kBlock / 32) + w] = ballot;
-        warp_counts[w] = __popc(ballot);
+        comp[w] = m;
     }
     __syncthreads();
+    // primes below kSmall mark many candidates each: all threads share their
+    // marks; the larger primes are spread one per thread
+    int k = 0;
+    for (; k < nprimes && primes[k] < kSmall; k++) {
+        const uint32_t l = primes[k];
+        const uint32_t ah = static_cast<uint32_t>(a_hi % l), cm = static_cast<uint32_t>(c0 % l);
+        for (int j = 0; j < 2; j++) {
+            // a_hi - c = r (mod l)  <=>  c = a_hi - r (mod l)
+            const uint32_t t = (ah + l - (j ? rq[k] : rp[k])) % l;
+            const uint32_t start = (t + l - cm) % l;
+            for (uint32_t c = start + threadIdx.x * l; c < static_cast<uint32_t>(kSeg); c += kBlock * l)
+                atomicOr(&comp[c >> 5], 1u << (c & 31));
+        }
+    }
+    for (k += threadIdx.x; k < nprimes; k += kBlock) {
+        const uint32_t l = primes[k];
+        const uint32_t ah = static_cast<uint32_t>(a_hi % l), cm = static_cast<uint32_t>(c0 % l);
+        for (int j = 0; j < 2; j++) {
+            const uint32_t t = (ah + l - (j ? rq[k] : rp[k])) % l;
+            for (uint32_t c = (t + l - cm) % l; c < static_cast<uint32_t>(kSeg); c += l)
+                atomicOr(&comp[c >> 5], 1u << (c & 31));
+        }
+    }
+    __syncthreads();
+    // each thread tests the survivors of 8 consecutive words (256 candidates)
+    uint32_t hits = 0;
+    const int w0 = threadIdx.x * (kSeg / 32 / kBlock);
+    for (int w = w0; w < w0 + kSeg / 32 / kBlock; w++) {
+        uint32_t live = ~comp[w], out = 0;
+        while (live) {
+            const int b = __ffs(live) - 1;
+            live &= live - 1;
+            const uint32_t a = static_cast<uint32_t>(a_hi - (c0 + 32 * w + b));
+            const uint64_t p = (static_cast<uint64_t>(a) << 32) - 1, q = (static_cast<uint64_t>(a) << 31) - 1;
+            if (is_prime_odd64(q) && is_prime_odd64(p)) out |= 1u << b;
+        }
+        flags[(c0 >> 5) + w] = out;
+        hits += __popc(out);
+    }
+    for (int o = 16; o > 0; o >>= 1) hits += __shfl_down_sync(0xffffffffu, hits, o);
+    if ((threadIdx.x & 31) == 0) warp_hits[threadIdx.x >> 5] = hits;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t s = 0;
-        for (int i = 0; i < kBlock / 32; i++) s += warp_counts[i];
-        block_counts[blockIdx.x] = s;
+        uint32_t t = 0;
+        for (int i = 0; i < kBlock / 32; i++) t += warp_hits[i];
+        block_counts[blockIdx.x] = t;
     }
 }
 
-__global__ void k_scatter(uint64_t a_hi, uint64_t count, const uint32_t *flags, const uint64_t *block_offsets,
-                          uint32_t *table, uint64_t base, uint64_t cap)
+// Writes the hits of each block in candidate order (descending a) at the
+// block's offset of the running table.
+__global__ void __launch_bounds__(kBlock) k_scatter(uint64_t a_hi, const uint32_t *flags, const uint64_t *block_offsets,
+                                                    uint32_t *table, uint64_t base, uint64_t cap)
 {
-    const uint64_t c = static_cast<uint64_t>(blockIdx.x) * kBlock + threadIdx.x;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const uint32_t ballot = flags[blockIdx.x * (kBlock / 32) + w];
-    if (c >= count || !((ballot >> lane) & 1)) return;
-    uint64_t rank = block_offsets[blockIdx.x];
-    for (int i = 0; i < w; i++) rank += __popc(flags[blockIdx.x * (kBlock / 32) + i]);
-    rank += __popc(ballot & ((1u << lane) - 1));
-    if (base + rank < cap) table[base + rank] = static_cast<uint32_t>(a_hi - c);
+    __shared__ uint32_t scan[kBlock];
+    const uint64_t c0 = static_cast<uint64_t>(blockIdx.x) * kSeg;
+    const int per = kSeg / 32 / kBlock;
+    const int w0 = threadIdx.x * per;
+    uint32_t mine = 0;
+    for (int w = w0; w < w0 + per; w++) mine += __popc(flags[(c0 >> 5) + w]);
+    scan[threadIdx.x] = mine;
+    __syncthreads();
+    for (int o = 1; o < kBlock; o <<= 1) {  // inclusive scan
+        const uint32_t v = threadIdx.x >= o ? scan[threadIdx.x - o] : 0;
+        __syncthreads();
+        scan[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint64_t pos = base + block_offsets[blockIdx.x] + scan[threadIdx.x] - mine;
+    for (int w = w0; w < w0 + per; w++) {
+        uint32_t f = flags[(c0 >> 5) + w];
+        while (f) {
+            const int b = __ffs(f) - 1;
+            f &= f - 1;
+            if (pos < cap) table[pos] = static_cast<uint32_t>(a_hi - (c0 + 32 * w + b));
+            pos++;
+        }
+    }
 }
 
 uint64_t host_powmod(uint64_t b, uint64_t e, uint64_t m)
@@ -83,7 +136,9 @@ struct Table {
     uint32_t *d = nullptr;
     uint64_t cap = 0, count = 0;
     uint64_t next_a = 0xffffffffull;  // next candidate to test
-    bool consts = false;
+    uint32_t *d_primes = nullptr;     // odd primes below 2^16 and their residues
+    uint32_t *d_rp = nullptr, *d_rq = nullptr;
+    int nprimes = 0;
 };
 Table g_tab[64];
 
@@ -99,23 +154,25 @@ int mwc_table(uint64_t need, const uint32_t **d_table, cudaStream_t s)
     }
     Table &t = g_tab[dev];
     std::lock_guard<std::mutex> lock(t.mu);
-    if (!t.consts) {
-        SmallPrimes sp;
-        int k = 0;
-        for (uint32_t l = 3; k < kNumSmall; l += 2) {
-            bool prime = true;
-            for (uint32_t d = 3; d * d <= l; d += 2)
-                if (l % d == 0) prime = false;
-            if (!prime) continue;
-            const uint64_t inv32 = host_powmod(host_powmod(2, 32, l), l - 2, l);
-            const uint64_t inv31 = host_powmod(host_powmod(2, 31, l), l - 2, l);
-            sp.l[k] = l;
-            sp.rp[k] = static_cast<uint32_t>(inv32);
-            sp.rq[k] = static_cast<uint32_t>(inv31);
-            k++;
+    if (!t.d_primes) {
+        std::vector<uint32_t> pr, rp, rq;
+        std::vector<char> compo(kSieveLimit, 0);
+        for (uint32_t l = 3; l < kSieveLimit; l += 2) {
+            if (compo[l]) continue;
+            for (uint64_t m = static_cast<uint64_t>(l) * l; m < kSieveLimit; m += 2 * l) compo[m] = 1;
+            pr.push_back(l);
+            // the a that make l divide a 2^32 - 1 (resp. a 2^31 - 1)
+            rp.push_back(static_cast<uint32_t>(host_powmod(host_powmod(2, 32, l), l - 2, l)));
+            rq.push_back(static_cast<uint32_t>(host_powmod(host_powmod(2, 31, l), l - 2, l)));
         }
-        RNGX_CHECK_CUDA(cudaMemcpyToSymbol(c_small, &sp, sizeof(sp)));
-        t.consts = true;
+        const size_t nb = pr.size() * 4;
+        RNGX_CHECK_CUDA(cudaMalloc(&t.d_primes, 3 * nb));
+        t.d_rp = t.d_primes + pr.size();
+        t.d_rq = t.d_rp + pr.size();
+        RNGX_CHECK_CUDA(cudaMemcpy(t.d_primes, pr.data(), nb, cudaMemcpyHostToDevice));
+        RNGX_CHECK_CUDA(cudaMemcpy(t.d_rp, rp.data(), nb, cudaMemcpyHostToDevice));
+        RNGX_CHECK_CUDA(cudaMemcpy(t.d_rq, rq.data(), nb, cudaMemcpyHostToDevice));
+        t.nprimes = static_cast<int>(pr.size());
     }
     if (t.count < need) {
         // room for the request plus one chunk's worth of hits (a chunk of
@@ -137,7 +194,7 @@ int mwc_table(uint64_t need, const uint32_t **d_table, cudaStream_t s)
             t.cap = cap;
         }
         const uint64_t chunk = 1ull << 26;
-        const uint64_t nblocks = chunk / kBlock;
+        const uint64_t nblocks = chunk / kSeg;
         uint32_t *flags = nullptr, *counts = nullptr;
         uint64_t *offs = nullptr;
         RNGX_CHECK_CUDA(cudaMalloc(&flags, chunk / 8));
@@ -153,7 +210,8 @@ int mwc_table(uint64_t need, const uint32_t **d_table, cudaStream_t s)
                 break;
             }
             const uint64_t cnt = t.next_a - 1 < chunk ? t.next_a - 1 : chunk;
-            k_flags<<<static_cast<unsigned>(nblocks), kBlock, 0, s>>>(t.next_a, cnt, flags, counts);
+            k_flags<<<static_cast<unsigned>(nblocks), kBlock, 0, s>>>(t.next_a, cnt, t.d_primes, t.d_rp, t.d_rq,
+                                                                     t.nprimes, flags, counts);
             cudaError_t e = cudaMemcpyAsync(h_counts.data(), counts, nblocks * 4, cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) {
@@ -167,7 +225,7 @@ int mwc_table(uint64_t need, const uint32_t **d_table, cudaStream_t s)
             }
             e = cudaMemcpyAsync(offs, h_offs.data(), nblocks * 8, cudaMemcpyHostToDevice, s);
             if (e == cudaSuccess) {
-                k_scatter<<<static_cast<unsigned>(nblocks), kBlock, 0, s>>>(t.next_a, cnt, flags, offs, t.d, t.count,
+                k_scatter<<<static_cast<unsigned>(nblocks), kBlock, 0, s>>>(t.next_a, flags, offs, t.d, t.count,
                                                                               t.cap);
                 e = cudaGetLastError();
             }
