@@ -70,6 +70,7 @@ def lib():
                 "orc_ising_energy": (None, [u32, p, p, p]),
                 "orc_ising_run": (i32, [u32, dbl, i32, u32, u64, u32, u64, u32, i32, p, p, p]),
                 "orc_mt19937_raw": (None, [u32, u64, p]),
+                "orc_ising_run_multihit": (i32, [u32, dbl, i32, u32, u64, u32, u32, u32, u64, u32, i32, p, p, p]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -210,6 +211,19 @@ def ising_run(L: int, beta: float, kind: int, seed: int, n_sweeps: int, *, G: in
     nm = ctypes.c_uint64()
     _check(lib().orc_ising_run(L, beta, kind, flags, seed & (2**64 - 1), G, n_sweeps, measure_every,
                                philox_rounds, _ptr(s), _ptr(acc), ctypes.byref(nm)), "ising_run")
+    return s, acc, nm.value
+
+
+def ising_run_multihit(L: int, beta: float, kind: int, seed: int, n_rounds: int, *, k: int, n_strips: int,
+                       G: int = 2, flags: int = 0, measure_every: int = 0, spins: np.ndarray | None = None,
+                       philox_rounds: int = 10):
+    """n_rounds double-checkerboard rounds of k hits; returns (spins, acc[4], n_meas)."""
+    s = ising_init_spins(L, seed) if spins is None else np.ascontiguousarray(spins, dtype=np.int8).copy()
+    acc = np.zeros(4, dtype=np.int64)
+    nm = ctypes.c_uint64()
+    _check(lib().orc_ising_run_multihit(L, beta, kind, flags, seed & (2**64 - 1), G, n_strips, k, n_rounds,
+                                        measure_every, philox_rounds, _ptr(s), _ptr(acc), ctypes.byref(nm)),
+           "ising_run_multihit")
     return s, acc, nm.value
 
 

@@ -959,6 +959,96 @@ int orc_ising_run(uint32_t L, double beta, int kind, uint32_t flags, uint64_t se
     return ORC_OK;
 }
 
+/*
+ * Multi-hit updates with a double checkerboard (Sec. 2: "k hits" per tile
+ * load, with k = 1 and k = 100 in Table 1).  The lattice is cut into
+ * n_strips strips of L / n_strips rows (n_strips even); strip b has coarse
+ * colour b & 1.  A round is: for coarse colour C = 0, 1 in turn, k sweeps
+ * (colour 0 then colour 1 sites) over the rows of every strip of coarse
+ * colour C, while the strips of the other coarse colour -- the only
+ * neighbours of those rows outside the strip -- stay fixed.  In each
+ * half-sweep every stream of an updated strip draws one number per owned
+ * site, in increasing q, as in orc_ising_run.  Every step is a single-site
+ * Metropolis update, so the Boltzmann distribution is left invariant.
+ * Measurements (if measure_every > 0) follow every measure_every-th round.
+ */
+int orc_ising_run_multihit(uint32_t L, double beta, int kind, uint32_t flags, uint64_t seed, uint32_t G,
+                           uint32_t n_strips, uint32_t k_hits, uint64_t n_rounds, uint32_t measure_every,
+                           int philox_rounds, int8_t *s, int64_t acc[4], uint64_t *n_meas)
+{
+    if (L < 2 || L % 2 || G == 0 || (L / 2) % G || kind == K_MT || n_strips < 2 || n_strips % 2 ||
+        L % n_strips || k_hits == 0)
+        return ORC_EINVAL;
+    uint64_t nstreams = (uint64_t)L * L / 2 / G;
+    uint64_t n = kind == K_XS1024W ? (nstreams + 31) / 32 * 32 : nstreams;
+    int st = check_kind_flags(kind, flags, n);
+    if (st) return st;
+    uint64_t T[9] = {0};
+    T[4] = orc_ising_threshold(beta, 4);
+    T[8] = orc_ising_threshold(beta, 8);
+    uint64_t spr = (uint64_t)(L / 2) / G;       /* streams per row */
+    uint64_t rows = L / n_strips;               /* rows per strip */
+    uint64_t per_strip = rows * spr;            /* streams per strip */
+    if (kind == K_XS1024W && per_strip % 32) return ORC_EINVAL;  /* a warp state within one strip */
+
+    inst_t *inst = NULL;
+    uint32_t *xs = NULL;
+    uint64_t *xs_steps = NULL;   /* the Weyl step count of each warp state */
+    uint64_t nwarps = n / 32;
+    if (kind == K_XS1024W) {
+        xs = (uint32_t *)malloc(nwarps * XS_WORDS * sizeof(uint32_t));
+        xs_steps = (uint64_t *)calloc(nwarps, sizeof(uint64_t));
+        if (!xs || !xs_steps) { free(xs); free(xs_steps); return ORC_ENOMEM; }
+        for (uint64_t j = 0; j < nwarps; j++)
+            if ((st = xs_warp_init(flags, seed, j, xs + j * XS_WORDS))) { free(xs); free(xs_steps); return st; }
+    } else {
+        inst = (inst_t *)calloc(n, sizeof(inst_t));
+        if (!inst) return ORC_ENOMEM;
+        for (uint64_t i = 0; i < n; i++)
+            if ((st = inst_init(&inst[i], kind, flags, seed, n, i))) { free(inst); return st; }
+    }
+    for (uint64_t t = 1; t <= n_rounds; t++) {
+        for (uint32_t C = 0; C < 2; C++) {
+            for (uint32_t hit = 0; hit < k_hits; hit++) {
+                for (int c = 0; c < 2; c++) {
+                    for (uint32_t b = C; b < n_strips; b += 2) {
+                        uint64_t s0 = b * per_strip, s1 = s0 + per_strip;
+                        if (kind == K_XS1024W) {
+                            for (uint32_t g = 0; g < G; g++)
+                                for (uint64_t j = s0 / 32; j < s1 / 32; j++) {
+                                    uint32_t o[XS_WORDS];
+                                    xs_steps[j]++;
+                                    xs_step(xs + j * XS_WORDS, xs_steps[j], o);
+                                    for (int l = 0; l < XS_WORDS; l++) {
+                                        uint64_t sidx = 32 * j + l;
+                                        if (sidx < nstreams) ising_site(L, s, sidx * G + g, c, o[l], T);
+                                    }
+                                }
+                        } else {
+                            for (uint64_t sidx = s0; sidx < s1; sidx++)
+                                for (uint32_t g = 0; g < G; g++)
+                                    ising_site(L, s, sidx * G + g, c, inst_next(&inst[sidx], philox_rounds), T);
+                        }
+                    }
+                }
+            }
+        }
+        if (measure_every && t % measure_every == 0) {
+            int64_t E, M;
+            orc_ising_energy(L, s, &E, &M);
+            acc[0] += E;
+            acc[1] += E * E;
+            acc[2] += M * M;
+            acc[3] += M < 0 ? -M : M;
+            (*n_meas)++;
+        }
+    }
+    free(xs);
+    free(xs_steps);
+    free(inst);
+    return ORC_OK;
+}
+
 /* The MT19937 generator alone, for the standard-library comparison:
  * out[k] = k-th output after seeding with the 32-bit seed s. */
 void orc_mt19937_raw(uint32_t s, uint64_t K, uint32_t *out)

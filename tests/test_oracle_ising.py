@@ -141,3 +141,43 @@ def test_infinite_temperature_flips_every_site_once_per_sweep():
     assert np.array_equal(out, -init)
     out2, _, _ = O.ising_run(32, 0.0, O.LCG64, 5, 2)
     assert np.array_equal(out2, init)
+
+
+# ------------------------------------------- multi-hit (double checkerboard)
+def test_multihit_infinite_temperature_flips_k_times_per_round():
+    init = O.ising_init_spins(16, 4)
+    for k in (1, 2, 3):
+        out, _, _ = O.ising_run_multihit(16, 0.0, O.XORWOW, 4, 1, k=k, n_strips=4)
+        assert np.array_equal(out, init if k % 2 == 0 else -init)
+
+
+def test_multihit_zero_temperature_energy_never_increases():
+    s = O.ising_init_spins(16, 9)
+    E_prev = O.ising_energy(s)[0]
+    for t in range(10):
+        s, _, _ = O.ising_run_multihit(16, 50.0, O.PHILOX4X32_10, 9 + t, 1, k=3, n_strips=2, spins=s)
+        E = O.ising_energy(s)[0]
+        assert E <= E_prev
+        E_prev = E
+
+
+@pytest.mark.parametrize("k,strips", [(1, 2), (5, 4)])
+@pytest.mark.parametrize("beta", [0.3, 0.4])
+def test_multihit_chain_reproduces_exact_energy(k, strips, beta):
+    # single-site Metropolis steps in any order keep the Boltzmann weights:
+    # e and C_V of an 8x8 torus from 50 independent chunks
+    L, chunks, rounds = 8, 50, 2000 // k
+    e_c, cv_c = [], []
+    N = L * L
+    for c in range(chunks):
+        s0, _, _ = O.ising_run_multihit(L, beta, O.XORWOW, 300 + c, 100, k=k, n_strips=strips)
+        _, acc, nm = O.ising_run_multihit(L, beta, O.XORWOW, 700 + c, rounds, k=k, n_strips=strips,
+                                          measure_every=1, spins=s0)
+        mE, mE2 = acc[0] / nm, acc[1] / nm
+        e_c.append(-mE / N)
+        cv_c.append(beta * beta * (mE2 - mE * mE) / N)
+    e_ex, cv_ex = X.exact_e_cv(L, beta)
+    e_est, e_err = np.mean(e_c), np.std(e_c, ddof=1) / np.sqrt(chunks)
+    cv_est, cv_err = np.mean(cv_c), np.std(cv_c, ddof=1) / np.sqrt(chunks)
+    assert abs(e_est - e_ex) < 4.5 * e_err, (e_est, e_ex, e_err)
+    assert abs(cv_est - cv_ex) < 4.5 * cv_err + 0.03 * cv_ex, (cv_est, cv_ex, cv_err)
