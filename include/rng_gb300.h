@@ -210,6 +210,26 @@ int ising_create(ising_t *out, uint32_t L, double beta, int layout, int rng_kind
  * next ising_observables / ising_get_spins. */
 int ising_sweep(ising_t h, uint64_t n_sweeps, uint32_t measure_every, void *cuda_stream);
 
+/* n_rounds rounds of the multi-hit (double checkerboard) update, Sec. 2
+ * (the t_up^{k=100} column of Table 1: k hits per tile load).  The rows
+ * are cut into n_strips equal strips (n_strips even, dividing L); strip b
+ * has coarse colour b & 1.  A round is two phases C = 0, 1: in phase C the
+ * strips of coarse colour C each take k full checkerboard sweeps of their
+ * own rows (colour 0 then colour 1, k times) while the other strips stay
+ * fixed, so a strip's updates see its neighbours' boundary rows as they
+ * were at the start of the phase.  Each stream draws its G numbers per
+ * half-sweep in the same order as in ising_sweep, so a round advances every
+ * stream by 2kG draws; k = 1 is a legal Markov chain with a different
+ * update order than ising_sweep, and no round equals a plain sweep.
+ * measure_every counts rounds (E, M measured after the round).  Requires
+ * one lattice per handle (else RNG_EUNSUPPORTED), 1 <= k <= 65536, each
+ * strip's streams a multiple of 32 (whole warps), L % 8 == 0 for
+ * ISING_INT8, two strips per block fitting in shared memory and n_strips/2
+ * co-resident blocks (else RNG_EINVAL / RNG_EUNSUPPORTED).  Asynchronous
+ * like ising_sweep. */
+int ising_sweep_multihit(ising_t h, uint64_t n_rounds, uint32_t k, uint32_t n_strips, uint32_t measure_every,
+                         void *cuda_stream);
+
 /* Same result as ising_sweep, one kernel launch per half-sweep with the
  * generator state and lattice in global memory (the baseline the
  * persistent kernel is compared with). */

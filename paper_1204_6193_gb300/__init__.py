@@ -59,6 +59,7 @@ _SIGS = {
     "ising_destroy": [_p],
     "ising_sweep": [_p, _u64, _u32, _p],
     "ising_sweep_plain": [_p, _u64, _u32, _p],
+    "ising_sweep_multihit": [_p, _u64, _u32, _u32, _u32, _p],
     "ising_observables": [_p, _p, _p, _p, _p],
     "ising_get_spins": [_p, _p],
     "ising_set_spins": [_p, _p],
@@ -198,6 +199,11 @@ def ising_sweep(h: int, n_sweeps: int, measure_every: int = 0, stream=None) -> N
 
 def ising_sweep_plain(h: int, n_sweeps: int, measure_every: int = 0, stream=None) -> None:
     _call("ising_sweep_plain", h, n_sweeps, measure_every, _stream(stream))
+
+
+def ising_sweep_multihit(h: int, n_rounds: int, k: int, n_strips: int, measure_every: int = 0,
+                         stream=None) -> None:
+    _call("ising_sweep_multihit", h, n_rounds, k, n_strips, measure_every, _stream(stream))
 
 
 def _obs(name, h, *idx):

@@ -20,6 +20,7 @@ int launch_persist(int, int, const PersistArgs &, unsigned, unsigned, size_t, cu
 namespace {
 
 constexpr uint64_t kChunkSweeps = 4096;  // sweeps per persistent launch
+constexpr uint32_t kMaxHits = 65536;      // multi-hit sweeps per strip phase
 constexpr size_t kSmemCap = 200 * 1024;  // dynamic shared memory per block we plan for
 
 int dispatch_half(int kind, const LatDev &lat, int c, cudaStream_t s)
@@ -215,6 +216,8 @@ struct Plan {
     uint32_t *d_cta = nullptr;
     uint8_t *d_halo = nullptr;
     uint32_t *d_flags = nullptr;
+    // per strip: 2 slots x 2 rows x 2 colours of (tag, data) words
+    size_t halo_bytes() const { return static_cast<size_t>(nsegs) * 8 * halo_row_bytes; }
 };
 
 struct ising_s {
@@ -226,6 +229,8 @@ struct ising_s {
     int *d_err = nullptr;
     std::vector<Plan> plans;
     bool planned = false;
+    std::vector<Plan> mh_plans;  // the multi-hit plan (one lattice) and its strip count
+    uint32_t mh_strips = 0;
     unsigned cfg_threads = 0;    // 0: heuristic
     int cfg_ctas_per_sm = 0;     // 0: heuristic
     uint32_t cfg_min_sites = 0;  // 0: heuristic (1024)
@@ -342,14 +347,17 @@ int upload_lats(ising_t h)
 
 void free_plans(ising_t h)
 {
-    for (auto &p : h->plans) {
-        dfree(p.d_segs, h->stream);
-        dfree(p.d_cta, h->stream);
-        dfree(p.d_halo, h->stream);
-        dfree(p.d_flags, h->stream);
-    }
+    for (auto *v : {&h->plans, &h->mh_plans})
+        for (auto &p : *v) {
+            dfree(p.d_segs, h->stream);
+            dfree(p.d_cta, h->stream);
+            dfree(p.d_halo, h->stream);
+            dfree(p.d_flags, h->stream);
+        }
     h->plans.clear();
+    h->mh_plans.clear();
     h->planned = false;
+    h->mh_strips = 0;
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
     h->gexec = nullptr;
@@ -375,6 +383,9 @@ size_t seg_smem(const IsingLat &t, uint32_t rows)
 struct SegPlan {
     uint32_t lat, y0, y1;
 };
+
+int materialize_plan(ising_t h, int kind, int layout, const std::vector<std::vector<SegPlan>> &blocks, Plan &P,
+                     bool multihit);
 
 // Plans one kind group: splits big lattices into aligned row strips, packs
 // small whole lattices into shared blocks, and picks the block shape.
@@ -440,8 +451,15 @@ int build_plan(ising_t h, int kind, int layout, const std::vector<uint32_t> &ids
         }
     }
     for (auto &b : wb) blocks.push_back(b);
+    return materialize_plan(h, kind, layout, blocks, P, false);
+}
 
-    // segments, neighbour links and per-block shared memory
+// Segments, ring links, block shape and device buffers of a list of blocks
+// (each a list of strips).  Strips of one lattice are linked into a ring in
+// list order; a strip's coarse colour is its position in that ring mod 2.
+int materialize_plan(ising_t h, int kind, int layout, const std::vector<std::vector<SegPlan>> &blocks, Plan &P,
+                     bool multihit)
+{
     std::vector<SegDev> segs;
     std::vector<uint32_t> cta(1, 0);
     std::vector<std::vector<uint32_t>> lat_strips(h->lats.size());
@@ -455,6 +473,7 @@ int build_plan(ising_t h, int kind, int layout, const std::vector<uint32_t> &ids
             const IsingLat &t = h->lats[sp.lat];
             SegDev d;
             d.lat = sp.lat;
+            d.coarse = static_cast<uint32_t>(lat_strips[sp.lat].size() & 1);
             d.y0 = sp.y0;
             d.y1 = sp.y1;
             d.smem_off = static_cast<uint32_t>(off);
@@ -490,6 +509,12 @@ int build_plan(ising_t h, int kind, int layout, const std::vector<uint32_t> &ids
         threads = 512;
         spt = std::min<uint64_t>(4, (max_streams + threads - 1) / threads);
     }
+    if (multihit && !h->cfg_threads && max_streams <= 2048) {
+        // one stream of each coarse colour per thread: every thread works
+        // in both phases (the multi-hit kernel runs two slots at up to 1024)
+        threads = static_cast<unsigned>(std::max<uint64_t>(32, max_streams / 2));
+        spt = 2;
+    }
     P.kind = kind;
     P.layout = layout;
     P.smax = spt <= 1 ? 1 : (spt <= 2 ? 2 : 4);
@@ -500,8 +525,7 @@ int build_plan(ising_t h, int kind, int layout, const std::vector<uint32_t> &ids
     P.halo_row_bytes = (2 * halo_rb + 15) / 16 * 16;  // one 64-bit (tag, data) word per 32 data bits
     RNGX_CHECK(dalloc(reinterpret_cast<void **>(&P.d_segs), segs.size() * sizeof(SegDev), h->stream));
     RNGX_CHECK(dalloc(reinterpret_cast<void **>(&P.d_cta), cta.size() * sizeof(uint32_t), h->stream));
-    RNGX_CHECK(dalloc(reinterpret_cast<void **>(&P.d_halo), static_cast<size_t>(P.nsegs) * 4 * P.halo_row_bytes,
-                      h->stream));
+    RNGX_CHECK(dalloc(reinterpret_cast<void **>(&P.d_halo), P.halo_bytes(), h->stream));
     RNGX_CHECK(dalloc(reinterpret_cast<void **>(&P.d_flags), P.nsegs * sizeof(uint32_t), h->stream));
     RNGX_CHECK_CUDA(cudaStreamSynchronize(h->stream));
     RNGX_CHECK_CUDA(cudaMemcpy(P.d_segs, segs.data(), segs.size() * sizeof(SegDev), cudaMemcpyHostToDevice));
@@ -509,12 +533,40 @@ int build_plan(ising_t h, int kind, int layout, const std::vector<uint32_t> &ids
     int max_blocks = 0;
     PersistArgs dummy;
     memset(&dummy, 0, sizeof(dummy));
+    dummy.k_hits = multihit ? 1 : 0;  // selects the kernel whose occupancy is asked
     RNGX_CHECK(dispatch_persist(kind, layout, P.smax, dummy, 0, P.threads, P.smem, h->stream, &max_blocks));
     if (static_cast<int>(P.nblocks) > max_blocks) {
         set_error("Ising: plan needs %u co-resident blocks, device holds %d", P.nblocks, max_blocks);
         return RNG_EUNSUPPORTED;
     }
     return RNG_OK;
+}
+
+// The multi-hit plan of a single lattice: n_strips equal row strips, block
+// m holding strips 2m (coarse colour 0) and 2m + 1 (coarse colour 1), so
+// that every thread has streams in both and works in both phases.
+int build_multihit_plan(ising_t h, uint32_t n_strips, Plan &P)
+{
+    const IsingLat &t = h->lats[0];
+    const uint32_t R = t.L / n_strips;
+    const uint64_t per_strip = static_cast<uint64_t>(R) * (t.L / 2 / t.G);
+    if (per_strip % 32) {
+        set_error("Ising multi-hit: a strip's %llu streams must be whole warps (a multiple of 32)",
+                  static_cast<unsigned long long>(per_strip));
+        return RNG_EINVAL;
+    }
+    if (t.layout == ISING_INT8 && t.L % 8) {
+        set_error("Ising multi-hit: the int8 layout exchanges rows as 32-bit words and needs L %% 8 == 0");
+        return RNG_EINVAL;
+    }
+    if (2 * seg_smem(t, R) > kSmemCap) {
+        set_error("Ising multi-hit: two strips of %u rows exceed the shared memory of a block", R);
+        return RNG_EUNSUPPORTED;
+    }
+    std::vector<std::vector<SegPlan>> blocks;
+    for (uint32_t m = 0; m < n_strips / 2; m++)
+        blocks.push_back({{0, 2 * m * R, (2 * m + 1) * R}, {0, (2 * m + 1) * R, (2 * m + 2) * R}});
+    return materialize_plan(h, t.kind, t.layout, blocks, P, true);
 }
 
 int ensure_plan(ising_t h)
@@ -556,18 +608,25 @@ int ensure_meas(ising_t h, uint64_t need)
     return RNG_OK;
 }
 
-// Enqueues n_sweeps persistent sweeps of every lattice (no host sync).
-int enqueue_persistent(ising_t h, uint64_t n_sweeps, uint32_t measure_every, cudaStream_t s)
+// Sweeps (k_hits = 0) or multi-hit rounds (k_hits = k) per persistent launch.
+uint64_t chunk_units(uint32_t k_hits) { return k_hits ? std::max<uint64_t>(1, kChunkSweeps / k_hits) : kChunkSweeps; }
+
+// Enqueues n_units persistent sweeps (k_hits = 0) or multi-hit rounds of k
+// sweeps per strip phase (k_hits = k) of every lattice (no host sync).
+int enqueue_persistent(ising_t h, std::vector<Plan> &plans, uint64_t n_units, uint32_t k_hits,
+                       uint32_t measure_every, cudaStream_t s)
 {
+    const uint64_t per_launch = chunk_units(k_hits);
+    const uint64_t sweeps_per_unit = k_hits ? k_hits : 1;
     uint64_t done = 0;
-    while (done < n_sweeps) {
-        const uint64_t chunk = std::min(kChunkSweeps, n_sweeps - done);
+    while (done < n_units) {
+        const uint64_t chunk = std::min(per_launch, n_units - done);
         const uint64_t n_meas = measure_every ? (chunk + (done % measure_every)) / measure_every : 0;
         for (auto &t : h->lats)
             if (n_meas) RNGX_CHECK_CUDA(cudaMemsetAsync(t.meas, 0, 2 * n_meas * sizeof(int64_t), s));
-        for (auto &P : h->plans) {
-            // halo words carry half-sweep tags that restart at every launch
-            RNGX_CHECK_CUDA(cudaMemsetAsync(P.d_halo, 0, static_cast<size_t>(P.nsegs) * 4 * P.halo_row_bytes, s));
+        for (auto &P : plans) {
+            // halo words carry phase tags that restart at every launch
+            RNGX_CHECK_CUDA(cudaMemsetAsync(P.d_halo, 0, P.halo_bytes(), s));
             PersistArgs a;
             a.lats = h->d_lats;
             a.segs = P.d_segs;
@@ -581,16 +640,22 @@ int enqueue_persistent(ising_t h, uint64_t n_sweeps, uint32_t measure_every, cud
             a.sweep0 = done;
             a.mute_seg = h->mute_seg;
             a.wait_budget_ns = h->wait_budget_ns;
+            a.k_hits = k_hits;
             RNGX_CHECK(dispatch_persist(P.kind, P.layout, P.smax, a, P.nblocks, P.threads, P.smem, s, nullptr));
         }
         for (auto &t : h->lats) {
             if (n_meas) k_meas_finalize<<<1, 256, 0, s>>>(t.meas, static_cast<uint32_t>(n_meas), t.acc);
-            k_add_u64<<<1, 1, 0, s>>>(t.pos_dev, 2 * t.G * chunk);
+            k_add_u64<<<1, 1, 0, s>>>(t.pos_dev, 2 * t.G * sweeps_per_unit * chunk);
         }
         RNGX_CHECK_CUDA(cudaGetLastError());
         done += chunk;
     }
     return RNG_OK;
+}
+
+int enqueue_persistent(ising_t h, uint64_t n_sweeps, uint32_t measure_every, cudaStream_t s)
+{
+    return enqueue_persistent(h, h->plans, n_sweeps, 0, measure_every, s);
 }
 
 void advance_host_pos(ising_t h, uint64_t n_sweeps)
@@ -754,6 +819,48 @@ int ising_sweep(ising_t h, uint64_t n_sweeps, uint32_t measure_every, void *cuda
     for (auto &t : h->lats) k_set_u64<<<1, 1, 0, s>>>(t.pos_dev, t.rng->g.pos);
     RNGX_CHECK(enqueue_persistent(h, n_sweeps, measure_every, s));
     advance_host_pos(h, n_sweeps);
+    return RNG_OK;
+}
+
+int ising_sweep_multihit(ising_t h, uint64_t n_rounds, uint32_t k, uint32_t n_strips, uint32_t measure_every,
+                         void *cuda_stream)
+{
+    RNGX_CHECK(valid(h));
+    if (h->lats.size() != 1) {
+        set_error("Ising multi-hit: one lattice per handle (batch handles sweep with ising_batch_sweep)");
+        return RNG_EUNSUPPORTED;
+    }
+    const IsingLat &t = h->lats[0];
+    if (k == 0 || k > kMaxHits || n_strips < 2 || n_strips % 2 || t.L % n_strips) {
+        set_error("Ising multi-hit: need 1 <= k <= %u and an even strip count >= 2 that divides L=%u (got k=%u, "
+                  "n_strips=%u)",
+                  kMaxHits, t.L, k, n_strips);
+        return RNG_EINVAL;
+    }
+    if (n_rounds == 0) return RNG_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (h->mh_strips != n_strips) {
+        for (auto &p : h->mh_plans) {
+            dfree(p.d_segs, h->stream);
+            dfree(p.d_cta, h->stream);
+            dfree(p.d_halo, h->stream);
+            dfree(p.d_flags, h->stream);
+        }
+        h->mh_plans.clear();
+        h->mh_strips = 0;
+        Plan P;
+        const int st = build_multihit_plan(h, n_strips, P);
+        h->mh_plans.push_back(P);
+        if (st != RNG_OK) {
+            free_plans(h);
+            return st;
+        }
+        h->mh_strips = n_strips;
+    }
+    RNGX_CHECK(ensure_meas(h, measure_every ? std::max<uint64_t>(1, chunk_units(k) / measure_every + 1) : 1));
+    for (auto &l : h->lats) k_set_u64<<<1, 1, 0, s>>>(l.pos_dev, l.rng->g.pos);
+    RNGX_CHECK(enqueue_persistent(h, h->mh_plans, n_rounds, k, measure_every, s));
+    advance_host_pos(h, n_rounds * k);
     return RNG_OK;
 }
 

@@ -32,6 +32,7 @@ struct LatDev {
 // A row strip [y0, y1) of one lattice held by one thread block.
 struct SegDev {
     uint32_t lat;                  // lattice index
+    uint32_t coarse;               // strip index parity (multi-hit phases)
     uint32_t y0, y1;
     uint32_t smem_off;             // bytes into the block's dynamic shared memory
     int32_t up, down;              // segments holding rows y0-1 and y1; -1: this one (whole lattice)

@@ -33,10 +33,11 @@ struct PersistArgs {
     uint32_t measure_every;    // measure after sweeps sweep0+t+1 that are multiples
     int32_t mute_seg;          // test hook: this segment never publishes (-1: none)
     uint64_t wait_budget_ns;   // limit of one neighbour wait
+    uint32_t k_hits;           // 0: exact checkerboard; k > 0: multi-hit rounds of k sweeps per strip phase
 };
 
 struct SegLocal {              // per-segment constants held in shared memory
-    uint32_t L, half, W, G, y0, R, off, lat;
+    uint32_t L, half, W, G, y0, R, off, lat, coarse;
     int32_t up, down, gid;
     uint64_t s0, prefix, T4, T8;
     uint64_t n_valid, n_inst;  // streams with sites; generator instances
@@ -271,19 +272,31 @@ __device__ __forceinline__ bool slot_on_boundary(const SegLocal *S, const Stream
     return sl.in && (sl.row == sg.y0 || sl.row + 1 == sg.y0 + sg.R);
 }
 
-// Updates the warps that hold a first or last row of their strip
-// (boundary = true) or the other warps (boundary = false).  A warp is
-// classified as a whole, so warp-wide steps see all 32 lanes.
+// Which warps a pass updates: those holding a first or last row of their
+// strip, the others, or all warps of the strips of one coarse colour
+// (multi-hit phases).  A warp is classified as a whole, so warp-wide steps
+// see all 32 lanes.
+enum { SEL_BOUNDARY = 0, SEL_INTERIOR = 1, SEL_COARSE0 = 2, SEL_COARSE1 = 3 };
+
+__device__ __forceinline__ bool warp_selected(const SegLocal *S, const StreamSlot &sl, int sel)
+{
+    if (sel >= SEL_COARSE0) return S[sl.seg].coarse == static_cast<uint32_t>(sel - SEL_COARSE0);
+    return __any_sync(0xffffffffu, slot_on_boundary(S, sl)) == (sel == SEL_BOUNDARY);
+}
+
+// Updates the colour-c sites of the selected warps.  pos_off is the number
+// of draws every updated stream made earlier in this launch (streamed
+// states reload their position from it).
 template <int KIND, int LAYOUT, int SMAX>
 __device__ __forceinline__ void update_pass(uint8_t *smem, const SegLocal *S, uint32_t nseg, uint64_t prefix_end,
-                                            const PersistArgs &a, bool resident, Gen<KIND> (&gen)[SMAX],
-                                            const StreamSlot (&slot)[SMAX], uint64_t t, int c, int lane, bool boundary)
+                                            bool resident, Gen<KIND> (&gen)[SMAX], const StreamSlot (&slot)[SMAX],
+                                            uint64_t pos_off, int c, int lane, int sel)
 {
     if (resident) {
 #pragma unroll
         for (int k = 0; k < SMAX; k++) {
             if (!__any_sync(0xffffffffu, slot[k].in)) continue;
-            if (__any_sync(0xffffffffu, slot_on_boundary(S, slot[k])) != boundary) continue;
+            if (!warp_selected(S, slot[k], sel)) continue;
             update_slot<KIND, LAYOUT>(smem, S[slot[k].seg], slot[k], gen[k], c, lane);
         }
         return;
@@ -292,6 +305,7 @@ __device__ __forceinline__ void update_pass(uint8_t *smem, const SegLocal *S, ui
     // strips' stream counts are multiples of 32, so warps never straddle two)
     for (uint32_t j = 0; j < nseg; j++) {
         const SegLocal &sg = S[j];
+        if (sel >= SEL_COARSE0 && sg.coarse != static_cast<uint32_t>(sel - SEL_COARSE0)) continue;
         const uint64_t count = (j + 1 < nseg ? S[j + 1].prefix : prefix_end) - sg.prefix;
         for (uint64_t base = 0; base < count; base += blockDim.x) {
             const uint64_t f = base + threadIdx.x;
@@ -304,9 +318,9 @@ __device__ __forceinline__ void update_pass(uint8_t *smem, const SegLocal *S, ui
             sl.row = q0 / sg.half;
             sl.xh0 = q0 - sl.row * sg.half;
             if (!__any_sync(0xffffffffu, sl.in)) continue;
-            if (__any_sync(0xffffffffu, slot_on_boundary(S, sl)) != boundary) continue;
+            if (!warp_selected(S, sl, sel)) continue;
             DevParams rp = sg.rng;
-            rp.pos += (2 * t + c) * sg.G;
+            rp.pos += pos_off;
             Gen<KIND> g;
             g.load(rp, sl.s < sg.n_inst ? sl.s : sg.n_inst - 1);
             update_slot<KIND, LAYOUT>(smem, sg, sl, g, c, lane);
@@ -315,8 +329,86 @@ __device__ __forceinline__ void update_pass(uint8_t *smem, const SegLocal *S, ui
     }
 }
 
-template <int KIND, int LAYOUT, int SMAX>
-__global__ void __launch_bounds__(SMAX >= 2 ? 512 : 1024) k_ising_persist(PersistArgs a)
+// Halo buffer: per strip, 2 slots x 2 rows (first, last) x 2 colours.
+__device__ __forceinline__ uint64_t *halo_row(const PersistArgs &a, int gid, uint32_t slot, int row, int colour)
+{
+    return reinterpret_cast<uint64_t *>(
+        a.halo + ((((static_cast<size_t>(gid) * 2 + slot) * 2 + row) * 2 + colour)) * a.halo_row_bytes);
+}
+
+// Publishes the first and last rows of colour c of strip sg as 64-bit
+// (tag, 32 data bits) words: one relaxed atomic store each, no fence.
+template <int LAYOUT>
+__device__ __forceinline__ void publish_rows(uint8_t *smem, const SegLocal &sg, const PersistArgs &a, uint32_t slot,
+                                             uint32_t tag, int c)
+{
+    if (sg.gid == a.mute_seg) return;  // test hook: a strip that never publishes
+    const uint32_t words = row_bytes<LAYOUT>(sg) / 4;
+    const uint32_t *row0 = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, c, 0));
+    const uint32_t *rowl = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, c, sg.R - 1));
+    uint64_t *d0 = halo_row(a, sg.gid, slot, 0, c), *d1 = halo_row(a, sg.gid, slot, 1, c);
+    const uint64_t t = static_cast<uint64_t>(tag) << 32;
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) {
+        st_relaxed_u64(d0 + i, t | row0[i]);
+        st_relaxed_u64(d1 + i, t | rowl[i]);
+    }
+}
+
+// Polls the neighbours' rows of colour c into strip sg's halo rows (the up
+// neighbour's last row above, the down neighbour's first row below) until
+// their words carry `tag`; the wait is bounded by two clocks (the global ns
+// timer and the SM cycle counter, at most 4 cycles per ns of budget).
+template <int LAYOUT>
+__device__ __forceinline__ bool poll_rows(uint8_t *smem, const SegLocal &sg, const PersistArgs &a, uint32_t slot,
+                                          uint32_t tag, int c, uint64_t t0, long long c0)
+{
+    const uint32_t words = row_bytes<LAYOUT>(sg) / 4;
+    const uint64_t *up_last = halo_row(a, sg.up, slot, 1, c), *dn_first = halo_row(a, sg.down, slot, 0, c);
+    uint32_t *top = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, -1));
+    uint32_t *bot = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, sg.R));
+    for (uint32_t i = threadIdx.x; i < 2 * words; i += blockDim.x) {
+        const uint64_t *src = i < words ? up_last + i : dn_first + (i - words);
+        uint64_t v;
+        while (((v = ld_relaxed_u64(src)) >> 32) != tag) {
+            __nanosleep(20);  // light backoff: many blocks poll the L2 at once
+            if (global_ns() - t0 > a.wait_budget_ns || static_cast<uint64_t>(clock64() - c0) > 4 * a.wait_budget_ns ||
+                ld_acquire(reinterpret_cast<const uint32_t *>(a.err)) != 0) {
+                atomicCAS(a.err, 0, RNG_ETIMEOUT);
+                return false;
+            }
+        }
+        (i < words ? top[i] : bot[i - words]) = static_cast<uint32_t>(v);
+    }
+    return true;
+}
+
+template <int LAYOUT>
+__device__ void measure_strips(uint8_t *smem, const SegLocal *S, uint32_t nseg, const PersistArgs &a,
+                               uint64_t meas_idx, long long *red)
+{
+    for (uint32_t j = 0; j < nseg; j++) {
+        long long E, M;
+        strip_energy<LAYOUT>(smem, S[j], E, M);
+        const long long Es = block_sum(E, red);
+        __syncthreads();
+        const long long Ms = block_sum(M, red);
+        if (threadIdx.x == 0) {
+            int64_t *meas = a.lats[S[j].lat].meas;
+            atomicAdd(reinterpret_cast<unsigned long long *>(meas + 2 * meas_idx), static_cast<unsigned long long>(Es));
+            atomicAdd(reinterpret_cast<unsigned long long *>(meas + 2 * meas_idx + 1),
+                      static_cast<unsigned long long>(Ms));
+        }
+        __syncthreads();
+    }
+}
+
+// MH selects the multi-hit round loop (a.k_hits > 0) at compile time, so
+// that the exact-checkerboard kernel keeps its own register allocation.
+// Launch bounds: the exact-checkerboard kernel runs multi-slot shapes with
+// at most 512 threads; the multi-hit kernel also runs two slots (one stream
+// in each coarse colour) with up to 1024 threads.
+template <int KIND, int LAYOUT, int SMAX, bool MH>
+__global__ void __launch_bounds__(SMAX >= (MH ? 4 : 2) ? 512 : 1024) k_ising_persist(PersistArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ SegLocal S[kPersistMaxSegs];
@@ -336,6 +428,7 @@ __global__ void __launch_bounds__(SMAX >= 2 ? 512 : 1024) k_ising_persist(Persis
         s.R = d.y1 - d.y0;
         s.off = d.smem_off;
         s.lat = d.lat;
+        s.coarse = d.coarse;
         s.up = d.up;
         s.down = d.down;
         s.gid = static_cast<int32_t>(sb + threadIdx.x);
@@ -382,100 +475,105 @@ __global__ void __launch_bounds__(SMAX >= 2 ? 512 : 1024) k_ising_persist(Persis
 
     uint64_t meas_idx = 0;
     const int lane = threadIdx.x & 31;
-    for (uint64_t t = 0; t < a.n_sweeps; t++) {
-        for (int c = 0; c < 2; c++) {
-            // ---- warps that hold a strip's first or last row go first ...
-            const uint32_t h = static_cast<uint32_t>(2 * t + c);
-            update_pass<KIND, LAYOUT, SMAX>(smem, S, nseg, prefix_end, a, resident, gen, slot, t, c, lane, true);
-            __syncthreads();
-            // ---- ... their rows are published (a whole lattice copies them
-            // into its own halo rows) ...
-            bool any_split = false;
-            for (uint32_t j = 0; j < nseg; j++) {
-                const SegLocal &sg = S[j];
-                const uint32_t rb = row_bytes<LAYOUT>(sg);
-                if (sg.up < 0) {
-                    // byte copies: an int8 row of L/2 bytes need not be word aligned
-                    uint8_t *top = plane_row<LAYOUT>(smem, sg, c, -1), *bot = plane_row<LAYOUT>(smem, sg, c, sg.R);
-                    const uint8_t *last = plane_row<LAYOUT>(smem, sg, c, sg.R - 1), *first = plane_row<LAYOUT>(smem, sg, c, 0);
-                    for (uint32_t i = threadIdx.x; i < rb; i += blockDim.x) {
-                        top[i] = last[i];
-                        bot[i] = first[i];
-                    }
-                } else {
-                    any_split = true;
-                    if (sg.gid == a.mute_seg) continue;  // test hook: a strip that never publishes
-                    // each 64-bit word carries (half-sweep number + 1, 32 bits of
-                    // the row): one relaxed atomic store, no fence, no flag
-                    uint64_t *dst = reinterpret_cast<uint64_t *>(a.halo + (static_cast<size_t>(sg.gid) * 4 + (h & 1) * 2) *
-                                                                              a.halo_row_bytes);
-                    const uint32_t *row0 = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, c, 0));
-                    const uint32_t *rowl = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, c, sg.R - 1));
-                    const uint64_t tag = static_cast<uint64_t>(h + 1) << 32;
-                    for (uint32_t i = threadIdx.x; i < rb / 4; i += blockDim.x) {
-                        st_relaxed_u64(dst + i, tag | row0[i]);
-                        st_relaxed_u64(dst + a.halo_row_bytes / 8 + i, tag | rowl[i]);
+    if constexpr (!MH) {
+        // ---------------- exact checkerboard: all strips, every half-sweep
+        for (uint64_t t = 0; t < a.n_sweeps; t++) {
+            for (int c = 0; c < 2; c++) {
+                const uint32_t h = static_cast<uint32_t>(2 * t + c);
+                const uint64_t pos_off = (2 * t + c) * static_cast<uint64_t>(S[0].G);
+                // warps that hold a strip's first or last row go first ...
+                update_pass<KIND, LAYOUT, SMAX>(smem, S, nseg, prefix_end, resident, gen, slot, pos_off, c, lane,
+                                                SEL_BOUNDARY);
+                __syncthreads();
+                // ... their rows are published (a whole lattice copies them into
+                // its own halo rows) ...
+                bool any_split = false;
+                for (uint32_t j = 0; j < nseg; j++) {
+                    const SegLocal &sg = S[j];
+                    if (sg.up < 0) {
+                        // byte copies: an int8 row of L/2 bytes need not be word aligned
+                        const uint32_t rb = row_bytes<LAYOUT>(sg);
+                        uint8_t *top = plane_row<LAYOUT>(smem, sg, c, -1), *bot = plane_row<LAYOUT>(smem, sg, c, sg.R);
+                        const uint8_t *last = plane_row<LAYOUT>(smem, sg, c, sg.R - 1);
+                        const uint8_t *first = plane_row<LAYOUT>(smem, sg, c, 0);
+                        for (uint32_t i = threadIdx.x; i < rb; i += blockDim.x) {
+                            top[i] = last[i];
+                            bot[i] = first[i];
+                        }
+                    } else {
+                        any_split = true;
+                        publish_rows<LAYOUT>(smem, sg, a, h & 1, h + 1, c);
                     }
                 }
+                // ... the interior rows are updated while those words travel ...
+                update_pass<KIND, LAYOUT, SMAX>(smem, S, nseg, prefix_end, resident, gen, slot, pos_off, c, lane,
+                                                SEL_INTERIOR);
+                // ... and the neighbours' rows are polled into the halo rows
+                if (any_split) {
+                    const uint64_t t0 = global_ns();
+                    const long long c0 = clock64();
+                    bool ok = true;
+                    for (uint32_t j = 0; j < nseg && ok; j++)
+                        if (S[j].up >= 0) ok = poll_rows<LAYOUT>(smem, S[j], a, h & 1, h + 1, c, t0, c0);
+                    if (!ok) s_abort = 1;
+                }
+                __syncthreads();
+                if (s_abort) goto done;
             }
-            // ---- ... the interior rows are updated while those words travel ...
-            update_pass<KIND, LAYOUT, SMAX>(smem, S, nseg, prefix_end, a, resident, gen, slot, t, c, lane, false);
-            // ---- ... and the neighbours' rows are polled into the halo rows
-            if (any_split) {
+            if (a.measure_every && (a.sweep0 + t + 1) % a.measure_every == 0) {
+                measure_strips<LAYOUT>(smem, S, nseg, a, meas_idx, red);
+                meas_idx++;
+            }
+        }
+    } else {
+        // ---------------- multi-hit rounds (double checkerboard): the strips
+        // of coarse colour C take k sweeps of their own rows while the other
+        // strips stay fixed; then they publish both colours of their first
+        // and last rows, which the other strips poll before their phase
+        const uint32_t k = a.k_hits;
+        for (uint64_t t = 0; t < a.n_sweeps; t++) {
+            for (int C = 0; C < 2; C++) {
+                const uint32_t ph = static_cast<uint32_t>(2 * t + C);
+                if (ph > 0) {  // the other coarse colour published at the end of phase ph - 1
+                    const uint64_t t0 = global_ns();
+                    const long long c0 = clock64();
+                    bool ok = true;
+                    for (uint32_t j = 0; j < nseg && ok; j++)
+                        if (S[j].coarse == static_cast<uint32_t>(C))
+                            for (int cc = 0; cc < 2 && ok; cc++)
+                                ok = poll_rows<LAYOUT>(smem, S[j], a, ((ph - 1) >> 1) & 1, ph, cc, t0, c0);
+                    if (!ok) s_abort = 1;
+                    __syncthreads();
+                    if (s_abort) goto done;
+                }
+                for (uint32_t hit = 0; hit < k; hit++) {
+                    for (int c = 0; c < 2; c++) {
+                        const uint64_t pos_off = (2 * (t * k + hit) + c) * static_cast<uint64_t>(S[0].G);
+                        update_pass<KIND, LAYOUT, SMAX>(smem, S, nseg, prefix_end, resident, gen, slot, pos_off, c,
+                                                        lane, SEL_COARSE0 + C);
+                        __syncthreads();
+                    }
+                }
+                for (uint32_t j = 0; j < nseg; j++)
+                    if (S[j].coarse == static_cast<uint32_t>(C))
+                        for (int cc = 0; cc < 2; cc++) publish_rows<LAYOUT>(smem, S[j], a, (ph >> 1) & 1, ph + 1, cc);
+            }
+            if (a.measure_every && (a.sweep0 + t + 1) % a.measure_every == 0) {
+                // the coarse-0 strips first take the rows the coarse-1 strips just published
+                const uint32_t ph = static_cast<uint32_t>(2 * t + 1);
                 const uint64_t t0 = global_ns();
                 const long long c0 = clock64();
-                bool failed = false;
-                for (uint32_t j = 0; j < nseg && !failed; j++) {
-                    const SegLocal &sg = S[j];
-                    if (sg.up < 0) continue;
-                    const uint32_t words = row_bytes<LAYOUT>(sg) / 4;
-                    const uint64_t *up_bottom = reinterpret_cast<const uint64_t *>(
-                        a.halo + (static_cast<size_t>(sg.up) * 4 + (h & 1) * 2 + 1) * a.halo_row_bytes);
-                    const uint64_t *dn_top = reinterpret_cast<const uint64_t *>(
-                        a.halo + (static_cast<size_t>(sg.down) * 4 + (h & 1) * 2) * a.halo_row_bytes);
-                    uint32_t *top = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, -1));
-                    uint32_t *bot = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, sg.R));
-                    for (uint32_t i = threadIdx.x; i < 2 * words && !failed; i += blockDim.x) {
-                        const uint64_t *src = i < words ? up_bottom + i : dn_top + (i - words);
-                        uint64_t v;
-                        // bounded by two clocks: the global ns timer and the SM
-                        // cycle counter (at most 4 cycles per ns of budget)
-                        while (((v = ld_relaxed_u64(src)) >> 32) != h + 1) {
-                            __nanosleep(20);  // light backoff: many blocks poll the L2 at once
-                            if (global_ns() - t0 > a.wait_budget_ns ||
-                                static_cast<uint64_t>(clock64() - c0) > 4 * a.wait_budget_ns ||
-                                ld_acquire(reinterpret_cast<uint32_t *>(a.err)) != 0) {
-                                atomicCAS(a.err, 0, RNG_ETIMEOUT);
-                                failed = true;
-                                break;
-                            }
-                        }
-                        if (!failed) (i < words ? top[i] : bot[i - words]) = static_cast<uint32_t>(v);
-                    }
-                }
-                if (failed) s_abort = 1;
-            }
-            __syncthreads();
-            if (s_abort) goto done;
-        }
-        // ---- measurement after every measure_every-th sweep of this launch
-        if (a.measure_every && (a.sweep0 + t + 1) % a.measure_every == 0) {
-            for (uint32_t j = 0; j < nseg; j++) {
-                long long E, M;
-                strip_energy<LAYOUT>(smem, S[j], E, M);
-                const long long Es = block_sum(E, red);
+                bool ok = true;
+                for (uint32_t j = 0; j < nseg && ok; j++)
+                    if (S[j].coarse == 0)
+                        for (int cc = 0; cc < 2 && ok; cc++)
+                            ok = poll_rows<LAYOUT>(smem, S[j], a, (ph >> 1) & 1, ph + 1, cc, t0, c0);
+                if (!ok) s_abort = 1;
                 __syncthreads();
-                const long long Ms = block_sum(M, red);
-                if (threadIdx.x == 0) {
-                    int64_t *meas = a.lats[S[j].lat].meas;
-                    atomicAdd(reinterpret_cast<unsigned long long *>(meas + 2 * meas_idx),
-                              static_cast<unsigned long long>(Es));
-                    atomicAdd(reinterpret_cast<unsigned long long *>(meas + 2 * meas_idx + 1),
-                              static_cast<unsigned long long>(Ms));
-                }
-                __syncthreads();
+                if (s_abort) goto done;
+                measure_strips<LAYOUT>(smem, S, nseg, a, meas_idx, red);
+                meas_idx++;
             }
-            meas_idx++;
         }
     }
 done:
