@@ -38,6 +38,7 @@ struct PersistArgs {
 
 struct SegLocal {              // per-segment constants held in shared memory
     uint32_t L, half, W, G, y0, R, off, lat, coarse;
+    uint32_t pstride;          // plane 1 - plane 0 offset in shared memory
     int32_t up, down, gid;
     uint64_t s0, prefix, T4, T8;
     uint64_t n_valid, n_inst;  // streams with sites; generator instances
@@ -175,26 +176,57 @@ __device__ __forceinline__ long long block_sum(long long v, long long *red)
     return s;  // valid in thread 0
 }
 
-// One stream slot of a thread: which strip, which stream, where its sites are.
+// One stream slot of a thread: which strip, which stream, where its sites
+// are, and the warp-uniform flags the passes select on (all fixed for a
+// launch, so computed once).
 struct StreamSlot {
-    uint32_t seg, row, xh0;  // strip index in the block, global row, first column of its sites
-    bool in, val;            // inside the block's stream range; owns sites
-    uint64_t s;              // stream (instance) index in its lattice
+    uint32_t seg;            // strip index in the block
+    uint32_t xh0;            // first column of its sites
+    uint32_t base;           // shared-memory offset of the slot's row in plane 0
+    uint32_t s;              // stream (instance) index in its lattice (s G < L^2/2 <= 2^31)
+    uint32_t flags;          // SL_* bits
+    __device__ __forceinline__ bool in() const { return flags & 1u; }
+    __device__ __forceinline__ bool val() const { return flags & 2u; }
+};
+enum : uint32_t {
+    SL_IN = 1u,         // inside the block's stream range
+    SL_VAL = 2u,        // owns sites
+    SL_WARP_IN = 4u,    // some lane of the warp is inside
+    SL_WARP_BND = 8u,   // some lane of the warp holds a first or last row of the strip
+    SL_COARSE = 16u,    // the strip's coarse colour is 1 (multi-hit phases)
+    SL_ODD_ROW = 32u,   // the sites' row is odd
 };
 
+template <int LAYOUT>
+__device__ __forceinline__ void finish_slot(const SegLocal &sg, bool in, bool val, StreamSlot &o)
+{
+    const uint32_t q0 = o.s * sg.G;
+    const uint32_t row = q0 / sg.half;
+    o.xh0 = q0 - row * sg.half;
+    o.base = sg.off + (row - sg.y0 + 1) * row_bytes<LAYOUT>(sg);
+    const bool wi = __any_sync(0xffffffffu, in);
+    const bool wb = __any_sync(0xffffffffu, in && (row == sg.y0 || row + 1 == sg.y0 + sg.R));
+    o.flags = (in ? SL_IN : 0u) | (val ? SL_VAL : 0u) | (wi ? SL_WARP_IN : 0u) | (wb ? SL_WARP_BND : 0u) |
+              (sg.coarse ? SL_COARSE : 0u) | ((row & 1u) ? SL_ODD_ROW : 0u);
+}
+
+template <int LAYOUT>
 __device__ __forceinline__ void setup_slot(const SegLocal *S, uint32_t nseg, uint64_t prefix_end, uint64_t f,
                                            StreamSlot &o)
 {
-    o.in = f < prefix_end;
+    const bool in = f < prefix_end;
     uint32_t j = 0;
     while (j + 1 < nseg && f >= S[j + 1].prefix) j++;
     o.seg = j;
-    o.s = S[j].s0 + (o.in ? f - S[j].prefix : 0);
-    o.val = o.in && o.s < S[j].n_valid;
-    // s G < L^2 / 2 <= 2^31: 32-bit arithmetic suffices
-    const uint32_t q0 = static_cast<uint32_t>(o.s) * S[j].G;
-    o.row = q0 / S[j].half;
-    o.xh0 = q0 - o.row * S[j].half;
+    o.s = static_cast<uint32_t>(S[j].s0 + (in ? f - S[j].prefix : 0));
+    finish_slot<LAYOUT>(S[j], in, in && o.s < S[j].n_valid, o);
+}
+
+// Metropolis acceptance of a site whose aligned-neighbour sum is
+// a = s_i sum_nn s_j (dE = 2a): always for a <= 0, else iff r < T[2a].
+__device__ __forceinline__ bool accept_a(int a, uint32_t r, uint64_t T4, uint64_t T8)
+{
+    return a <= 0 || static_cast<uint64_t>(r) < (a == 2 ? T4 : T8);
 }
 
 // Draws G numbers from the slot's generator and updates its G colour-c
@@ -203,38 +235,55 @@ template <int KIND, int LAYOUT>
 __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, const StreamSlot &sl, Gen<KIND> &gen,
                                             int c, int lane)
 {
-    const uint32_t y = sl.row;
-    const int r = static_cast<int>(y - sg.y0);
-    const uint32_t p = (c + y) & 1u;
+    const uint32_t p = (c + ((sl.flags & SL_ODD_ROW) ? 1u : 0u)) & 1u;
+    const uint32_t half = sg.half, G = sg.G;
+    const uint64_t T4 = sg.T4, T8 = sg.T8;
+    const uint32_t pstride = sg.pstride;
+    uint8_t *own_row = smem + sl.base + (c ? pstride : 0u);
+    uint8_t *o_row = smem + sl.base + (c ? 0u : pstride);
     if (LAYOUT == ISING_INT8) {
-        int8_t *own = reinterpret_cast<int8_t *>(plane_row<LAYOUT>(smem, sg, c, r));
-        const int8_t *o = reinterpret_cast<const int8_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r));
-        const int8_t *ou = reinterpret_cast<const int8_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r - 1));
-        const int8_t *od = reinterpret_cast<const int8_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r + 1));
-        for (uint32_t g = 0; g < sg.G; g++) {
+        int8_t *own = reinterpret_cast<int8_t *>(own_row);
+        const int8_t *o = reinterpret_cast<const int8_t *>(o_row);
+        const int8_t *ou = o - half, *od = o + half;
+        if (G == 2) {
+            // the two sites xh, xh + 1 (xh even) share their middle row
+            // neighbour; draws are taken in site order before either update
+            const uint32_t r0 = gen.next(), r1 = gen.next();
+            if (!sl.val()) return;
+            const uint32_t xh = sl.xh0;
+            const uint32_t li = p ? xh : (xh == 0 ? half - 1 : xh - 1);      // left of site xh
+            const uint32_t ri = p ? (xh + 2 == half ? 0 : xh + 2) : xh + 1;  // right of site xh + 1
+            const int mid = o[xh + p];
+            const int s0 = own[xh], s1 = own[xh + 1];
+            const int a0 = s0 * (o[li] + mid + ou[xh] + od[xh]);
+            const int a1 = s1 * (mid + o[ri] + ou[xh + 1] + od[xh + 1]);
+            if (accept_a(a0, r0, T4, T8)) own[xh] = static_cast<int8_t>(-s0);
+            if (accept_a(a1, r1, T4, T8)) own[xh + 1] = static_cast<int8_t>(-s1);
+            return;
+        }
+        for (uint32_t g = 0; g < G; g++) {
             const uint32_t rr = gen.next();
-            if (!sl.val) continue;
+            if (!sl.val()) continue;
             const uint32_t xh = sl.xh0 + g;
-            const int nn = o[col_left(xh, p, sg.half)] + o[col_right(xh, p, sg.half)] + ou[xh] + od[xh];
+            const int nn = o[col_left(xh, p, half)] + o[col_right(xh, p, half)] + ou[xh] + od[xh];
             const int sp = own[xh];
-            if (accept_flip(2 * sp * nn, rr, sg.T4, sg.T8)) own[xh] = static_cast<int8_t>(-sp);
+            if (accept_a(sp * nn, rr, T4, T8)) own[xh] = static_cast<int8_t>(-sp);
         }
     } else {
-        const uint32_t *own = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, c, r));
-        const uint32_t *o = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r));
-        const uint32_t *ou = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r - 1));
-        const uint32_t *od = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, 1 - c, r + 1));
-        const uint32_t G = sg.G;
+        const uint32_t W = sg.W;
+        const uint32_t *own = reinterpret_cast<const uint32_t *>(own_row);
+        const uint32_t *o = reinterpret_cast<const uint32_t *>(o_row);
+        const uint32_t *ou = o - W, *od = o + W;
         const uint32_t lq0 = lane * G;
         uint32_t c_lo = 0, c_hi = 0;
         for (uint32_t g = 0; g < G; g++) {
             const uint32_t rr = gen.next();
-            if (!sl.val) continue;
+            if (!sl.val()) continue;
             const uint32_t xh = sl.xh0 + g;
-            const int nn = bit_spin(o, col_left(xh, p, sg.half)) + bit_spin(o, col_right(xh, p, sg.half)) +
+            const int nn = bit_spin(o, col_left(xh, p, half)) + bit_spin(o, col_right(xh, p, half)) +
                            bit_spin(ou, xh) + bit_spin(od, xh);
             const int sp = bit_spin(own, xh);
-            if (accept_flip(2 * sp * nn, rr, sg.T4, sg.T8)) {
+            if (accept_a(sp * nn, rr, T4, T8)) {
                 const uint32_t lq = lq0 + g;
                 if ((lq >> 5) == (lq0 >> 5)) c_lo |= 1u << (lq & 31);
                 else c_hi |= 1u << (lq & 31);
@@ -243,13 +292,13 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
         // the warp's 32 G sites are G consecutive words of plane c
         const uint32_t f0 = __shfl_sync(0xffffffffu, static_cast<uint32_t>(sl.s - sg.s0), 0);
         const uint64_t q_first = (sg.s0 + f0) * G;
-        const uint32_t base = static_cast<uint32_t>((q_first - static_cast<uint64_t>(sg.y0) * sg.half) >> 5);
+        const uint32_t wbase = static_cast<uint32_t>((q_first - static_cast<uint64_t>(sg.y0) * half) >> 5);
         uint32_t *plane_c = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, 0));
-        const uint32_t own_words = sg.R * sg.W;
+        const uint32_t own_words = sg.R * W;
         for (uint32_t m = 0; m < G; m++) {
             const uint32_t mine = ((lq0 >> 5) == m ? c_lo : 0u) | ((lq0 >> 5) + 1 == m ? c_hi : 0u);
             const uint32_t word = __reduce_or_sync(0xffffffffu, mine);
-            if (lane == 0 && word && base + m < own_words) plane_c[base + m] ^= word;
+            if (lane == 0 && word && wbase + m < own_words) plane_c[wbase + m] ^= word;
         }
     }
 }
@@ -266,22 +315,17 @@ __device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p)
     return v;
 }
 
-__device__ __forceinline__ bool slot_on_boundary(const SegLocal *S, const StreamSlot &sl)
-{
-    const SegLocal &sg = S[sl.seg];
-    return sl.in && (sl.row == sg.y0 || sl.row + 1 == sg.y0 + sg.R);
-}
-
 // Which warps a pass updates: those holding a first or last row of their
 // strip, the others, or all warps of the strips of one coarse colour
 // (multi-hit phases).  A warp is classified as a whole, so warp-wide steps
 // see all 32 lanes.
 enum { SEL_BOUNDARY = 0, SEL_INTERIOR = 1, SEL_COARSE0 = 2, SEL_COARSE1 = 3 };
 
-__device__ __forceinline__ bool warp_selected(const SegLocal *S, const StreamSlot &sl, int sel)
+__device__ __forceinline__ bool warp_selected(const StreamSlot &sl, int sel)
 {
-    if (sel >= SEL_COARSE0) return S[sl.seg].coarse == static_cast<uint32_t>(sel - SEL_COARSE0);
-    return __any_sync(0xffffffffu, slot_on_boundary(S, sl)) == (sel == SEL_BOUNDARY);
+    if (!(sl.flags & SL_WARP_IN)) return false;
+    if (sel >= SEL_COARSE0) return ((sl.flags & SL_COARSE) != 0) == (sel == SEL_COARSE1);
+    return ((sl.flags & SL_WARP_BND) != 0) == (sel == SEL_BOUNDARY);
 }
 
 // Updates the colour-c sites of the selected warps.  pos_off is the number
@@ -295,8 +339,7 @@ __device__ __forceinline__ void update_pass(uint8_t *smem, const SegLocal *S, ui
     if (resident) {
 #pragma unroll
         for (int k = 0; k < SMAX; k++) {
-            if (!__any_sync(0xffffffffu, slot[k].in)) continue;
-            if (!warp_selected(S, slot[k], sel)) continue;
+            if (!warp_selected(slot[k], sel)) continue;
             update_slot<KIND, LAYOUT>(smem, S[slot[k].seg], slot[k], gen[k], c, lane);
         }
         return;
@@ -311,20 +354,16 @@ __device__ __forceinline__ void update_pass(uint8_t *smem, const SegLocal *S, ui
             const uint64_t f = base + threadIdx.x;
             StreamSlot sl;
             sl.seg = j;
-            sl.in = f < count;
-            sl.s = sg.s0 + (sl.in ? f : 0);
-            sl.val = sl.in && sl.s < sg.n_valid;
-            const uint32_t q0 = static_cast<uint32_t>(sl.s) * sg.G;
-            sl.row = q0 / sg.half;
-            sl.xh0 = q0 - sl.row * sg.half;
-            if (!__any_sync(0xffffffffu, sl.in)) continue;
-            if (!warp_selected(S, sl, sel)) continue;
+            const bool in = f < count;
+            sl.s = static_cast<uint32_t>(sg.s0 + (in ? f : 0));
+            finish_slot<LAYOUT>(sg, in, in && sl.s < sg.n_valid, sl);
+            if (!warp_selected(sl, sel)) continue;
             DevParams rp = sg.rng;
             rp.pos += pos_off;
             Gen<KIND> g;
             g.load(rp, sl.s < sg.n_inst ? sl.s : sg.n_inst - 1);
             update_slot<KIND, LAYOUT>(smem, sg, sl, g, c, lane);
-            if (sl.in && sl.s < sg.n_inst) g.store(rp, sl.s);
+            if (sl.in() && sl.s < sg.n_inst) g.store(rp, sl.s);
         }
     }
 }
@@ -429,6 +468,7 @@ __global__ void __launch_bounds__(SMAX >= (MH ? 4 : 2) ? 512 : 1024) k_ising_per
         s.off = d.smem_off;
         s.lat = d.lat;
         s.coarse = d.coarse;
+        s.pstride = (s.R + 2) * (l.layout == ISING_INT8 ? l.half : l.W * 4u);
         s.up = d.up;
         s.down = d.down;
         s.gid = static_cast<int32_t>(sb + threadIdx.x);
@@ -466,7 +506,7 @@ __global__ void __launch_bounds__(SMAX >= (MH ? 4 : 2) ? 512 : 1024) k_ising_per
     if (resident) {
 #pragma unroll
         for (int k = 0; k < SMAX; k++) {
-            setup_slot(S, nseg, prefix_end, threadIdx.x + static_cast<uint64_t>(k) * blockDim.x, slot[k]);
+            setup_slot<LAYOUT>(S, nseg, prefix_end, threadIdx.x + static_cast<uint64_t>(k) * blockDim.x, slot[k]);
             const SegLocal &sg = S[slot[k].seg];
             gen[k].load(sg.rng, slot[k].s < sg.n_inst ? slot[k].s : sg.n_inst - 1);
         }
@@ -582,7 +622,7 @@ done:
     if (resident) {
 #pragma unroll
         for (int k = 0; k < SMAX; k++)
-            if (slot[k].in && slot[k].s < S[slot[k].seg].n_inst) gen[k].store(a.lats[S[slot[k].seg].lat].rng, slot[k].s);
+            if (slot[k].in() && slot[k].s < S[slot[k].seg].n_inst) gen[k].store(a.lats[S[slot[k].seg].lat].rng, slot[k].s);
     }
 }
 

@@ -1,7 +1,9 @@
-"""Runs one generation kernel configuration a few times, for profiling a
-single kernel under a profiler on a small case.
+"""Runs one generation kernel configuration a few times, or one persistent
+Ising launch, for profiling a single kernel under a profiler on a small case.
 
     python -m paper_1204_6193_gb300.profile_case --kind xs1024w --form u32 --n 262144 --K 256 --reps 3
+    python -m paper_1204_6193_gb300.profile_case --kind xorwow --ising 1024 --sweeps 200
+    python -m paper_1204_6193_gb300.profile_case --kind xorwow --ising 1024 --sweeps 2 --hits 100 --strips 256
 """
 import argparse
 
@@ -18,8 +20,24 @@ def main():
     ap.add_argument("--n", type=int, default=1 << 18)
     ap.add_argument("--K", type=int, default=256)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--ising", type=int, default=0, help="lattice size L: one persistent Ising launch instead")
+    ap.add_argument("--spins", default="int8", choices=["int8", "multispin"])
+    ap.add_argument("--sweeps", type=int, default=200, help="sweeps (or multi-hit rounds)")
+    ap.add_argument("--hits", type=int, default=0, help="k > 0: multi-hit rounds of k sweeps per strip phase")
+    ap.add_argument("--strips", type=int, default=256, help="row strips of the multi-hit update")
     a = ap.parse_args()
     kind = {v: k for k, v in R.KIND_NAMES.items()}[a.kind]
+    if a.ising:
+        layout = R.ISING_INT8 if a.spins == "int8" else R.ISING_MULTISPIN32
+        h = R.ising_create(a.ising, 0.4406867935097715, layout, kind, 0, 12345, 2)
+        if a.hits:
+            R.ising_sweep_multihit(h, a.sweeps, a.hits, a.strips)
+        else:
+            R.ising_sweep(h, a.sweeps)
+        R.ising_observables(h)
+        R.ising_destroy(h)
+        print("ok")
+        return
     layout = R.RNG_STEP_MAJOR if a.layout == "step" else R.RNG_INSTANCE_MAJOR
     h = R.rng_create(kind, a.n)
     R.rng_seed(h, 12345)
