@@ -24,11 +24,11 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
-LCG32, LCG64, MWC, XORWOW, PHILOX4X32_10, XS1024W, MT19937_SHARED = range(7)
-SEED_RANDOM, SEED_LEAPFROG, SEED_SUBSTREAM, MWC_SAME_A = 0, 1, 2, 4
+LCG32, LCG64, MWC, XORWOW, PHILOX4X32_10, XS1024W, MT19937_SHARED, PHILOX4X32_7 = range(8)
+SEED_RANDOM, SEED_LEAPFROG, SEED_SUBSTREAM, MWC_SAME_A, PHILOX_INTRINSIC_KEY = 0, 1, 2, 4, 8
 KIND_NAMES = {LCG32: "lcg32", LCG64: "lcg64", MWC: "mwc", XORWOW: "xorwow",
               PHILOX4X32_10: "philox4x32_10", XS1024W: "xs1024w",
-              MT19937_SHARED: "mt19937_shared"}
+              MT19937_SHARED: "mt19937_shared", PHILOX4X32_7: "philox4x32_7"}
 
 _lock = threading.Lock()
 _lib = None

@@ -29,8 +29,8 @@
 
 typedef unsigned __int128 u128;
 
-enum { K_LCG32 = 0, K_LCG64 = 1, K_MWC = 2, K_XORWOW = 3, K_PHILOX = 4, K_XS1024W = 5, K_MT = 6 };
-enum { F_LEAPFROG = 1, F_SUBSTREAM = 2, F_MWC_SAME_A = 4 };
+enum { K_LCG32 = 0, K_LCG64 = 1, K_MWC = 2, K_XORWOW = 3, K_PHILOX = 4, K_XS1024W = 5, K_MT = 6, K_PHILOX7 = 7 };
+enum { F_LEAPFROG = 1, F_SUBSTREAM = 2, F_MWC_SAME_A = 4, F_PHILOX_INTRINSIC = 8 };
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_EUNSUPPORTED = 3 };
 
 /* ------------------------------------------------------------------------ */
@@ -624,10 +624,19 @@ static int inst_init(inst_t *s, int kind, uint32_t flags, uint64_t seed, uint64_
         if (!(s->xw.x | s->xw.y | s->xw.z | s->xw.w | s->xw.v)) s->xw.x = 1;
         return ORC_OK;
     }
-    case K_PHILOX: {
-        uint64_t w = orc_seed_word(seed, i);
-        s->k0 = (uint32_t)w;
-        s->k1 = (uint32_t)(w >> 32);
+    case K_PHILOX:
+    case K_PHILOX7: {
+        if (flags & F_PHILOX_INTRINSIC) {
+            /* Sec. 7, intrinsic variables: the key is the instance (site)
+             * number and a word naming the run, here the low half of the
+             * seed; the counter (the block index) is the draw position */
+            s->k0 = (uint32_t)i;
+            s->k1 = (uint32_t)seed;
+        } else {
+            uint64_t w = orc_seed_word(seed, i);
+            s->k0 = (uint32_t)w;
+            s->k1 = (uint32_t)(w >> 32);
+        }
         s->pos = 0;
         return ORC_OK;
     }
@@ -656,11 +665,13 @@ static uint32_t inst_next(inst_t *s, int philox_rounds)
         return mwc_step(&s->v, s->a);
     case K_XORWOW:
         return xorwow_next(&s->xw);
-    case K_PHILOX: {
-        /* draw d is word d % 4 of block d / 4; counter = (block, 0) */
+    case K_PHILOX:
+    case K_PHILOX7: {
+        /* draw d is word d % 4 of block d / 4; counter = (block, 0);
+         * Philox4x32-7 (Sec. 7) always takes 7 rounds */
         uint64_t j = s->pos / 4;
         uint32_t ctr[4] = {(uint32_t)j, (uint32_t)(j >> 32), 0, 0}, o[4];
-        orc_philox4x32(ctr, s->k0, s->k1, philox_rounds, o);
+        orc_philox4x32(ctr, s->k0, s->k1, s->kind == K_PHILOX7 ? 7 : philox_rounds, o);
         return o[s->pos++ % 4];
     }
     case K_MT:
@@ -703,6 +714,7 @@ static int inst_jump(inst_t *s, uint64_t t)
         return ORC_OK;
     }
     case K_PHILOX:
+    case K_PHILOX7:
         s->pos += t;
         return ORC_OK;
     }
@@ -758,7 +770,9 @@ static int xs_warp_jump(uint32_t *x, uint64_t t)
 
 static int check_kind_flags(int kind, uint32_t flags, uint64_t n)
 {
-    if (kind < 0 || kind > K_MT || n == 0) return ORC_EINVAL;
+    if (kind < 0 || kind > K_PHILOX7 || n == 0) return ORC_EINVAL;
+    if ((flags & F_PHILOX_INTRINSIC) && kind != K_PHILOX && kind != K_PHILOX7) return ORC_EUNSUPPORTED;
+    if ((flags & F_PHILOX_INTRINSIC) && n > (1ULL << 32)) return ORC_EINVAL;  /* a 32-bit key word */
     if ((flags & F_LEAPFROG) && kind != K_LCG32 && kind != K_LCG64) return ORC_EUNSUPPORTED;
     if ((flags & F_SUBSTREAM) && kind != K_XS1024W) return ORC_EUNSUPPORTED;
     if ((flags & F_MWC_SAME_A) && kind != K_MWC) return ORC_EUNSUPPORTED;

@@ -352,6 +352,43 @@ def test_philox_stream_is_counter_blocks():
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("kind,rounds", [(O.PHILOX4X32_7, 7), (O.PHILOX4X32_10, 10)])
+@pytest.mark.parametrize("flags", [0, O.PHILOX_INTRINSIC_KEY])
+def test_philox_streams_against_torch_engine(torch_philox, kind, rounds, flags):
+    # Whole streams, key mapping and counter layout included, against the
+    # independent engine: draw d of instance i is word d % 4 of the block at
+    # counter d / 4, under key w_i or, with intrinsic keys (Sec. 7), under
+    # key (i, low half of the seed)
+    seed, n, K = 0xDEADBEEF00C0FFEE, 1 << 20, 11
+    idx = [0, 1, 77, n - 1]
+    got = np.concatenate([O.generate(kind, seed, n, K, flags=flags, i_lo=i, i_hi=i + 1, skip=5) for i in idx])
+    lines = []
+    for i in idx:
+        key = ((seed & 0xFFFFFFFF) << 32 | i) if flags else O.seed_word(seed, i)
+        lines += [f"{key} {j} {rounds}\n" for j in range(1, 5)]  # draws 5..15 lie in blocks 1..3
+    res = subprocess.run([torch_philox], input="".join(lines), capture_output=True, text=True, check=True)
+    words = np.array([[int(v) for v in ln.split()] for ln in res.stdout.strip().split("\n")], dtype=np.uint64)
+    words = words.reshape(len(idx), -1)
+    assert np.array_equal(got, words[:, 1:1 + K].astype(np.uint32))
+
+
+def test_philox_intrinsic_keys_do_not_depend_on_the_instance_count():
+    # a stream is named by its own index and the run word only: any shard or
+    # launch split of the instances reproduces it
+    a = O.generate(O.PHILOX4X32_7, SEED, 64, 20, flags=O.PHILOX_INTRINSIC_KEY, i_lo=10, i_hi=14)
+    b = O.generate(O.PHILOX4X32_7, SEED, 1 << 30, 20, flags=O.PHILOX_INTRINSIC_KEY, i_lo=10, i_hi=14)
+    assert np.array_equal(a, b)
+    # the run word is the low half of the seed
+    c = O.generate(O.PHILOX4X32_7, SEED ^ (1 << 40), 64, 20, flags=O.PHILOX_INTRINSIC_KEY, i_lo=10, i_hi=14)
+    assert np.array_equal(a, c)
+    d = O.generate(O.PHILOX4X32_7, SEED, 64, 20, i_lo=10, i_hi=14)
+    assert not np.array_equal(a, d)
+    with pytest.raises(O.OracleError):
+        O.generate(O.XORWOW, SEED, 64, 4, flags=O.PHILOX_INTRINSIC_KEY)
+    with pytest.raises(O.OracleError):  # instance indices past 2^32 do not fit the key word
+        O.generate(O.PHILOX4X32_7, SEED, (1 << 32) + 1, 4, flags=O.PHILOX_INTRINSIC_KEY, i_lo=0, i_hi=1)
+
+
 # ----------------------------------------------------------------------- MT
 def test_mt19937_cxx_standard_value():
     # The C++ standard ([rand.predef]) fixes the 10000th output of

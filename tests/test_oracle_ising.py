@@ -75,17 +75,18 @@ def test_initial_spins_are_balanced():
     assert abs(int(s.astype(np.int64).sum())) < 5 * np.sqrt(n)
 
 
-@pytest.mark.parametrize("kind", [O.XORWOW, O.XS1024W, O.PHILOX4X32_10, O.LCG64])
+@pytest.mark.parametrize("kind,flags", [(O.XORWOW, 0), (O.XS1024W, 0), (O.PHILOX4X32_10, 0), (O.LCG64, 0),
+                                        (O.PHILOX4X32_7, O.PHILOX_INTRINSIC_KEY)])
 @pytest.mark.parametrize("beta", [0.3, 0.4])
-def test_checkerboard_chain_reproduces_exact_energy(kind, beta):
+def test_checkerboard_chain_reproduces_exact_energy(kind, flags, beta):
     # Application test of Sec. 2 on a lattice whose exact values are cheap:
     # e and C_V of an 8x8 torus, estimated from 50 independent chunks.
     L, chunks, per = 8, 50, 2000
     e_chunks, cv_chunks = [], []
     N = L * L
     for c in range(chunks):
-        s0, _, _ = O.ising_run(L, beta, kind, 5000 + c, 200)  # equilibration
-        s, acc, nm = O.ising_run(L, beta, kind, 9000 + c, per, measure_every=1, spins=s0)
+        s0, _, _ = O.ising_run(L, beta, kind, 5000 + c, 200, flags=flags)  # equilibration
+        s, acc, nm = O.ising_run(L, beta, kind, 9000 + c, per, measure_every=1, spins=s0, flags=flags)
         mE = acc[0] / nm
         mE2 = acc[1] / nm
         e_chunks.append(-mE / N)
