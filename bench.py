@@ -5,7 +5,7 @@ Default (N=1): the bulk workload -- 2^20 resident instances of every
 generator kind, 1024 draws each (2^30 outputs per call; the block-shared
 MT19937 as 32768 warp-shared generators x 2^15 draws), written to HBM as u32, exact
 uniform f32 and Box-Muller normals, and consumed in registers (u32 XOR
-reduce).  One step = those 28 calls.  `value` = outputs of all ranks /
+reduce).  One step = those 32 calls (eight kinds x four forms).  `value` = outputs of all ranks /
 device time (Gnum/s).  Extra keys report the Ising sweep (flips/ns) and
 the other workloads.
 
@@ -40,7 +40,8 @@ FORMS = ["u32", "f32", "normal", "u32_xor"]
 # state bytes moved per instance and call: load + store of the state, plus
 # the MWC multiplier read; Philox only reads its key (the position is the
 # handle's counter)
-STATE_TRAFFIC = {0: 8, 1: 16, 2: 20, 3: 48, 4: 8, 5: 8, 6: 2 * 624 * 4}
+STATE_TRAFFIC = {0: 8, 1: 16, 2: 20, 3: 48, 4: 8, 5: 8, 6: 2 * 624 * 4, 7: 8}
+N_KINDS = 8  # LCG32, LCG64, MWC, XORWOW, Philox4x32-10, XS1024W, MT19937, Philox4x32-7
 
 
 def shard_range(rank: int, world: int, per_rank: int):
@@ -150,7 +151,7 @@ class Bulk:
     def __init__(self, R, torch, rank, world):
         self.R, self.torch = R, torch
         self.handles = {}
-        for kind in range(7):
+        for kind in range(N_KINDS):
             per = MT_GENS if kind == R.RNG_MT19937_SHARED else N_INST
             first, n, total = shard_range(rank, world, per)
             h = R.rng_create_shard(kind, total, first, n, 0)
@@ -163,7 +164,7 @@ class Bulk:
         """(name, kind, form, fn, n, K, layout) for one step."""
         R = self.R
         res = []
-        for kind in range(7):
+        for kind in range(N_KINDS):
             h, n = self.handles[kind]
             K = MT_DRAWS if kind == R.RNG_MT19937_SHARED else K_DRAWS
             lay = R.RNG_INSTANCE_MAJOR if kind == R.RNG_MT19937_SHARED else R.RNG_STEP_MAJOR
@@ -291,7 +292,7 @@ def run_gpu(args):
 
         def run_direct():
             for st in range(e_steps):
-                for kind in range(7):
+                for kind in range(N_KINDS):
                     R.rng_seed(bulk.handles[kind][0], SEED + 1 + st)
                 for c in calls:
                     launch_into(c, hred.data_ptr() if c[2] == "u32_xor" else host.data_ptr())
@@ -315,7 +316,7 @@ def run_gpu(args):
         def run_copy():
             i = 0
             for st in range(e_steps):
-                for kind in range(7):
+                for kind in range(N_KINDS):
                     R.rng_seed(bulk.handles[kind][0], SEED + 1 + st)
                 for c in calls:
                     b = bufs[i % 2]
@@ -377,7 +378,7 @@ def run_gpu(args):
             "config": {
                 "workload": "bulk generation: 2^20 resident instances x 1024 draws per call (MT19937: 32768 "
                             "warp-shared generators x 2^15), 7 generators x {u32, f32, normal} written to HBM + "
-                            "u32 consumed in registers (XOR reduce); 28 calls per step",
+                            "u32 consumed in registers (XOR reduce); 32 calls per step",
                 "instances_per_gpu": N_INST, "draws_per_call": K_DRAWS, "outputs_per_step_per_gpu":
                     outputs_per_step_rank, "layout": "step-major (MT19937: instance-major)",
                 "l2": "no flush: every write call streams 4 GiB (> 129 MB L2)", "seed": hex(SEED),
@@ -401,6 +402,15 @@ def run_gpu(args):
 BETA_C = 0.44068679350977151
 
 
+# (kind, flags) of the Ising consumers: the paper's generator, xorwow, both
+# Philox variants (Philox4x32-7 with intrinsic keys, Sec. 7) and LCG32
+ISING_KINDS = ((5, 0), (3, 0), (4, 0), (7, 8), (0, 0))
+
+
+def _ising_kind_name(R, kind, flags):
+    return R.KIND_NAMES[kind] + ("_intrinsic" if flags & R.RNG_PHILOX_INTRINSIC_KEY else "")
+
+
 def _time_sweeps(R, torch, h, n, plain=False):
     stream = torch.cuda.current_stream()
     a = torch.cuda.Event(enable_timing=True)
@@ -421,23 +431,74 @@ def ising_section(R, torch, args):
     n = args.ising_sweeps
     for L in (1024, 64):
         for layout, lname in ((R.ISING_INT8, "int8"), (R.ISING_MULTISPIN32, "multispin32")):
-            for kind in (R.RNG_XS1024W, R.RNG_XORWOW, R.RNG_PHILOX4X32_10, R.RNG_LCG32):
+            for kind, flags in ISING_KINDS:
                 if L == 64 and kind not in (R.RNG_XS1024W, R.RNG_XORWOW):
                     continue
-                h = R.ising_create(L, BETA_C, layout, kind, 0, SEED, 2)
+                h = R.ising_create(L, BETA_C, layout, kind, flags, SEED, 2)
                 try:
                     tuned = R.ising_autotune(h, 64)
                     R.ising_sweep(h, 50)
                     ms = _time_sweeps(R, torch, h, n)
                     nplain = max(20, n // 10)
                     ms_plain = _time_sweeps(R, torch, h, nplain, plain=True)
-                    key = f"L{L}/{lname}/{R.KIND_NAMES[kind]}"
+                    key = f"L{L}/{lname}/{_ising_kind_name(R, kind, flags)}"
                     out[key] = {
                         "flips_per_ns": round(L * L * n / (ms * 1e6), 2),
                         "us_per_sweep": round(1e3 * ms / n, 3),
                         "plain_flips_per_ns": round(L * L * nplain / (ms_plain * 1e6), 3),
                         "sweeps_timed": n, "launch": tuned, "plan": R.ising_plan_info(h),
                     }
+                finally:
+                    R.ising_destroy(h)
+    out["multihit"] = multihit_section(R, torch, n)
+    return out
+
+
+def _time_rounds(R, torch, h, rounds, k, strips):
+    stream = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    R.ising_sweep_multihit(h, rounds, k, strips, 0, stream.cuda_stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    R.ising_observables(h)
+    return a.elapsed_time(b)
+
+
+def multihit_section(R, torch, n):
+    """Multi-hit (double checkerboard) rounds: k sweeps per strip phase, k = 1,
+    2 (Sec. 7) and 100 (the t_up^{k=100} column of Table 1), flips/ns = L^2 k
+    rounds / device time; the strip count is the fastest of a few on a short
+    probe."""
+    out = {}
+    for L, cands in ((1024, (256, 512, 1024)), (64, (2, 4, 8, 16))):
+        for layout, lname in ((R.ISING_INT8, "int8"), (R.ISING_MULTISPIN32, "multispin32")):
+            for kind, flags in ISING_KINDS:
+                if L == 64 and kind not in (R.RNG_XS1024W, R.RNG_XORWOW):
+                    continue
+                h = R.ising_create(L, BETA_C, layout, kind, flags, SEED, 2)
+                try:
+                    best = None
+                    for strips in cands:
+                        try:
+                            R.ising_sweep_multihit(h, 1, 100, strips)
+                            ms = _time_rounds(R, torch, h, 2, 100, strips)
+                        except R.RngError:
+                            continue
+                        if best is None or ms < best[0]:
+                            best = (ms, strips)
+                    if best is None:
+                        continue
+                    strips = best[1]
+                    rec = {"strips": strips}
+                    for k in (1, 2, 100):
+                        rounds = max(2, n // k)
+                        ms = _time_rounds(R, torch, h, rounds, k, strips)
+                        rec[f"k{k}_flips_per_ns"] = round(L * L * k * rounds / (ms * 1e6), 2)
+                        rec[f"k{k}_rounds_timed"] = rounds
+                    out[f"L{L}/{lname}/{_ising_kind_name(R, kind, flags)}"] = rec
                 finally:
                     R.ising_destroy(h)
     return out
@@ -644,7 +705,7 @@ def oracle_sample(per_form: int):
     O.mwc_multipliers(8192)  # multiplier table outside the timed region
     total = 0
     t0 = time.perf_counter()
-    for kind in range(7):
+    for kind in range(N_KINDS):
         if kind == O.MT19937_SHARED:
             n, K = 4, per_form // 4
         else:
@@ -666,7 +727,7 @@ def cpu_baseline(args):
     per_form = args.cpu_sample
     total, dt = oracle_sample(per_form)
     return {"value": round(total / dt / 1e9, 4), "unit": "Gnum/s", "cores": 1, "kind": "oracle",
-            "sample": f"{per_form} outputs per kind and form (7 kinds x 4 forms = {total} outputs), "
+            "sample": f"{per_form} outputs per kind and form ({N_KINDS} kinds x 4 forms = {total} outputs), "
                       f"single-threaded C oracle, {dt:.1f} s"}
 
 

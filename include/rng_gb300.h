@@ -60,7 +60,9 @@ enum {
     RNG_XORWOW = 3,         /* Sec. 6: Marsaglia's 160-bit xorshift plus Weyl sequence */
     RNG_PHILOX4X32_10 = 4,  /* Sec. 7: counter-based Philox4x32, 10 rounds */
     RNG_XS1024W = 5,        /* Sec. 6, Listing 1: the paper's 1024-bit warp-shared xorshift plus Weyl */
-    RNG_MT19937_SHARED = 6  /* Sec. 5: MT19937, one block-shared state per generator */
+    RNG_MT19937_SHARED = 6, /* Sec. 5: MT19937, one block-shared state per generator */
+    RNG_PHILOX4X32_7 = 7    /* Sec. 7: Philox4x32 with 7 rounds (the fewest the Philox authors found
+                               Crush-resistant); streams laid out as RNG_PHILOX4X32_10 */
 };
 
 /* Seeding flags (rng_create). */
@@ -68,7 +70,12 @@ enum {
     RNG_SEED_RANDOM = 0,    /* each instance seeded from its own SplitMix64 words */
     RNG_SEED_LEAPFROG = 1,  /* LCGs only, Sec. 2 Eq. (2): instances interleave one serial sequence */
     RNG_SEED_SUBSTREAM = 2, /* XS1024W only, Sec. 6: warp j starts 2^137 j steps into one sequence */
-    RNG_MWC_SAME_A = 4      /* MWC only, Sec. 3: one shared multiplier instead of one per instance */
+    RNG_MWC_SAME_A = 4,     /* MWC only, Sec. 3: one shared multiplier instead of one per instance */
+    RNG_PHILOX_INTRINSIC_KEY = 8 /* Philox kinds only, Sec. 7: intrinsic-variable keys -- instance i
+                                    (an Ising stream: its site-pair number) has key (k0, k1) =
+                                    (i, low 32 bits of the seed), the run word; counter = draw
+                                    block index, which for two sites per stream is the sweep
+                                    number.  Needs n_total <= 2^32. */
 };
 
 /* Output layouts (rng_generate_*). */
@@ -92,8 +99,8 @@ enum {
  * of a warp-shared 1024-bit state, Sec. 6, so n_instances must be a multiple
  * of 32; for RNG_MT19937_SHARED an instance is one MT19937 generator whose
  * 624-word state a thread block shares, Sec. 5).  `flags` is an OR of the
- * RNG_SEED_* / RNG_MWC_SAME_A values valid for the kind, else
- * RNG_EUNSUPPORTED.  The instances are unseeded until rng_seed.
+ * RNG_SEED_* / RNG_MWC_SAME_A / RNG_PHILOX_INTRINSIC_KEY values valid for
+ * the kind, else RNG_EUNSUPPORTED.  The instances are unseeded until rng_seed.
  * RNG_MWC without RNG_MWC_SAME_A needs n_instances distinct multipliers
  * (more than 10^6 exist below 2^32, Sec. 3); beyond the table, RNG_EINVAL. */
 int rng_create(rng_t *out, int kind, uint64_t n_instances, uint32_t flags, void *cuda_stream);

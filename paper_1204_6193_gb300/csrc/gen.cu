@@ -30,19 +30,20 @@ __global__ void __launch_bounds__(kBlock) k_generate(DevParams p, void *out_, ui
     if (active) g.load(p, i);
     else g.load(p, n - 1);  // dummy state, output discarded
 
-    if constexpr (KIND == RNG_PHILOX4X32_10) {
+    if constexpr (is_philox(KIND)) {
         // block-aligned calls: one block evaluation yields draws k..k+3
         if (LAYOUT != RNG_INSTANCE_MAJOR && (p.pos & 3) == 0 && (K & 3) == 0) {
+            constexpr int RR = Gen<KIND>::kRounds;
             const uint64_t blk0 = p.pos >> 2;
-            const PhiloxKeys keys(g.k0, g.k1);
+            const PhiloxKeys<RR> keys(g.k0, g.k1);
             uint32_t xacc = 0;
             float facc = 0.0f;
 #pragma unroll 2
             for (uint64_t k = 0; k < K; k += 4) {
                 const uint64_t blk = blk0 + (k >> 2);
                 uint32_t o[4];
-                philox10_keys(static_cast<uint32_t>(blk), static_cast<uint32_t>(blk >> 32), 0u, 0u, keys, o[0], o[1],
-                              o[2], o[3]);
+                philox_keys<RR>(static_cast<uint32_t>(blk), static_cast<uint32_t>(blk >> 32), 0u, 0u, keys, o[0],
+                                o[1], o[2], o[3]);
                 if (OUT == OUT_NORMAL) {
                     float z[4];
                     box_muller(o[0], o[1], z[0], z[1]);
@@ -513,6 +514,7 @@ int launch_generate(const GenState &g, void *d_out, uint64_t K, int out_kind, in
     case RNG_MWC: return launch_kind<RNG_MWC>(g, d_out, K, out_kind, layout, s);
     case RNG_XORWOW: return launch_kind<RNG_XORWOW>(g, d_out, K, out_kind, layout, s);
     case RNG_PHILOX4X32_10: return launch_kind<RNG_PHILOX4X32_10>(g, d_out, K, out_kind, layout, s);
+    case RNG_PHILOX4X32_7: return launch_kind<RNG_PHILOX4X32_7>(g, d_out, K, out_kind, layout, s);
     case RNG_XS1024W: return launch_kind<RNG_XS1024W>(g, d_out, K, out_kind, layout, s);
     case RNG_MT19937_SHARED: return launch_kind<RNG_MT19937_SHARED>(g, d_out, K, out_kind, layout, s);
     }

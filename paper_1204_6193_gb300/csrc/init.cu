@@ -79,11 +79,15 @@ __global__ void k_seed_xorwow(DevParams p, uint64_t seed, uint64_t first)
     for (int k = 0; k < 6; k++) static_cast<uint32_t *>(p.s[k])[li] = v[k];
 }
 
-__global__ void k_seed_philox(DevParams p, uint64_t seed, uint64_t first)
+// Philox keys: the instance's seed word, or the intrinsic key (global
+// instance index, low half of the seed) -- Sec. 7.
+__global__ void k_seed_philox(DevParams p, uint64_t seed, uint64_t first, bool intrinsic)
 {
     const uint64_t li = static_cast<uint64_t>(blockIdx.x) * kBlock + threadIdx.x;
     if (li >= p.n) return;
-    static_cast<uint64_t *>(p.s[0])[li] = d_seed_word(seed, first + li);
+    const uint64_t i = first + li;
+    static_cast<uint64_t *>(p.s[0])[li] =
+        intrinsic ? ((seed & 0xFFFFFFFFull) << 32) | (i & 0xFFFFFFFFull) : d_seed_word(seed, i);
 }
 
 // Random seeding of the 1024-bit generator: lane l of global warp J takes
@@ -219,7 +223,10 @@ int launch_seed(GenState &g, uint64_t seed, cudaStream_t s)
         break;
     case RNG_MWC: k_seed_mwc<<<nb, kBlock, 0, s>>>(p, seed, g.first); break;
     case RNG_XORWOW: k_seed_xorwow<<<nb, kBlock, 0, s>>>(p, seed, g.first); break;
-    case RNG_PHILOX4X32_10: k_seed_philox<<<nb, kBlock, 0, s>>>(p, seed, g.first); break;
+    case RNG_PHILOX4X32_10:
+    case RNG_PHILOX4X32_7:
+        k_seed_philox<<<nb, kBlock, 0, s>>>(p, seed, g.first, (g.flags & RNG_PHILOX_INTRINSIC_KEY) != 0);
+        break;
     case RNG_XS1024W:
         if (g.flags & RNG_SEED_SUBSTREAM) {
             int levels = 0;
@@ -261,7 +268,8 @@ int launch_skipahead(GenState &g, uint64_t t, cudaStream_t s)
         k_skip_lcg<<<nb, kBlock, 0, s>>>(p, t, g.kind == RNG_LCG64);
         break;
     case RNG_MWC: k_skip_mwc<<<nb, kBlock, 0, s>>>(p, t); break;
-    case RNG_PHILOX4X32_10: break;  // counter-based: the position alone moves
+    case RNG_PHILOX4X32_10:
+    case RNG_PHILOX4X32_7: break;  // counter-based: the position alone moves
     case RNG_XORWOW:
     case RNG_XS1024W: {
         const int n = g.kind == RNG_XS1024W ? 1024 : 160;

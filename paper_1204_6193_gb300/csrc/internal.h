@@ -11,6 +11,7 @@
 namespace rngx {
 
 constexpr int MT_N_WORDS = 624;  // MT19937 state words (Sec. 5: N = 624)
+constexpr int kNumKinds = RNG_PHILOX4X32_7 + 1;  // generator kinds 0 .. kNumKinds-1
 
 // ------------------------------------------------------------- errors
 void set_error(const char *fmt, ...);

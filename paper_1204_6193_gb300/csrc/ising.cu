@@ -31,6 +31,7 @@ int dispatch_half(int kind, const LatDev &lat, int c, cudaStream_t s)
     case RNG_MWC: return launch_half<RNG_MWC>(lat, c, s);
     case RNG_XORWOW: return launch_half<RNG_XORWOW>(lat, c, s);
     case RNG_PHILOX4X32_10: return launch_half<RNG_PHILOX4X32_10>(lat, c, s);
+    case RNG_PHILOX4X32_7: return launch_half<RNG_PHILOX4X32_7>(lat, c, s);
     case RNG_XS1024W: return launch_half<RNG_XS1024W>(lat, c, s);
     }
     set_error("Ising: generator kind %d not supported", kind);
@@ -46,6 +47,7 @@ int dispatch_persist(int kind, int layout, int smax, const PersistArgs &a, unsig
     case RNG_MWC: return launch_persist<RNG_MWC>(layout, smax, a, nb, th, smem, s, max_blocks);
     case RNG_XORWOW: return launch_persist<RNG_XORWOW>(layout, smax, a, nb, th, smem, s, max_blocks);
     case RNG_PHILOX4X32_10: return launch_persist<RNG_PHILOX4X32_10>(layout, smax, a, nb, th, smem, s, max_blocks);
+    case RNG_PHILOX4X32_7: return launch_persist<RNG_PHILOX4X32_7>(layout, smax, a, nb, th, smem, s, max_blocks);
     case RNG_XS1024W: return launch_persist<RNG_XS1024W>(layout, smax, a, nb, th, smem, s, max_blocks);
     }
     set_error("Ising: generator kind %d not supported", kind);
@@ -267,7 +269,7 @@ int lat_create(IsingLat &t, uint32_t L, double beta, int layout, int kind, uint3
         set_error("Ising: G (sites per stream per colour) must divide L/2");
         return RNG_EINVAL;
     }
-    if (kind == RNG_MT19937_SHARED || kind < RNG_LCG32 || kind > RNG_MT19937_SHARED) {
+    if (kind == RNG_MT19937_SHARED || kind < RNG_LCG32 || kind >= kNumKinds) {
         set_error("Ising: generator kind %d is not supported by the application test", kind);
         return RNG_EUNSUPPORTED;
     }

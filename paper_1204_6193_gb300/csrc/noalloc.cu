@@ -61,6 +61,7 @@ extern "C" int rng_skipahead_noalloc(int kind, void *d_state, uint64_t n_instanc
     case RNG_LCG64:
     case RNG_MWC:
     case RNG_PHILOX4X32_10:
+    case RNG_PHILOX4X32_7:
         set_error("rng_skipahead_noalloc: kind %d skips without scratch; use rng_skipahead", kind);
         return RNG_EUNSUPPORTED;
     default: set_error("rng_skipahead_noalloc: unknown generator kind %d", kind); return RNG_EINVAL;

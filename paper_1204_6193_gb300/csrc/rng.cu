@@ -55,7 +55,8 @@ void state_layout(int kind, size_t &bytes_per, int &arrays, size_t &elem)
     case RNG_LCG64: bytes_per = 8; arrays = 1; elem = 8; break;
     case RNG_MWC: bytes_per = 8; arrays = 1; elem = 8; break;
     case RNG_XORWOW: bytes_per = 24; arrays = 6; elem = 4; break;
-    case RNG_PHILOX4X32_10: bytes_per = 8; arrays = 1; elem = 8; break;
+    case RNG_PHILOX4X32_10:
+    case RNG_PHILOX4X32_7: bytes_per = 8; arrays = 1; elem = 8; break;
     case RNG_XS1024W: bytes_per = 4; arrays = 1; elem = 4; break;
     case RNG_MT19937_SHARED: bytes_per = 4 * MT_N_WORDS; arrays = 1; elem = 4 * MT_N_WORDS; break;
     default: bytes_per = 0; arrays = 0; elem = 0;
@@ -64,7 +65,8 @@ void state_layout(int kind, size_t &bytes_per, int &arrays, size_t &elem)
 
 int check_flags(int kind, uint32_t flags)
 {
-    if (flags & ~static_cast<uint32_t>(RNG_SEED_LEAPFROG | RNG_SEED_SUBSTREAM | RNG_MWC_SAME_A)) {
+    if (flags & ~static_cast<uint32_t>(RNG_SEED_LEAPFROG | RNG_SEED_SUBSTREAM | RNG_MWC_SAME_A |
+                                       RNG_PHILOX_INTRINSIC_KEY)) {
         set_error("unknown flag bits 0x%x", flags);
         return RNG_EINVAL;
     }
@@ -78,6 +80,10 @@ int check_flags(int kind, uint32_t flags)
     }
     if ((flags & RNG_MWC_SAME_A) && kind != RNG_MWC) {
         set_error("RNG_MWC_SAME_A is defined for RNG_MWC only");
+        return RNG_EUNSUPPORTED;
+    }
+    if ((flags & RNG_PHILOX_INTRINSIC_KEY) && kind != RNG_PHILOX4X32_10 && kind != RNG_PHILOX4X32_7) {
+        set_error("RNG_PHILOX_INTRINSIC_KEY is defined for the Philox kinds only");
         return RNG_EUNSUPPORTED;
     }
     return RNG_OK;
@@ -170,7 +176,7 @@ int rng_create_shard(rng_t *out, int kind, uint64_t n_total, uint64_t first, uin
         return RNG_EINVAL;
     }
     *out = nullptr;
-    if (kind < RNG_LCG32 || kind > RNG_MT19937_SHARED) {
+    if (kind < RNG_LCG32 || kind >= kNumKinds) {
         set_error("unknown generator kind %d", kind);
         return RNG_EINVAL;
     }
@@ -186,6 +192,10 @@ int rng_create_shard(rng_t *out, int kind, uint64_t n_total, uint64_t first, uin
     }
     if (kind == RNG_MT19937_SHARED && count > 0x7fffffffull) {
         set_error("too many MT19937 generators");
+        return RNG_EINVAL;
+    }
+    if ((flags & RNG_PHILOX_INTRINSIC_KEY) && n_total > (1ull << 32)) {
+        set_error("intrinsic Philox keys hold the instance index in 32 bits: at most 2^32 instances");
         return RNG_EINVAL;
     }
     if (count > (1ull << 34)) {
@@ -207,7 +217,7 @@ int rng_create_shard(rng_t *out, int kind, uint64_t n_total, uint64_t first, uin
     g.first = first;
     g.n_total = n_total;
     g.pos = 0;
-    g.philox_rounds = 10;
+    g.philox_rounds = kind == RNG_PHILOX4X32_7 ? 7 : 10;
     g.mwc_a = nullptr;
     g.mwc_a0 = 0;
     for (int i = 0; i < 6; i++) g.s[i] = nullptr;

@@ -389,7 +389,7 @@ int rng_server_create(rng_server_t *out, uint32_t n_sets, uint32_t instances_per
     int st = cudaGetDevice(&S->device) == cudaSuccess ? RNG_OK : RNG_ECUDA;
     S->slots.resize(n_slots + 1, nullptr);
     S->slot_req.resize(n_slots + 1, nullptr);
-    S->work.assign(n_slots + 1, std::vector<rng_t>(RNG_MT19937_SHARED + 1, nullptr));
+    S->work.assign(n_slots + 1, std::vector<rng_t>(kNumKinds, nullptr));
     for (auto &s : S->slots)
         if (st == RNG_OK && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) st = RNG_ECUDA;
     if (st == RNG_OK) st = build_ladders(S, S->slots[0]);
@@ -410,13 +410,15 @@ int rng_server_submit(rng_server_t S, const rng_request_t *req, uint64_t *ticket
     }
     const rng_request_t &r = *req;
     if (r.type == RNG_REQ_DRAW) {
-        if (r.kind < RNG_LCG32 || r.kind >= RNG_MT19937_SHARED || r.count == 0 || r.out < RNG_OUT_U32 ||
+        if (r.kind < RNG_LCG32 || r.kind >= kNumKinds || r.kind == RNG_MT19937_SHARED || r.count == 0 ||
+            r.out < RNG_OUT_U32 ||
             r.out > RNG_OUT_NORMAL || (r.out == RNG_OUT_NORMAL && (r.count & 1))) {
             set_error("rng_server_submit: bad draw request (kind, count, output form)");
             return RNG_EINVAL;
         }
     } else if (r.type == RNG_REQ_SWEEP) {
-        if (r.L < 4 || r.L % 2 || r.L > 16384 || r.kind < RNG_LCG32 || r.kind >= RNG_MT19937_SHARED) {
+        if (r.L < 4 || r.L % 2 || r.L > 16384 || r.kind < RNG_LCG32 || r.kind >= kNumKinds ||
+            r.kind == RNG_MT19937_SHARED) {
             set_error("rng_server_submit: bad sweep request");
             return RNG_EINVAL;
         }

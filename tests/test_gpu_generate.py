@@ -9,7 +9,7 @@ import oracle as O
 pytestmark = pytest.mark.gpu
 
 SEED = 0x0123456789ABCDEF
-THREAD_KINDS = [O.LCG32, O.LCG64, O.MWC, O.XORWOW, O.PHILOX4X32_10, O.XS1024W]
+THREAD_KINDS = [O.LCG32, O.LCG64, O.MWC, O.XORWOW, O.PHILOX4X32_10, O.XS1024W, O.PHILOX4X32_7]
 ALL_KINDS = THREAD_KINDS + [O.MT19937_SHARED]
 NORMAL_TOL = 2e-6  # absolute, for float32 Box-Muller against the double oracle
 
@@ -130,13 +130,14 @@ def test_consume_in_register_modes(R, torch_cuda, kind):
     assert np.all(np.abs(gz - z.sum(axis=1)) <= tol)
 
 
+@pytest.mark.parametrize("kind", [O.PHILOX4X32_10, O.PHILOX4X32_7])
 @pytest.mark.parametrize("layout", [0, 2])
 @pytest.mark.parametrize("out", ["u32", "f32", "normal"])
-def test_philox_block_aligned_and_misaligned(R, torch_cuda, layout, out):
+def test_philox_block_aligned_and_misaligned(R, torch_cuda, kind, layout, out):
     n = 300
-    o = O.generate(O.PHILOX4X32_10, SEED, n, 2 + 96 + 96)
+    o = O.generate(kind, SEED, n, 2 + 96 + 96)
     for Ks in ([96, 96], [2, 96, 96]):  # block-aligned calls, then misaligned ones
-        g = run_gpu(R, torch_cuda, O.PHILOX4X32_10, n, Ks, layout=layout, out=out)
+        g = run_gpu(R, torch_cuda, kind, n, Ks, layout=layout, out=out)
         start = 0
         for K, a in zip(Ks, g):
             ref = o[:, start:start + K]
@@ -183,7 +184,7 @@ def test_consecutive_calls_continue_the_streams(R, torch_cuda, kind):
     assert np.array_equal(np.concatenate(g, axis=1), o)
 
 
-@pytest.mark.parametrize("kind", [O.LCG32, O.LCG64, O.MWC, O.XORWOW, O.PHILOX4X32_10, O.XS1024W])
+@pytest.mark.parametrize("kind", [O.LCG32, O.LCG64, O.MWC, O.XORWOW, O.PHILOX4X32_10, O.XS1024W, O.PHILOX4X32_7])
 @pytest.mark.parametrize("t", [1, 1003, 2**33 + 7])
 def test_skipahead(R, torch_cuda, kind, t):
     n = 256 if kind != O.MWC else 64
@@ -218,6 +219,28 @@ def test_xs1024w_substream_seeding(R, torch_cuda):
     g = run_gpu(R, torch_cuda, O.XS1024W, n, [K], flags=O.SEED_SUBSTREAM)[0]
     o = O.generate(O.XS1024W, SEED, n, K, flags=O.SEED_SUBSTREAM)
     assert np.array_equal(g, o)
+
+
+@pytest.mark.parametrize("kind", [O.PHILOX4X32_10, O.PHILOX4X32_7])
+def test_philox_intrinsic_keys(R, torch_cuda, kind):
+    # Sec. 7: key = (instance number, run word); shards and launch splits
+    # name the same streams
+    n, K = 5000, 45
+    o = O.generate(kind, SEED, n, K, flags=O.PHILOX_INTRINSIC_KEY)
+    g = run_gpu(R, torch_cuda, kind, n, [K], flags=O.PHILOX_INTRINSIC_KEY)[0]
+    assert np.array_equal(g, o)
+    b = run_gpu(R, torch_cuda, kind, n, [K], flags=O.PHILOX_INTRINSIC_KEY, shard=(1234, 3000))[0]
+    assert np.array_equal(b, o[1234:4234])
+    for out in ("f32", "normal"):
+        g = run_gpu(R, torch_cuda, kind, n, [44], flags=O.PHILOX_INTRINSIC_KEY, out=out)[0]
+        ref = as_f32_oracle(o[:, :44]) if out == "f32" else O.box_muller(o[:, :44])
+        assert np.abs(g - ref).max() <= (0 if out == "f32" else NORMAL_TOL)
+    with pytest.raises(R.RngError) as e:
+        R.rng_create(R.RNG_XORWOW, 64, R.RNG_PHILOX_INTRINSIC_KEY)
+    assert e.value.status == R.RNG_EUNSUPPORTED
+    with pytest.raises(R.RngError) as e:
+        R.rng_create_shard(kind, (1 << 32) + 64, 0, 64, R.RNG_PHILOX_INTRINSIC_KEY)
+    assert e.value.status == R.RNG_EINVAL
 
 
 def test_mwc_same_a(R, torch_cuda):

@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 
 SEED = 0x0123456789ABCDEF
 BETA_C = float(np.log(1 + np.sqrt(2)) / 2)
-KINDS = [O.LCG32, O.LCG64, O.MWC, O.XORWOW, O.PHILOX4X32_10, O.XS1024W]
+KINDS = [O.LCG32, O.LCG64, O.MWC, O.XORWOW, O.PHILOX4X32_10, O.XS1024W, O.PHILOX4X32_7]
 
 
 @pytest.fixture(scope="module")
@@ -72,11 +72,32 @@ def test_multispin_other_G(R):
 
 
 @pytest.mark.parametrize("flags,kind", [(O.SEED_LEAPFROG, O.LCG32), (O.SEED_SUBSTREAM, O.XS1024W),
-                                        (O.MWC_SAME_A, O.MWC)])
+                                        (O.MWC_SAME_A, O.MWC), (O.PHILOX_INTRINSIC_KEY, O.PHILOX4X32_10),
+                                        (O.PHILOX_INTRINSIC_KEY, O.PHILOX4X32_7)])
 def test_seeding_flags(R, flags, kind):
     ref, _, _ = O.ising_run(64, 0.4, kind, SEED, 30, flags=flags)
     spins, _ = gpu_run(R, 64, 0.4, kind, 30, flags=flags)
     assert np.array_equal(spins, ref)
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+def test_intrinsic_philox_keys_L1024(R, layout):
+    # Sec. 7: key = (site-pair number, run word), counter = sweep number
+    # (two sites per stream: a sweep draws exactly one 4-word block)
+    flags = O.PHILOX_INTRINSIC_KEY
+    ref, acc, nm = O.ising_run(1024, BETA_C, O.PHILOX4X32_7, SEED, 100, flags=flags, measure_every=20)
+    spins, obs = gpu_run(R, 1024, BETA_C, O.PHILOX4X32_7, 100, layout=layout, flags=flags, measure_every=20)
+    assert np.array_equal(spins, ref)
+    assert obs["acc"] == acc.tolist() and obs["n_meas"] == nm
+    # the keys take the seed's low half only: from the same start, a seed
+    # that differs above bit 31 gives the same run
+    h = R.ising_create(1024, BETA_C, layout, O.PHILOX4X32_7, flags, SEED ^ (0xABCD << 40), 2)
+    try:
+        R.ising_set_spins(h, O.ising_init_spins(1024, SEED))
+        R.ising_sweep(h, 100)
+        assert np.array_equal(R.ising_get_spins(h), ref)
+    finally:
+        R.ising_destroy(h)
 
 
 def test_degenerate_temperatures(R):

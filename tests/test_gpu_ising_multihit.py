@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 SEED = 0x0123456789ABCDEF
 BETA_C = float(np.log(1 + np.sqrt(2)) / 2)
-KINDS = [O.LCG32, O.LCG64, O.MWC, O.XORWOW, O.PHILOX4X32_10, O.XS1024W]
+KINDS = [O.LCG32, O.LCG64, O.MWC, O.XORWOW, O.PHILOX4X32_10, O.XS1024W, O.PHILOX4X32_7]
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
@@ -64,6 +64,19 @@ def test_L64_strip_counts_and_hits(R, n_strips, k):
 def test_L1024_bit_exact(R, kind, layout, n_strips):
     ref, acc, nm = O.ising_run_multihit(1024, BETA_C, kind, SEED, 2, k=5, n_strips=n_strips, measure_every=1)
     spins, obs = gpu_multihit(R, 1024, BETA_C, kind, 2, k=5, n_strips=n_strips, layout=layout, measure_every=1)
+    assert np.array_equal(spins, ref)
+    assert obs["acc"] == acc.tolist() and obs["n_meas"] == nm
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+def test_k2_intrinsic_philox7_L1024(R, layout):
+    # the k = 2 configuration of Sec. 7 with Philox4x32-7 and intrinsic keys:
+    # a strip phase of two sweeps consumes two whole 4-word blocks per stream
+    flags = O.PHILOX_INTRINSIC_KEY
+    ref, acc, nm = O.ising_run_multihit(1024, BETA_C, O.PHILOX4X32_7, SEED, 3, k=2, n_strips=256, flags=flags,
+                                        measure_every=1)
+    spins, obs = gpu_multihit(R, 1024, BETA_C, O.PHILOX4X32_7, 3, k=2, n_strips=256, layout=layout, flags=flags,
+                              measure_every=1)
     assert np.array_equal(spins, ref)
     assert obs["acc"] == acc.tolist() and obs["n_meas"] == nm
 

@@ -56,10 +56,11 @@ def measure(R, L, beta, kind, flags=0, layout=0, equil=2000, bins=40, per_bin=25
     return (e_b.mean(), e_b.std(ddof=1) / np.sqrt(bins)), (c_b.mean(), c_b.std(ddof=1) / np.sqrt(bins))
 
 
-@pytest.mark.parametrize("kind", [3, 5, 4])  # xorwow, the paper's generator, Philox
+# xorwow, the paper's generator, Philox4x32-10, Philox4x32-7 with intrinsic keys
+@pytest.mark.parametrize("kind,flags", [(3, 0), (5, 0), (4, 0), (7, 8)])
 @pytest.mark.parametrize("L,beta", [(64, 0.4), (128, 0.4)])
-def test_energy_and_specific_heat_match_exact(R, kind, L, beta):
-    (e, de), (cv, dcv) = measure(R, L, beta, kind)
+def test_energy_and_specific_heat_match_exact(R, kind, flags, L, beta):
+    (e, de), (cv, dcv) = measure(R, L, beta, kind, flags=flags)
     e_ex, cv_ex = exact(L, beta)
     print(f"L={L} beta={beta} kind={kind}: e={e:.6f}({de:.1e}) exact {e_ex:.6f} "
           f"Delta_rel={(e - e_ex) / de:+.2f}; C_V={cv:.5f}({dcv:.1e}) exact {cv_ex:.5f} "
