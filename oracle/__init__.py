@@ -24,11 +24,13 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
-LCG32, LCG64, MWC, XORWOW, PHILOX4X32_10, XS1024W, MT19937_SHARED, PHILOX4X32_7 = range(8)
+LCG32, LCG64, MWC, XORWOW, PHILOX4X32_10, XS1024W, MT19937_SHARED, PHILOX4X32_7, LFIB521, LFIB1279 = range(10)
 SEED_RANDOM, SEED_LEAPFROG, SEED_SUBSTREAM, MWC_SAME_A, PHILOX_INTRINSIC_KEY = 0, 1, 2, 4, 8
 KIND_NAMES = {LCG32: "lcg32", LCG64: "lcg64", MWC: "mwc", XORWOW: "xorwow",
               PHILOX4X32_10: "philox4x32_10", XS1024W: "xs1024w",
-              MT19937_SHARED: "mt19937_shared", PHILOX4X32_7: "philox4x32_7"}
+              MT19937_SHARED: "mt19937_shared", PHILOX4X32_7: "philox4x32_7", LFIB521: "lfib521",
+              LFIB1279: "lfib1279"}
+LFIB_LAGS = {LFIB521: (521, 353), LFIB1279: (1279, 861)}
 
 _lock = threading.Lock()
 _lib = None
@@ -70,6 +72,7 @@ def lib():
                 "orc_ising_energy": (None, [u32, p, p, p]),
                 "orc_ising_run": (i32, [u32, dbl, i32, u32, u64, u32, u64, u32, i32, p, p, p]),
                 "orc_mt19937_raw": (None, [u32, u64, p]),
+                "orc_lfib_raw": (i32, [u32, u32, i32, p, u64, p]),
                 "orc_ising_run_multihit": (i32, [u32, dbl, i32, u32, u64, u32, u32, u32, u64, u32, i32, p, p, p]),
             }
             for name, (res, args) in sig.items():
@@ -225,6 +228,15 @@ def ising_run_multihit(L: int, beta: float, kind: int, seed: int, n_rounds: int,
                                         measure_every, philox_rounds, _ptr(s), _ptr(acc), ctypes.byref(nm)),
            "ising_run_multihit")
     return s, acc, nm.value
+
+
+def lfib_raw(r: int, s: int, bits: int, seeds, K: int) -> np.ndarray:
+    """K outputs of x_n = x_(n-r) + x_(n-s) mod 2^bits from seeds x_(-r) .. x_(-1)."""
+    sd = np.ascontiguousarray(seeds, dtype=np.uint32)
+    assert sd.shape == (r,)
+    out = np.zeros(K, dtype=np.uint32)
+    _check(lib().orc_lfib_raw(r, s, bits, _ptr(sd), K, _ptr(out)), "lfib_raw")
+    return out
 
 
 def mt19937_raw(seed32: int, K: int) -> np.ndarray:

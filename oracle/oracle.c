@@ -29,7 +29,8 @@
 
 typedef unsigned __int128 u128;
 
-enum { K_LCG32 = 0, K_LCG64 = 1, K_MWC = 2, K_XORWOW = 3, K_PHILOX = 4, K_XS1024W = 5, K_MT = 6, K_PHILOX7 = 7 };
+enum { K_LCG32 = 0, K_LCG64 = 1, K_MWC = 2, K_XORWOW = 3, K_PHILOX = 4, K_XS1024W = 5, K_MT = 6, K_PHILOX7 = 7,
+       K_LFIB521 = 8, K_LFIB1279 = 9 };
 enum { F_LEAPFROG = 1, F_SUBSTREAM = 2, F_MWC_SAME_A = 4, F_PHILOX_INTRINSIC = 8 };
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_EUNSUPPORTED = 3 };
 
@@ -380,6 +381,65 @@ static uint32_t mt_next(mt_t *g)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Additive lagged Fibonacci generators, Sec. 4, Eq. (used_fibonacci):       */
+/* u_n = u_(n-r) + u_(n-s) (mod 1) with (r, s) = (521, 353) or (1279, 861).  */
+/* Written on the 32-bit words x_n = 2^32 u_n, where the same recurrence is  */
+/* x_n = x_(n-r) + x_(n-s) mod 2^32 (m = 2^32, the modulus the section      */
+/* fixes).  The ring `hist` holds the last r values: x_m sits in slot m mod  */
+/* r.  The generic width `bits` (1..32) serves the small-lag period checks.  */
+/* ------------------------------------------------------------------------ */
+typedef struct { uint32_t r, s, mask; uint64_t n; uint32_t *hist; } lfib_t;
+
+/* hist[j] = x_(j-r) for j < r: the r seed values, oldest first */
+static int lfib_init(lfib_t *g, uint32_t r, uint32_t s, int bits, const uint32_t *seeds)
+{
+    g->r = r;
+    g->s = s;
+    g->mask = bits >= 32 ? 0xffffffffu : ((1u << bits) - 1u);
+    g->n = 0;
+    g->hist = (uint32_t *)malloc(r * sizeof(uint32_t));
+    if (!g->hist) return ORC_ENOMEM;
+    for (uint32_t j = 0; j < r; j++) g->hist[j] = seeds[j] & g->mask;
+    return ORC_OK;
+}
+
+static uint32_t lfib_next(lfib_t *g)
+{
+    uint32_t old_r = g->hist[g->n % g->r];                   /* x_(n-r) */
+    uint32_t old_s = g->hist[(g->n + g->r - g->s) % g->r];   /* x_(n-s) */
+    uint32_t x = (old_r + old_s) & g->mask;
+    g->hist[g->n % g->r] = x;
+    g->n++;
+    return x;
+}
+
+/* Seeds of generator i ("seed the ring buffers ... with an independent RNG",
+ * Sec. 4): x_(j-r) = low half of w_(r i + j); if all r are even, the low bit
+ * of the first is set (an all-even start never reaches an odd value and
+ * misses the full period 2^31 (2^r - 1)). */
+static void lfib_seeds(uint64_t seed, uint32_t r, uint64_t i, uint32_t *out)
+{
+    uint32_t odd = 0;
+    for (uint32_t j = 0; j < r; j++) {
+        out[j] = (uint32_t)orc_seed_word(seed, (uint64_t)r * i + j);
+        odd |= out[j] & 1u;
+    }
+    if (!odd) out[0] |= 1u;
+}
+
+/* Generic small-width form for the tests: K outputs of the (r, s) generator
+ * on `bits`-bit words from the given r seed values. */
+int orc_lfib_raw(uint32_t r, uint32_t s, int bits, const uint32_t *seeds, uint64_t K, uint32_t *out)
+{
+    if (r < 2 || s < 1 || s >= r || bits < 1 || bits > 32) return ORC_EINVAL;
+    lfib_t g;
+    if (lfib_init(&g, r, s, bits, seeds)) return ORC_ENOMEM;
+    for (uint64_t k = 0; k < K; k++) out[k] = lfib_next(&g);
+    free(g.hist);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Bit matrices over GF(2) (Sec. 6, Eq. threeshift): states are row vectors  */
 /* and x' = x M, so row i of M is the image of the unit vector e_i.          */
 /* ------------------------------------------------------------------------ */
@@ -561,6 +621,8 @@ typedef struct {
     uint64_t pos;         /* draws consumed */
     /* MT */
     mt_t *mt;
+    /* lagged Fibonacci */
+    lfib_t lf;
 } inst_t;
 
 /* Seeds per-thread instance i of n (not XS1024W, whose unit is a warp). */
@@ -646,11 +708,27 @@ static int inst_init(inst_t *s, int kind, uint32_t flags, uint64_t seed, uint64_
         mt_seed(s->mt, (uint32_t)orc_seed_word(seed, i));
         return ORC_OK;
     }
+    case K_LFIB521:
+    case K_LFIB1279: {
+        uint32_t r = kind == K_LFIB521 ? 521 : 1279, sl = kind == K_LFIB521 ? 353 : 861;
+        uint32_t *seeds = (uint32_t *)malloc(r * sizeof(uint32_t));
+        if (!seeds) return ORC_ENOMEM;
+        lfib_seeds(seed, r, i, seeds);
+        int st = lfib_init(&s->lf, r, sl, 32, seeds);
+        free(seeds);
+        return st;
+    }
     }
     return ORC_EINVAL;
 }
 
-static void inst_free(inst_t *s) { free(s->mt); s->mt = NULL; }
+static void inst_free(inst_t *s)
+{
+    free(s->mt);
+    s->mt = NULL;
+    free(s->lf.hist);
+    s->lf.hist = NULL;
+}
 
 static uint32_t inst_next(inst_t *s, int philox_rounds)
 {
@@ -676,6 +754,9 @@ static uint32_t inst_next(inst_t *s, int philox_rounds)
     }
     case K_MT:
         return mt_next(s->mt);
+    case K_LFIB521:
+    case K_LFIB1279:
+        return lfib_next(&s->lf);
     }
     return 0;
 }
@@ -770,7 +851,7 @@ static int xs_warp_jump(uint32_t *x, uint64_t t)
 
 static int check_kind_flags(int kind, uint32_t flags, uint64_t n)
 {
-    if (kind < 0 || kind > K_PHILOX7 || n == 0) return ORC_EINVAL;
+    if (kind < 0 || kind > K_LFIB1279 || n == 0) return ORC_EINVAL;
     if ((flags & F_PHILOX_INTRINSIC) && kind != K_PHILOX && kind != K_PHILOX7) return ORC_EUNSUPPORTED;
     if ((flags & F_PHILOX_INTRINSIC) && n > (1ULL << 32)) return ORC_EINVAL;  /* a 32-bit key word */
     if ((flags & F_LEAPFROG) && kind != K_LCG32 && kind != K_LCG64) return ORC_EUNSUPPORTED;
@@ -793,7 +874,7 @@ int orc_generate(int kind, uint32_t flags, uint64_t seed, uint64_t n, uint64_t s
     int st = check_kind_flags(kind, flags, n);
     if (st) return st;
     if (i_lo > i_hi || i_hi > n) return ORC_EINVAL;
-    if (kind == K_MT && jump && skip) return ORC_EUNSUPPORTED;
+    if ((kind == K_MT || kind == K_LFIB521 || kind == K_LFIB1279) && jump && skip) return ORC_EUNSUPPORTED;
     if (kind == K_XS1024W) {
         for (uint64_t j = i_lo / 32; j * 32 < i_hi; j++) {
             uint32_t x[XS_WORDS], o[XS_WORDS];
@@ -914,7 +995,9 @@ int orc_ising_run(uint32_t L, double beta, int kind, uint32_t flags, uint64_t se
                   uint64_t n_sweeps, uint32_t measure_every, int philox_rounds, int8_t *s,
                   int64_t acc[4], uint64_t *n_meas)
 {
-    if (L < 2 || L % 2 || G == 0 || ((uint64_t)L * L / 2) % G || kind == K_MT) return ORC_EINVAL;
+    if (L < 2 || L % 2 || G == 0 || ((uint64_t)L * L / 2) % G || kind == K_MT || kind == K_LFIB521 ||
+        kind == K_LFIB1279)
+        return ORC_EINVAL;
     uint64_t nstreams = (uint64_t)L * L / 2 / G;
     uint64_t n = kind == K_XS1024W ? (nstreams + 31) / 32 * 32 : nstreams;
     int st = check_kind_flags(kind, flags, n);
@@ -990,7 +1073,8 @@ int orc_ising_run_multihit(uint32_t L, double beta, int kind, uint32_t flags, ui
                            uint32_t n_strips, uint32_t k_hits, uint64_t n_rounds, uint32_t measure_every,
                            int philox_rounds, int8_t *s, int64_t acc[4], uint64_t *n_meas)
 {
-    if (L < 2 || L % 2 || G == 0 || (L / 2) % G || kind == K_MT || n_strips < 2 || n_strips % 2 ||
+    if (L < 2 || L % 2 || G == 0 || (L / 2) % G || kind == K_MT || kind == K_LFIB521 || kind == K_LFIB1279 ||
+        n_strips < 2 || n_strips % 2 ||
         L % n_strips || k_hits == 0)
         return ORC_EINVAL;
     uint64_t nstreams = (uint64_t)L * L / 2 / G;

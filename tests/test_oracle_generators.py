@@ -389,6 +389,89 @@ def test_philox_intrinsic_keys_do_not_depend_on_the_instance_count():
         O.generate(O.PHILOX4X32_7, SEED, (1 << 32) + 1, 4, flags=O.PHILOX_INTRINSIC_KEY, i_lo=0, i_hi=1)
 
 
+# ---------------------------------------------------- lagged Fibonacci (Sec. 4)
+def _gf2_mulmod(a, b, P, deg):
+    r = 0
+    while b:
+        if b & 1:
+            r ^= a
+        b >>= 1
+        a <<= 1
+        if (a >> deg) & 1:
+            a ^= P
+    return r
+
+
+@pytest.mark.parametrize("lags", [(521, 353), (1279, 861)])
+def test_lfib_trinomials_are_primitive(golden, lags):
+    # x^r + x^s + 1 over GF(2): with r prime, Rabin's test reduces to
+    # x^(2^r) = x (mod P) and P having no root in GF(2); as 2^r - 1 is then
+    # a (Mersenne) prime, irreducible means primitive, so the low bits have
+    # period 2^r - 1 and the words 2^31 (2^r - 1) (Brent's bound, Sec. 4)
+    assert list(lags) in golden["lfib"]["lags"]
+    r, s = lags
+    P = (1 << r) | (1 << s) | 1
+    x = 2
+    for _ in range(r):
+        x = _gf2_mulmod(x, x, P, r)
+    assert x == 2
+    assert P & 1 and bin(P).count("1") % 2 == 1  # P(0) = P(1) = 1
+
+
+@pytest.mark.parametrize("kind", [O.LFIB521, O.LFIB1279])
+def test_lfib_low_bits_follow_the_papers_lags(kind):
+    # Berlekamp-Massey on the low bit of the oracle's words must return the
+    # trinomial 1 + x^s + x^r of the lags printed in Sec. 4: a wrong lag, a
+    # wrong ring index or a subtraction for the addition all fail here
+    r, s = O.LFIB_LAGS[kind]
+    out = O.generate(kind, SEED, 3, 3 * r, i_lo=2, i_hi=3)[0]
+    C, L = _bm_gf2([int(v) & 1 for v in out])
+    assert L == r
+    assert C == (1 | (1 << s) | (1 << r))
+
+
+def _period(seq, r):
+    """Least P > 0 with the r-word state after P outputs equal to the start."""
+    start = seq[:r]
+    for P in range(1, len(seq) - r):
+        if seq[P] == start[0] and np.array_equal(seq[P:P + r], start):
+            return P
+    return None
+
+
+@pytest.mark.parametrize("r,s", [(5, 2), (5, 3), (7, 3), (7, 1)])
+@pytest.mark.parametrize("bits", [1, 3, 6])
+def test_lfib_small_lag_periods(r, s, bits):
+    # additive lagged Fibonacci mod 2^m on a primitive trinomial: period
+    # 2^(m-1) (2^r - 1) when a seed is odd (Sec. 4, after Brent); the ring
+    # arithmetic of the oracle is the one the production lags use
+    rng = np.random.default_rng(r * 100 + s * 10 + bits)
+    seeds = rng.integers(0, 1 << bits, r, dtype=np.uint32)
+    seeds[0] |= 1
+    expect = (1 << (bits - 1)) * ((1 << r) - 1)
+    seq = O.lfib_raw(r, s, bits, seeds, 2 * expect + r + 1)
+    assert _period(seq, r) == expect
+    if bits > 1:  # all seeds even: the words never leave the even residues
+        ev = O.lfib_raw(r, s, bits, seeds & ~np.uint32(1), 2 * expect + r + 1)
+        assert np.all(ev & 1 == 0)
+        assert _period(ev, r) <= expect // 2
+
+
+@pytest.mark.parametrize("kind", [O.LFIB521, O.LFIB1279])
+def test_lfib_streams_start_from_their_seed_words(kind):
+    r, s = O.LFIB_LAGS[kind]
+    i = 5
+    seeds = np.array([O.seed_word(SEED, r * i + j) & 0xFFFFFFFF for j in range(r)], dtype=np.uint32)
+    if not np.any(seeds & 1):
+        seeds[0] |= 1
+    got = O.generate(kind, SEED, 8, 2000, i_lo=i, i_hi=i + 1)[0]
+    assert np.array_equal(got, O.lfib_raw(r, s, 32, seeds, 2000))
+    # the first outputs are the recurrence on the seeds themselves
+    assert got[0] == (int(seeds[0]) + int(seeds[r - s])) & 0xFFFFFFFF
+    with pytest.raises(O.OracleError):
+        O.generate(kind, SEED, 8, 4, skip=10, jump=True)  # no skip-ahead for the ring generators
+
+
 # ----------------------------------------------------------------------- MT
 def test_mt19937_cxx_standard_value():
     # The C++ standard ([rand.predef]) fixes the 10000th output of

@@ -9,7 +9,8 @@ import pytest
 import oracle as O
 
 SEED = 0x0123456789ABCDEF
-KINDS = [O.LCG32, O.LCG64, O.MWC, O.XORWOW, O.PHILOX4X32_10, O.XS1024W, O.MT19937_SHARED]
+KINDS = [O.LCG32, O.LCG64, O.MWC, O.XORWOW, O.PHILOX4X32_10, O.XS1024W, O.MT19937_SHARED, O.PHILOX4X32_7,
+         O.LFIB521, O.LFIB1279]
 
 
 def chi2_cells(cells, ncells):
@@ -23,7 +24,7 @@ def bound(dof, sig=7.0):
 
 
 def streams(kind):
-    if kind == O.MT19937_SHARED:
+    if kind in (O.MT19937_SHARED, O.LFIB521, O.LFIB1279):  # block-shared states: few long streams
         return O.generate(kind, SEED, 4, 1 << 18)
     return O.generate(kind, SEED, 1024, 1024)
 
