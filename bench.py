@@ -3,9 +3,10 @@
 
 Default (N=1): the bulk workload -- 2^20 resident instances of every
 generator kind, 1024 draws each (2^30 outputs per call; the block-shared
-MT19937 as 32768 warp-shared generators x 2^15 draws), written to HBM as u32, exact
+MT19937 and lagged Fibonacci generators as 32768 warp-shared generators x
+2^15 draws), written to HBM as u32, exact
 uniform f32 and Box-Muller normals, and consumed in registers (u32 XOR
-reduce).  One step = those 32 calls (eight kinds x four forms).  `value` = outputs of all ranks /
+reduce).  One step = those 40 calls (ten kinds x four forms).  `value` = outputs of all ranks /
 device time (Gnum/s).  Extra keys report the Ising sweep (flips/ns) and
 the other workloads.
 
@@ -40,8 +41,11 @@ FORMS = ["u32", "f32", "normal", "u32_xor"]
 # state bytes moved per instance and call: load + store of the state, plus
 # the MWC multiplier read; Philox only reads its key (the position is the
 # handle's counter)
-STATE_TRAFFIC = {0: 8, 1: 16, 2: 20, 3: 48, 4: 8, 5: 8, 6: 2 * 624 * 4, 7: 8}
-N_KINDS = 8  # LCG32, LCG64, MWC, XORWOW, Philox4x32-10, XS1024W, MT19937, Philox4x32-7
+STATE_TRAFFIC = {0: 8, 1: 16, 2: 20, 3: 48, 4: 8, 5: 8, 6: 2 * 624 * 4, 7: 8, 8: 2 * 521 * 4, 9: 2 * 1279 * 4}
+# LCG32, LCG64, MWC, XORWOW, Philox4x32-10, XS1024W, MT19937, Philox4x32-7,
+# lagged Fibonacci (521, 353) and (1279, 861)
+N_KINDS = 10
+SHARED = (6, 8, 9)  # block-shared kinds: one state per warp, 2^15 generators x 2^15 draws
 
 
 def shard_range(rank: int, world: int, per_rank: int):
@@ -152,7 +156,7 @@ class Bulk:
         self.R, self.torch = R, torch
         self.handles = {}
         for kind in range(N_KINDS):
-            per = MT_GENS if kind == R.RNG_MT19937_SHARED else N_INST
+            per = MT_GENS if kind in SHARED else N_INST
             first, n, total = shard_range(rank, world, per)
             h = R.rng_create_shard(kind, total, first, n, 0)
             R.rng_seed(h, SEED)
@@ -166,8 +170,8 @@ class Bulk:
         res = []
         for kind in range(N_KINDS):
             h, n = self.handles[kind]
-            K = MT_DRAWS if kind == R.RNG_MT19937_SHARED else K_DRAWS
-            lay = R.RNG_INSTANCE_MAJOR if kind == R.RNG_MT19937_SHARED else R.RNG_STEP_MAJOR
+            K = MT_DRAWS if kind in SHARED else K_DRAWS
+            lay = R.RNG_INSTANCE_MAJOR if kind in SHARED else R.RNG_STEP_MAJOR
             for form in FORMS:
                 res.append((f"{R.KIND_NAMES[kind]}/{form}", kind, form, h, n, K, lay))
         return res
@@ -376,11 +380,12 @@ def run_gpu(args):
             "dtype": "u32",
             "data": "synthetic",
             "config": {
-                "workload": "bulk generation: 2^20 resident instances x 1024 draws per call (MT19937: 32768 "
-                            "warp-shared generators x 2^15), 7 generators x {u32, f32, normal} written to HBM + "
-                            "u32 consumed in registers (XOR reduce); 32 calls per step",
+                "workload": "bulk generation: 2^20 resident instances x 1024 draws per call (MT19937 and the "
+                            "lagged Fibonacci (521, 353), (1279, 861): 32768 warp-shared generators x 2^15), "
+                            "10 generators x {u32, f32, normal} written to HBM + u32 consumed in registers "
+                            "(XOR reduce); 40 calls per step",
                 "instances_per_gpu": N_INST, "draws_per_call": K_DRAWS, "outputs_per_step_per_gpu":
-                    outputs_per_step_rank, "layout": "step-major (MT19937: instance-major)",
+                    outputs_per_step_rank, "layout": "step-major (block-shared kinds: instance-major)",
                 "l2": "no flush: every write call streams 4 GiB (> 129 MB L2)", "seed": hex(SEED),
                 "parallelism": f"instance shards x{world}",
             },
@@ -706,7 +711,7 @@ def oracle_sample(per_form: int):
     total = 0
     t0 = time.perf_counter()
     for kind in range(N_KINDS):
-        if kind == O.MT19937_SHARED:
+        if kind in SHARED:
             n, K = 4, per_form // 4
         else:
             n, K = 256, per_form // 256

@@ -61,8 +61,11 @@ enum {
     RNG_PHILOX4X32_10 = 4,  /* Sec. 7: counter-based Philox4x32, 10 rounds */
     RNG_XS1024W = 5,        /* Sec. 6, Listing 1: the paper's 1024-bit warp-shared xorshift plus Weyl */
     RNG_MT19937_SHARED = 6, /* Sec. 5: MT19937, one block-shared state per generator */
-    RNG_PHILOX4X32_7 = 7    /* Sec. 7: Philox4x32 with 7 rounds (the fewest the Philox authors found
+    RNG_PHILOX4X32_7 = 7,   /* Sec. 7: Philox4x32 with 7 rounds (the fewest the Philox authors found
                                Crush-resistant); streams laid out as RNG_PHILOX4X32_10 */
+    RNG_LFIB521 = 8,        /* Sec. 4, Eq. (used_fibonacci): additive lagged Fibonacci, lags (521, 353),
+                               one ring shared by a warp; x_n = x_(n-521) + x_(n-353) mod 2^32 */
+    RNG_LFIB1279 = 9        /* Sec. 4: the same with lags (1279, 861) */
 };
 
 /* Seeding flags (rng_create). */
@@ -98,7 +101,8 @@ enum {
  * (Sec. 1: one instance per thread; for RNG_XS1024W an instance is one lane
  * of a warp-shared 1024-bit state, Sec. 6, so n_instances must be a multiple
  * of 32; for RNG_MT19937_SHARED an instance is one MT19937 generator whose
- * 624-word state a thread block shares, Sec. 5).  `flags` is an OR of the
+ * 624-word state a thread block shares, Sec. 5; for RNG_LFIB521/1279 one
+ * lagged Fibonacci generator whose r-word ring a warp shares, Sec. 4).  `flags` is an OR of the
  * RNG_SEED_* / RNG_MWC_SAME_A / RNG_PHILOX_INTRINSIC_KEY values valid for
  * the kind, else RNG_EUNSUPPORTED.  The instances are unseeded until rng_seed.
  * RNG_MWC without RNG_MWC_SAME_A needs n_instances distinct multipliers
@@ -123,14 +127,17 @@ int rng_destroy(rng_t h);
  * low32(w_i), c = high32(w_i) mod a_i; XORWOW (x,y),(z,w),(v,d) from
  * w_3i..w_3i+2; Philox key = w_i, counter = block index; XS1024W lane l of
  * warp j = low32(w_(32j+l)), or with SUBSTREAM base words from w_0..w_15 and
- * warp j advanced by j 2^137 steps; MT generator g seeded with low32(w_g).
- * Resets the draw position to 0. */
+ * warp j advanced by j 2^137 steps; MT generator g seeded with low32(w_g);
+ * lagged Fibonacci generator g (lags r, s) starts from x_(j-r) =
+ * low32(w_(r g + j)), j < r, with the low bit of x_(-r) set if all r words
+ * are even.  Resets the draw position to 0. */
 int rng_seed(rng_t h, uint64_t seed);
 
 /* Advances every instance by n draws without producing them (Sec. 2 Eq. (2)
  * for LCGs; v <- v a^n mod (a 2^32 - 1) for MWC; the n-th power of the
  * GF(2) transition matrix for XORWOW and XS1024W, Sec. 6; a counter add for
- * Philox, Sec. 7).  RNG_MT19937_SHARED: RNG_EUNSUPPORTED.  Allocates and
+ * Philox, Sec. 7).  Block-shared kinds (RNG_MT19937_SHARED, RNG_LFIB521,
+ * RNG_LFIB1279): RNG_EUNSUPPORTED.  Allocates and
  * frees device scratch on the handle's stream for the matrix kinds. */
 int rng_skipahead(rng_t h, uint64_t n);
 
@@ -147,7 +154,7 @@ int rng_skipahead(rng_t h, uint64_t n);
  *                 caller's and is not touched.
  *  Scratch: one file-scope device array of 384 KiB (three 1024 x 1024-bit
  *  matrices), held by every GPU that loads the library until the process
- *  exits.  States wider than 1024 bits (RNG_MT19937_SHARED) are rejected
+ *  exits.  States wider than 1024 bits (RNG_MT19937_SHARED, RNG_LFIB*) are rejected
  *  with RNG_EINVAL; kinds that skip without matrices (LCGs, MWC, Philox)
  *  with RNG_EUNSUPPORTED.  The first call on a device looks up the array's
  *  device address with that device current (make it before any stream
@@ -197,8 +204,8 @@ int rng_mwc_multipliers(uint64_t first, uint64_t count, uint32_t *host_out);
  * sites are numbered q = y (L/2) + (x >> 1); stream s owns q in
  * [sG, (s+1)G) of both colours, giving L^2/(2G) streams of generator
  * `rng_kind` seeded by rng_seed(seed) semantics with `rng_flags`
- * (RNG_MT19937_SHARED: RNG_EUNSUPPORTED; the paper ran no Ising test with
- * it, Sec. 5).  Initial spins: site j = y L + x is +1 iff bit j % 64 of
+ * (block-shared kinds -- RNG_MT19937_SHARED, RNG_LFIB521, RNG_LFIB1279 --
+ * give no per-site streams: RNG_EUNSUPPORTED).  Initial spins: site j = y L + x is +1 iff bit j % 64 of
  * SplitMix64 word j / 64 of (seed XOR 0x5350494E) is set.  Requires L even,
  * 4 <= L <= 65536, G dividing L/2 (each stream's sites lie in one row), and
  * L % 64 == 0 for ISING_MULTISPIN32. */
@@ -323,7 +330,7 @@ enum { RNG_OUT_U32 = 0, RNG_OUT_F32 = 1, RNG_OUT_NORMAL = 2 };
 
 typedef struct {
     int32_t type;      /* RNG_REQ_DRAW or RNG_REQ_SWEEP */
-    int32_t kind;      /* generator kind, any but RNG_MT19937_SHARED */
+    int32_t kind;      /* generator kind, any per-thread kind (not a block-shared one) */
     uint64_t seed;     /* draw: stream-set seed; sweep: lattice seed */
     uint64_t offset;   /* draw: draws skipped in every instance of the set */
     uint64_t count;    /* draw: numbers returned (even for normals) */

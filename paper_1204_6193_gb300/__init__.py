@@ -17,14 +17,16 @@ LIB_PATH = os.path.join(_HERE, "_build", "librng_gb300.so")
 
 RNG_OK, RNG_EINVAL, RNG_ENOMEM, RNG_EUNSUPPORTED, RNG_ECUDA, RNG_ETIMEOUT, RNG_EBUSY = range(7)
 (RNG_LCG32, RNG_LCG64, RNG_MWC, RNG_XORWOW, RNG_PHILOX4X32_10, RNG_XS1024W,
- RNG_MT19937_SHARED, RNG_PHILOX4X32_7) = range(8)
+ RNG_MT19937_SHARED, RNG_PHILOX4X32_7, RNG_LFIB521, RNG_LFIB1279) = range(10)
 RNG_SEED_RANDOM, RNG_SEED_LEAPFROG, RNG_SEED_SUBSTREAM, RNG_MWC_SAME_A, RNG_PHILOX_INTRINSIC_KEY = 0, 1, 2, 4, 8
 RNG_STEP_MAJOR, RNG_INSTANCE_MAJOR, RNG_XOR_REDUCE = 0, 1, 2
 ISING_INT8, ISING_MULTISPIN32 = 0, 1
 
 KIND_NAMES = {RNG_LCG32: "lcg32", RNG_LCG64: "lcg64", RNG_MWC: "mwc", RNG_XORWOW: "xorwow",
               RNG_PHILOX4X32_10: "philox4x32_10", RNG_XS1024W: "xs1024w",
-              RNG_MT19937_SHARED: "mt19937_shared", RNG_PHILOX4X32_7: "philox4x32_7"}
+              RNG_MT19937_SHARED: "mt19937_shared", RNG_PHILOX4X32_7: "philox4x32_7",
+              RNG_LFIB521: "lfib521", RNG_LFIB1279: "lfib1279"}
+BLOCK_SHARED_KINDS = (RNG_MT19937_SHARED, RNG_LFIB521, RNG_LFIB1279)
 
 
 class RngError(RuntimeError):

@@ -517,6 +517,8 @@ int launch_generate(const GenState &g, void *d_out, uint64_t K, int out_kind, in
     case RNG_PHILOX4X32_7: return launch_kind<RNG_PHILOX4X32_7>(g, d_out, K, out_kind, layout, s);
     case RNG_XS1024W: return launch_kind<RNG_XS1024W>(g, d_out, K, out_kind, layout, s);
     case RNG_MT19937_SHARED: return launch_kind<RNG_MT19937_SHARED>(g, d_out, K, out_kind, layout, s);
+    case RNG_LFIB521:
+    case RNG_LFIB1279: return launch_generate_lfib(g, d_out, K, out_kind, layout, s);
     }
     set_error("launch_generate: unknown kind %d", g.kind);
     return RNG_EINVAL;

@@ -240,6 +240,8 @@ int launch_seed(GenState &g, uint64_t seed, cudaStream_t s)
         }
         break;
     case RNG_MT19937_SHARED: k_seed_mt<<<nb, kBlock, 0, s>>>(p, seed, g.first); break;
+    case RNG_LFIB521:
+    case RNG_LFIB1279: return launch_seed_lfib(g, seed, s);
     default: set_error("launch_seed: unknown kind %d", g.kind); return RNG_EINVAL;
     }
     RNGX_CHECK_CUDA(cudaGetLastError());
@@ -289,7 +291,9 @@ int launch_skipahead(GenState &g, uint64_t t, cudaStream_t s)
         RNGX_CHECK(st);
         break;
     }
-    default: set_error("rng_skipahead: not defined for the block-shared MT19937"); return RNG_EUNSUPPORTED;
+    default:
+        set_error("rng_skipahead: not defined for the block-shared generators (MT19937, lagged Fibonacci)");
+        return RNG_EUNSUPPORTED;
     }
     RNGX_CHECK_CUDA(cudaGetLastError());
     g.pos += t;

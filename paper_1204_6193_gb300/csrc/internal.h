@@ -11,7 +11,14 @@
 namespace rngx {
 
 constexpr int MT_N_WORDS = 624;  // MT19937 state words (Sec. 5: N = 624)
-constexpr int kNumKinds = RNG_PHILOX4X32_7 + 1;  // generator kinds 0 .. kNumKinds-1
+constexpr int kNumKinds = RNG_LFIB1279 + 1;  // generator kinds 0 .. kNumKinds-1
+
+// Block-shared generators: an instance is one generator whose state a
+// group of threads shares (no per-thread stream, no Ising consumer).
+constexpr bool is_block_shared(int kind)
+{
+    return kind == RNG_MT19937_SHARED || kind == RNG_LFIB521 || kind == RNG_LFIB1279;
+}
 
 // ------------------------------------------------------------- errors
 void set_error(const char *fmt, ...);
@@ -69,6 +76,8 @@ namespace rngx {
 int launch_generate(const GenState &g, void *d_out, uint64_t K, int out_kind, int layout, cudaStream_t s);
 int launch_seed(GenState &g, uint64_t seed, cudaStream_t s);
 int launch_skipahead(GenState &g, uint64_t t, cudaStream_t s);
+int launch_generate_lfib(const GenState &g, void *d_out, uint64_t K, int out_kind, int layout, cudaStream_t s);
+int launch_seed_lfib(GenState &g, uint64_t seed, cudaStream_t s);
 
 // Output kinds of the generation kernels.
 enum { OUT_U32 = 0, OUT_F32 = 1, OUT_NORMAL = 2 };

@@ -269,7 +269,7 @@ int lat_create(IsingLat &t, uint32_t L, double beta, int layout, int kind, uint3
         set_error("Ising: G (sites per stream per colour) must divide L/2");
         return RNG_EINVAL;
     }
-    if (kind == RNG_MT19937_SHARED || kind < RNG_LCG32 || kind >= kNumKinds) {
+    if (kind < RNG_LCG32 || kind >= kNumKinds || is_block_shared(kind)) {
         set_error("Ising: generator kind %d is not supported by the application test", kind);
         return RNG_EUNSUPPORTED;
     }

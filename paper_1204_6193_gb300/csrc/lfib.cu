@@ -1,0 +1,189 @@
+// lfib.cu -- the additive lagged Fibonacci generators of Sec. 4,
+// Eq. (used_fibonacci): u_n = u_(n-r) + u_(n-s) (mod 1), (r, s) = (521, 353)
+// and (1279, 861), run on the 32-bit words x_n = 2^32 u_n, where the
+// recurrence is x_n = x_(n-r) + x_(n-s) mod 2^32 and is exact.
+//
+// An instance is one generator whose state (the last r words) a group of
+// threads shares.  Here that group is one warp: the ring of r + s words
+// sits in shared memory and the warp computes s new words per step in
+// parallel (word n+j needs x_(n+j-r) and x_(n+j-s), both older than n for
+// j < s, Sec. 4).  With r + s slots the s new words never overwrite a word
+// another lane still reads in the same step, so a step needs no barrier
+// beyond the warp sync between steps.
+//
+// State in HBM: r words per generator, x_m in slot m mod r for the r most
+// recent m; the handle's position counts the words produced.
+#include "gen_device.cuh"
+#include "internal.h"
+
+namespace rngx {
+
+namespace {
+
+template <int R, int S>
+struct Lfib {
+    static constexpr int kRing = R + S;                                   // shared ring words
+    static constexpr int kWarps = kRing * 4 * 8 <= 40 * 1024 ? 8 : 4;     // generators per block
+    static constexpr int kBlock = 32 * kWarps;
+};
+
+// Seeds: x_(j-r) = low half of w_(r g + j) for global generator g; an
+// all-even ring gets its low bit set (it could never become odd).
+template <int R>
+__global__ void k_seed_lfib(DevParams p, uint64_t seed, uint64_t first)
+{
+    const uint64_t g = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= p.n) return;  // whole warps
+    uint32_t *st = static_cast<uint32_t *>(p.s[0]) + g * R;
+    uint32_t odd = 0;
+    for (int j = lane; j < R; j += 32) {
+        const uint32_t v = static_cast<uint32_t>(d_seed_word(seed, static_cast<uint64_t>(R) * (first + g) + j));
+        st[j] = v;
+        odd |= v & 1u;
+    }
+    if (!__any_sync(0xffffffffu, odd != 0) && lane == 0) st[0] |= 1u;
+}
+
+template <int R, int S, int OUT, int LAYOUT>
+__global__ void __launch_bounds__(Lfib<R, S>::kBlock) k_generate_lfib(DevParams p, void *out_, uint64_t K)
+{
+    constexpr int RS = Lfib<R, S>::kRing;
+    constexpr int W = Lfib<R, S>::kWarps;
+    // a normal pair never straddles two steps: even steps from the call start
+    constexpr int STEP = OUT == OUT_NORMAL ? (S & ~1) : S;
+    __shared__ uint32_t ring_s[W][RS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t g = static_cast<uint64_t>(blockIdx.x) * W + w;
+    const uint64_t n = p.n;
+    if (g >= n) return;  // whole warps only: no block-wide barriers below
+    uint32_t *ring = ring_s[w];
+    uint32_t *st = static_cast<uint32_t *>(p.s[0]) + g * R;
+
+    // x_m, m in [pos - r, pos), goes to ring slot m mod (r + s); with
+    // head = pos mod (r + s), x_(pos-r+t) sits at head + s + t (mod r + s)
+    // and comes from state slot (pos + t) mod r
+    const uint32_t head0 = static_cast<uint32_t>(p.pos % RS);
+    const uint32_t sr0 = static_cast<uint32_t>(p.pos % R);
+    for (int t = lane; t < R; t += 32) {
+        uint32_t a = head0 + S + t;
+        a = a >= RS ? a - RS : a;
+        uint32_t b = sr0 + t;
+        b = b >= R ? b - R : b;
+        ring[a] = st[b];
+    }
+    __syncwarp();
+
+    auto out_index = [&](uint64_t d) -> uint64_t {
+        return LAYOUT == RNG_INSTANCE_MAJOR ? g * K + d : d * n + g;
+    };
+    uint32_t xacc = 0;
+    float facc = 0.0f;
+    uint32_t head = head0;
+    for (uint64_t k = 0; k < K;) {
+        const int cnt = static_cast<int>(K - k < static_cast<uint64_t>(STEP) ? K - k : STEP);
+        // word pos+k+j (slot head+j) = word -r (slot head+j+s) + word -s (slot head+j+r)
+        for (int j = lane; j < cnt; j += 32) {
+            uint32_t a = head + j + S, b = head + j + R, c = head + j;
+            a = a >= RS ? a - RS : a;
+            b = b >= RS ? b - RS : b;
+            c = c >= RS ? c - RS : c;
+            const uint32_t v = ring[a] + ring[b];
+            ring[c] = v;
+            if (OUT != OUT_NORMAL) {
+                const uint32_t bits = OUT == OUT_U32 ? v : __float_as_uint(u32_to_unit(v));
+                if (LAYOUT == RNG_XOR_REDUCE) xacc ^= bits;
+                else __stcs(static_cast<uint32_t *>(out_) + out_index(k + j), bits);
+            }
+        }
+        if (OUT == OUT_NORMAL) {
+            __syncwarp();
+            for (int t = lane; 2 * t < cnt; t += 32) {
+                uint32_t c0 = head + 2 * t, c1 = head + 2 * t + 1;
+                c0 = c0 >= RS ? c0 - RS : c0;
+                c1 = c1 >= RS ? c1 - RS : c1;
+                float z0, z1;
+                box_muller(ring[c0], ring[c1], z0, z1);
+                if (LAYOUT == RNG_XOR_REDUCE) {
+                    facc += z0;
+                    facc += z1;
+                } else {
+                    float *out = static_cast<float *>(out_);
+                    __stcs(out + out_index(k + 2 * t), z0);
+                    __stcs(out + out_index(k + 2 * t + 1), z1);
+                }
+            }
+        }
+        __syncwarp();
+        head += cnt;
+        head = head >= RS ? head - RS : head;
+        k += cnt;
+    }
+    if (LAYOUT == RNG_XOR_REDUCE) {
+        if (OUT == OUT_NORMAL) {
+            for (int o = 16; o > 0; o >>= 1) facc += __shfl_down_sync(0xffffffffu, facc, o);
+            if (lane == 0) static_cast<float *>(out_)[g] = facc;
+        } else {
+            for (int o = 16; o > 0; o >>= 1) xacc ^= __shfl_down_sync(0xffffffffu, xacc, o);
+            if (lane == 0) static_cast<uint32_t *>(out_)[g] = xacc;
+        }
+    }
+    // the r newest words back to their state slots: x_(pos+K-r+t) at
+    // ring head + s + t, state slot (pos + K + t) mod r
+    const uint32_t srK = static_cast<uint32_t>((p.pos + K) % R);
+    for (int t = lane; t < R; t += 32) {
+        uint32_t a = head + S + t;
+        a = a >= RS ? a - RS : a;
+        uint32_t b = srK + t;
+        b = b >= R ? b - R : b;
+        st[b] = ring[a];
+    }
+}
+
+template <int R, int S, int OUT>
+int launch_out(const GenState &g, void *out, uint64_t K, int layout, cudaStream_t s)
+{
+    const DevParams p = dev_params(g);
+    constexpr int W = Lfib<R, S>::kWarps;
+    const dim3 grid(static_cast<unsigned>((g.n + W - 1) / W));
+    switch (layout) {
+    case RNG_STEP_MAJOR: k_generate_lfib<R, S, OUT, RNG_STEP_MAJOR><<<grid, Lfib<R, S>::kBlock, 0, s>>>(p, out, K); break;
+    case RNG_INSTANCE_MAJOR:
+        k_generate_lfib<R, S, OUT, RNG_INSTANCE_MAJOR><<<grid, Lfib<R, S>::kBlock, 0, s>>>(p, out, K);
+        break;
+    default: k_generate_lfib<R, S, OUT, RNG_XOR_REDUCE><<<grid, Lfib<R, S>::kBlock, 0, s>>>(p, out, K); break;
+    }
+    RNGX_CHECK_CUDA(cudaGetLastError());
+    return RNG_OK;
+}
+
+template <int R, int S>
+int launch_lags(const GenState &g, void *out, uint64_t K, int out_kind, int layout, cudaStream_t s)
+{
+    switch (out_kind) {
+    case OUT_U32: return launch_out<R, S, OUT_U32>(g, out, K, layout, s);
+    case OUT_F32: return launch_out<R, S, OUT_F32>(g, out, K, layout, s);
+    default: return launch_out<R, S, OUT_NORMAL>(g, out, K, layout, s);
+    }
+}
+
+}  // namespace
+
+int launch_generate_lfib(const GenState &g, void *d_out, uint64_t K, int out_kind, int layout, cudaStream_t s)
+{
+    if (g.kind == RNG_LFIB521) return launch_lags<521, 353>(g, d_out, K, out_kind, layout, s);
+    return launch_lags<1279, 861>(g, d_out, K, out_kind, layout, s);
+}
+
+int launch_seed_lfib(GenState &g, uint64_t seed, cudaStream_t s)
+{
+    const DevParams p = dev_params(g);
+    const unsigned threads = 256;
+    const unsigned blocks = static_cast<unsigned>((g.n * 32 + threads - 1) / threads);
+    if (g.kind == RNG_LFIB521) k_seed_lfib<521><<<blocks, threads, 0, s>>>(p, seed, g.first);
+    else k_seed_lfib<1279><<<blocks, threads, 0, s>>>(p, seed, g.first);
+    RNGX_CHECK_CUDA(cudaGetLastError());
+    return RNG_OK;
+}
+
+}  // namespace rngx

@@ -57,6 +57,8 @@ extern "C" int rng_skipahead_noalloc(int kind, void *d_state, uint64_t n_instanc
     case RNG_XORWOW: state_bits = 160; break;
     case RNG_XS1024W: state_bits = 1024; break;
     case RNG_MT19937_SHARED: state_bits = 19937; break;
+    case RNG_LFIB521: state_bits = 521 * 32; break;
+    case RNG_LFIB1279: state_bits = 1279 * 32; break;
     case RNG_LCG32:
     case RNG_LCG64:
     case RNG_MWC:

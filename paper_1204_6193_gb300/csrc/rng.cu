@@ -59,6 +59,8 @@ void state_layout(int kind, size_t &bytes_per, int &arrays, size_t &elem)
     case RNG_PHILOX4X32_7: bytes_per = 8; arrays = 1; elem = 8; break;
     case RNG_XS1024W: bytes_per = 4; arrays = 1; elem = 4; break;
     case RNG_MT19937_SHARED: bytes_per = 4 * MT_N_WORDS; arrays = 1; elem = 4 * MT_N_WORDS; break;
+    case RNG_LFIB521: bytes_per = 4 * 521; arrays = 1; elem = 4 * 521; break;
+    case RNG_LFIB1279: bytes_per = 4 * 1279; arrays = 1; elem = 4 * 1279; break;
     default: bytes_per = 0; arrays = 0; elem = 0;
     }
 }
@@ -190,8 +192,8 @@ int rng_create_shard(rng_t *out, int kind, uint64_t n_total, uint64_t first, uin
         set_error("RNG_XS1024W shares one 1024-bit state per 32 lanes: sizes must be multiples of 32");
         return RNG_EINVAL;
     }
-    if (kind == RNG_MT19937_SHARED && count > 0x7fffffffull) {
-        set_error("too many MT19937 generators");
+    if (is_block_shared(kind) && count > 0x7fffffffull) {
+        set_error("too many block-shared generators");
         return RNG_EINVAL;
     }
     if ((flags & RNG_PHILOX_INTRINSIC_KEY) && n_total > (1ull << 32)) {

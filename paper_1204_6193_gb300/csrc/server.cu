@@ -410,7 +410,7 @@ int rng_server_submit(rng_server_t S, const rng_request_t *req, uint64_t *ticket
     }
     const rng_request_t &r = *req;
     if (r.type == RNG_REQ_DRAW) {
-        if (r.kind < RNG_LCG32 || r.kind >= kNumKinds || r.kind == RNG_MT19937_SHARED || r.count == 0 ||
+        if (r.kind < RNG_LCG32 || r.kind >= kNumKinds || is_block_shared(r.kind) || r.count == 0 ||
             r.out < RNG_OUT_U32 ||
             r.out > RNG_OUT_NORMAL || (r.out == RNG_OUT_NORMAL && (r.count & 1))) {
             set_error("rng_server_submit: bad draw request (kind, count, output form)");
@@ -418,7 +418,7 @@ int rng_server_submit(rng_server_t S, const rng_request_t *req, uint64_t *ticket
         }
     } else if (r.type == RNG_REQ_SWEEP) {
         if (r.L < 4 || r.L % 2 || r.L > 16384 || r.kind < RNG_LCG32 || r.kind >= kNumKinds ||
-            r.kind == RNG_MT19937_SHARED) {
+            is_block_shared(r.kind)) {
             set_error("rng_server_submit: bad sweep request");
             return RNG_EINVAL;
         }

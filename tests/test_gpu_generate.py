@@ -10,7 +10,8 @@ pytestmark = pytest.mark.gpu
 
 SEED = 0x0123456789ABCDEF
 THREAD_KINDS = [O.LCG32, O.LCG64, O.MWC, O.XORWOW, O.PHILOX4X32_10, O.XS1024W, O.PHILOX4X32_7]
-ALL_KINDS = THREAD_KINDS + [O.MT19937_SHARED]
+SHARED_KINDS = [O.MT19937_SHARED, O.LFIB521, O.LFIB1279]  # one state shared by a group of threads
+ALL_KINDS = THREAD_KINDS + SHARED_KINDS
 NORMAL_TOL = 2e-6  # absolute, for float32 Box-Muller against the double oracle
 
 
@@ -80,12 +81,22 @@ def test_mt_64_generators_x_65536_bit_exact(R, torch_cuda):
     assert np.array_equal(g, o)
 
 
+@pytest.mark.parametrize("kind", [O.LFIB521, O.LFIB1279])
+def test_lfib_64_generators_x_65536_bit_exact(R, torch_cuda, kind):
+    # warp-shared rings (Sec. 4): many steps of s words, and the state
+    # carried across calls of odd length
+    n = 64
+    o = O.generate(kind, SEED, n, 65536 + 777)
+    g = run_gpu(R, torch_cuda, kind, n, [65536, 777], layout=1)
+    assert np.array_equal(np.concatenate(g, axis=1), o)
+
+
 # ------------------------------------------------------ layouts and forms
 def ragged_n(kind):
     if kind == O.XS1024W:
         return 96
-    if kind == O.MT19937_SHARED:
-        return 5
+    if kind in SHARED_KINDS:
+        return 5  # a partial block of warp-shared generators
     return 1000  # not a multiple of 32: partial last warp
 
 
@@ -93,7 +104,7 @@ def ragged_n(kind):
 @pytest.mark.parametrize("layout", [0, 1])
 def test_u32_and_f32_layouts_ragged(R, torch_cuda, kind, layout):
     n = ragged_n(kind)
-    K = 1501 if kind == O.MT19937_SHARED else 77
+    K = 1501 if kind in SHARED_KINDS else 77
     o = O.generate(kind, SEED, n, K)
     g = run_gpu(R, torch_cuda, kind, n, [K], layout=layout)[0]
     assert np.array_equal(g, o)
@@ -106,7 +117,7 @@ def test_u32_and_f32_layouts_ragged(R, torch_cuda, kind, layout):
 @pytest.mark.parametrize("layout", [0, 1])
 def test_normals_within_2e6(R, torch_cuda, kind, layout):
     n = ragged_n(kind)
-    K = 1250 if kind == O.MT19937_SHARED else 78
+    K = 1250 if kind in SHARED_KINDS else 78
     o = O.box_muller(O.generate(kind, SEED, n, K))
     g = run_gpu(R, torch_cuda, kind, n, [K], layout=layout, out="normal")[0]
     err = np.abs(g.astype(np.float64) - o).max()
@@ -116,7 +127,7 @@ def test_normals_within_2e6(R, torch_cuda, kind, layout):
 @pytest.mark.parametrize("kind", ALL_KINDS)
 def test_consume_in_register_modes(R, torch_cuda, kind):
     n = ragged_n(kind)
-    K = 1250 if kind == O.MT19937_SHARED else 78
+    K = 1250 if kind in SHARED_KINDS else 78
     o = O.generate(kind, SEED, n, K)
     g = run_gpu(R, torch_cuda, kind, n, [K], layout=R.RNG_XOR_REDUCE)[0]
     assert np.array_equal(g, np.bitwise_xor.reduce(o, axis=1))
@@ -178,7 +189,7 @@ def test_xs1024w_unaligned_output_pointer(R, torch_cuda):
 @pytest.mark.parametrize("kind", ALL_KINDS)
 def test_consecutive_calls_continue_the_streams(R, torch_cuda, kind):
     n = ragged_n(kind)
-    Ks = [37, 91, 2] if kind != O.MT19937_SHARED else [37, 1300, 611]
+    Ks = [37, 91, 2] if kind not in SHARED_KINDS else [37, 1300, 611]
     o = O.generate(kind, SEED, n, sum(Ks))
     g = run_gpu(R, torch_cuda, kind, n, Ks)
     assert np.array_equal(np.concatenate(g, axis=1), o)
@@ -193,8 +204,9 @@ def test_skipahead(R, torch_cuda, kind, t):
     assert np.array_equal(g, o)
 
 
-def test_skipahead_unsupported_for_mt(R, torch_cuda):
-    h = R.rng_create(R.RNG_MT19937_SHARED, 2)
+@pytest.mark.parametrize("kind", SHARED_KINDS)
+def test_skipahead_unsupported_for_block_shared_kinds(R, torch_cuda, kind):
+    h = R.rng_create(kind, 2)
     try:
         R.rng_seed(h, 1)
         with pytest.raises(R.RngError) as e:
@@ -256,7 +268,7 @@ def test_mwc_multiplier_table_matches_oracle(R, torch_cuda):
 
 @pytest.mark.parametrize("kind", ALL_KINDS)
 def test_shards_reproduce_the_whole(R, torch_cuda, kind):
-    n = 256 if kind != O.MT19937_SHARED else 6
+    n = 256 if kind not in SHARED_KINDS else 6
     K = 21
     flags = O.SEED_LEAPFROG if kind == O.LCG32 else (O.SEED_SUBSTREAM if kind == O.XS1024W else 0)
     whole = run_gpu(R, torch_cuda, kind, n, [K], flags=flags)[0]
@@ -319,7 +331,7 @@ def test_full_size_sampled(R, torch_cuda, kind):
     """2^30 outputs per call in the bench's launch configuration, checked on
     sampled instances (every draw of each sampled instance)."""
     torch = torch_cuda
-    if kind == O.MT19937_SHARED:
+    if kind in SHARED_KINDS:
         n, K, layout = 1 << 15, 1 << 15, 1  # one generator per warp, 2^20 threads
     else:
         n, K, layout = 1 << 20, 1024, 0
