@@ -180,6 +180,14 @@ int rng_generate_f32(rng_t h, float *d_out, uint64_t n_per_instance, int layout,
  * transform of its uniform output. */
 int rng_generate_normal(rng_t h, float *d_out, uint64_t n_per_instance, int layout, void *cuda_stream);
 
+/* The same Box-Muller transform on caller-provided words: pair i of
+ * d_in (words 2i, 2i+1, as r0, r1 above) becomes normals d_out[2i],
+ * d_out[2i+1].  d_in, d_out: device arrays of 2 n_pairs elements, 16-byte
+ * aligned (else RNG_EINVAL), owned by the caller.  Asynchronous.  (The
+ * paper has no normal deviates; this exposes the conversion of
+ * rng_generate_normal for streams produced elsewhere.) */
+int rng_u32_to_normal(const uint32_t *d_in, float *d_out, uint64_t n_pairs, void *cuda_stream);
+
 /* Checkpoint: copies the full generator state (plus kind, sizes, flags and
  * draw position) into host_buf.  With host_buf == NULL only *bytes is set
  * to the required size.  rng_set_state restores a blob taken from a handle

@@ -52,6 +52,7 @@ _SIGS = {
     "rng_generate_u32": [_p, _p, _u64, _i32, _p],
     "rng_generate_f32": [_p, _p, _u64, _i32, _p],
     "rng_generate_normal": [_p, _p, _u64, _i32, _p],
+    "rng_u32_to_normal": [_p, _p, _u64, _p],
     "rng_get_state": [_p, _p, ctypes.POINTER(ctypes.c_size_t)],
     "rng_set_state": [_p, _p, ctypes.c_size_t],
     "rng_info": [_p, ctypes.POINTER(_i32), ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64)],
@@ -150,6 +151,10 @@ def rng_generate_f32(h: int, d_out: int, n_per_instance: int, layout: int = RNG_
 
 def rng_generate_normal(h: int, d_out: int, n_per_instance: int, layout: int = RNG_STEP_MAJOR, stream=None) -> None:
     _call("rng_generate_normal", h, d_out, n_per_instance, layout, _stream(stream))
+
+
+def rng_u32_to_normal(d_in: int, d_out: int, n_pairs: int, stream=None) -> None:
+    _call("rng_u32_to_normal", d_in, d_out, n_pairs, _stream(stream))
 
 
 def rng_get_state(h: int) -> bytes:

@@ -3,6 +3,8 @@
 // consume-in-register (XOR / sum) form.  The state is loaded into
 // registers once, stepped K times and stored once (the paper's concern
 // about state load/store overhead, Sec. 2 and the caption of Table 2).
+#include <algorithm>
+
 #include "gen_device.cuh"
 
 namespace rngx {
@@ -152,8 +154,9 @@ __global__ void __launch_bounds__(kBlock) k_generate(DevParams p, void *out_, ui
 // 624, which for i < 227 is not yet rewritten and for i >= 227 was
 // rewritten 227 positions earlier, i.e. in an earlier chunk; so a chunk
 // reads its inputs into registers, syncs the warp and writes -- no block
-// barriers.  The refilled words are tempered into a per-warp buffer from
-// which the outputs (pairs, for normals) are written.
+// barriers.  Uniform outputs are tempered and written as the refill makes
+// them; normals pair the refilled state words afterwards (tempering them as
+// they are read), so the warp needs no buffer beside its state.
 constexpr int kMtWarps = 8;
 constexpr int kMtBlock = 32 * kMtWarps;
 
@@ -212,12 +215,11 @@ template <int OUT, int LAYOUT>
 __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out_, uint64_t K)
 {
     __shared__ uint32_t mt_s[kMtWarps][MT_N];
-    __shared__ uint32_t buf_s[kMtWarps][MT_N + 2];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t gidx = static_cast<uint64_t>(blockIdx.x) * kMtWarps + w;
     const uint64_t n = p.n;
     if (gidx >= n) return;  // whole warps only: no block-wide barriers below
-    uint32_t *mt = mt_s[w], *buf = buf_s[w];
+    uint32_t *mt = mt_s[w];
     uint32_t *st = static_cast<uint32_t *>(p.s[0]) + gidx * MT_N;
     for (int t = lane; t < MT_N; t += 32) mt[t] = st[t];
     int mti = p.pos == 0 ? MT_N : static_cast<int>((p.pos - 1) % MT_N) + 1;
@@ -228,7 +230,7 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
     };
     uint32_t xacc = 0;
     float facc = 0.0f;
-    uint32_t pending = 0;  // first word of a normal pair split across refills
+    uint32_t pending = 0;  // tempered first word of a normal pair split across refills
     bool twisted = false;
     uint64_t k = 0;
     while (k < K) {
@@ -253,25 +255,25 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
                 for (int t = lane; t < cnt; t += 32) put(t, mt[mti + t]);
             }
         } else {
-            // buf[0] = pending word when k is odd, then the chunk
-            const int off = static_cast<int>(k & 1);
+            // pairs come straight from the state words (tempered here): draw
+            // k - off + 2t and the next, off = 1 when a pair began in the
+            // previous chunk (its tempered first word is `pending`)
             if (refill) {
-                mt_twist_warp(mt, lane, [&](int i, uint32_t v) {
-                    if (i < cnt) buf[off + i] = mt_temper(v);
-                });
+                mt_twist_warp(mt, lane, [](int, uint32_t) {});
                 mti = 0;
                 twisted = true;
-            } else {
-                for (int t = lane; t < cnt; t += 32) buf[off + t] = mt_temper(mt[mti + t]);
             }
-            if (lane == 0 && off) buf[0] = pending;
             __syncwarp();
-            const uint64_t d0 = k - off;  // draw index of buf[0], even
+            const int off = static_cast<int>(k & 1);
+            const uint64_t d0 = k - off;  // even draw index of the first pair
             const int avail = cnt + off;
             const int pairs = avail / 2;
             for (int t = lane; t < pairs; t += 32) {
+                const int i0 = mti - off + 2 * t;  // state index of the pair's first word (-1: pending)
+                const uint32_t a = i0 < mti ? pending : mt_temper(mt[i0]);
+                const uint32_t b = mt_temper(mt[i0 + 1]);
                 float z0, z1;
-                box_muller(buf[2 * t], buf[2 * t + 1], z0, z1);
+                box_muller(a, b, z0, z1);
                 if (LAYOUT == RNG_XOR_REDUCE) {
                     facc += z0;
                     facc += z1;
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
                     __stcs(out + out_index(d0 + 2 * t + 1), z1);
                 }
             }
-            if (avail & 1) pending = buf[avail - 1];  // same value in every lane
+            if (avail & 1) pending = mt_temper(mt[mti + cnt - 1]);  // same value in every lane
             __syncwarp();
         }
         k += cnt;
@@ -504,6 +506,41 @@ int launch_kind(const GenState &g, void *out, uint64_t K, int out_kind, int layo
 }
 
 }  // namespace
+
+namespace {
+// Word pairs -> normal pairs, 16-byte loads and stores for four words.
+__global__ void k_u32_to_normal(const uint32_t *in, float *out, uint64_t n_pairs)
+{
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    for (uint64_t q = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; 2 * q < n_pairs; q += stride) {
+        if (2 * q + 1 < n_pairs) {
+            const uint4 w = reinterpret_cast<const uint4 *>(in)[q];
+            float4 z;
+            box_muller(w.x, w.y, z.x, z.y);
+            box_muller(w.z, w.w, z.z, z.w);
+            reinterpret_cast<float4 *>(out)[q] = z;
+        } else {
+            float z0, z1;
+            box_muller(in[4 * q], in[4 * q + 1], z0, z1);
+            out[4 * q] = z0;
+            out[4 * q + 1] = z1;
+        }
+    }
+}
+}  // namespace
+
+int launch_u32_to_normal(const uint32_t *in, float *out, uint64_t n_pairs, cudaStream_t s)
+{
+    if (n_pairs == 0) return RNG_OK;
+    int dev = 0, sms = 0;
+    RNGX_CHECK_CUDA(cudaGetDevice(&dev));
+    RNGX_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const uint64_t quads = (n_pairs + 1) / 2;
+    const unsigned blocks = static_cast<unsigned>(std::min<uint64_t>((quads + 255) / 256, static_cast<uint64_t>(sms) * 8));
+    k_u32_to_normal<<<blocks, 256, 0, s>>>(in, out, n_pairs);
+    RNGX_CHECK_CUDA(cudaGetLastError());
+    return RNG_OK;
+}
 
 int launch_generate(const GenState &g, void *d_out, uint64_t K, int out_kind, int layout, cudaStream_t s)
 {

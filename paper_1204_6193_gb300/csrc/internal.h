@@ -76,6 +76,7 @@ namespace rngx {
 int launch_generate(const GenState &g, void *d_out, uint64_t K, int out_kind, int layout, cudaStream_t s);
 int launch_seed(GenState &g, uint64_t seed, cudaStream_t s);
 int launch_skipahead(GenState &g, uint64_t t, cudaStream_t s);
+int launch_u32_to_normal(const uint32_t *in, float *out, uint64_t n_pairs, cudaStream_t s);
 int launch_generate_lfib(const GenState &g, void *d_out, uint64_t K, int out_kind, int layout, cudaStream_t s);
 int launch_seed_lfib(GenState &g, uint64_t seed, cudaStream_t s);
 

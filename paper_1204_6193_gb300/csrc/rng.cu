@@ -305,6 +305,16 @@ int rng_generate_normal(rng_t h, float *d_out, uint64_t n_per_instance, int layo
     return generate(h, d_out, n_per_instance, OUT_NORMAL, layout, cuda_stream);
 }
 
+int rng_u32_to_normal(const uint32_t *d_in, float *d_out, uint64_t n_pairs, void *cuda_stream)
+{
+    if (n_pairs == 0) return RNG_OK;
+    if (!d_in || !d_out || (reinterpret_cast<uintptr_t>(d_in) & 15) || (reinterpret_cast<uintptr_t>(d_out) & 15)) {
+        set_error("rng_u32_to_normal: input and output must be non-null and 16-byte aligned");
+        return RNG_EINVAL;
+    }
+    return launch_u32_to_normal(d_in, d_out, n_pairs, static_cast<cudaStream_t>(cuda_stream));
+}
+
 int rng_get_state(rng_t h, void *host_buf, size_t *bytes)
 {
     RNGX_CHECK(valid(h));

@@ -124,6 +124,45 @@ def test_normals_within_2e6(R, torch_cuda, kind, layout):
     assert err <= NORMAL_TOL, err
 
 
+def test_box_muller_exhaustive_over_each_word(R, torch_cuda):
+    # every u1 (all 2^24 values of r0 >> 8) at the angles where cos = 1 and
+    # sin = 1, and every u2 at the largest radius (u1 = 2^-24), against the
+    # oracle's double-precision transform
+    torch = torch_cuda
+    m = np.arange(1 << 24, dtype=np.uint32) << np.uint32(8)
+    cases = []
+    for r1 in (0, (1 << 22) << 8):
+        w = np.empty(2 * len(m), dtype=np.uint32)
+        w[0::2], w[1::2] = m, r1
+        cases.append(w)
+    w = np.empty(2 * len(m), dtype=np.uint32)
+    w[0::2], w[1::2] = 0, m
+    cases.append(w)
+    worst = 0.0
+    for w in cases:
+        din = torch.from_numpy(w.view(np.int32)).cuda()
+        dout = torch.empty(len(w), dtype=torch.float32, device="cuda")
+        R.rng_u32_to_normal(din.data_ptr(), dout.data_ptr(), len(w) // 2)
+        torch.cuda.synchronize()
+        err = np.abs(dout.cpu().numpy().astype(np.float64) - O.box_muller(w))
+        worst = max(worst, float(err.max()))
+    print(f"Box-Muller max abs error over the exhaustive sweeps: {worst:.3e}")
+    assert worst <= NORMAL_TOL
+
+
+def test_u32_to_normal_ragged_and_errors(R, torch_cuda):
+    torch = torch_cuda
+    w = np.random.default_rng(3).integers(0, 2**32, 2 * 1001, dtype=np.uint32)
+    din = torch.from_numpy(w.view(np.int32)).cuda()
+    dout = torch.full((len(w) + 4,), 7.0, dtype=torch.float32, device="cuda")
+    R.rng_u32_to_normal(din.data_ptr(), dout.data_ptr(), 1001)  # an odd number of pairs
+    got = dout.cpu().numpy()
+    assert np.abs(got[:len(w)] - O.box_muller(w)).max() <= NORMAL_TOL
+    assert np.all(got[len(w):] == 7.0)  # nothing past the last pair
+    with pytest.raises(R.RngError):
+        R.rng_u32_to_normal(din.data_ptr() + 4, dout.data_ptr(), 4)  # not 16-byte aligned
+
+
 @pytest.mark.parametrize("kind", ALL_KINDS)
 def test_consume_in_register_modes(R, torch_cuda, kind):
     n = ragged_n(kind)
