@@ -28,7 +28,7 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LN_DEG, SIN_DEG, COS_DEG = 7, 3, 4  # degrees of P(t), S(y), C(y)
+LN_DEG, SIN_DEG, COS_DEG = 6, 3, 3  # degrees of P(t), S(y), C(y)
 
 
 def chebyshev_nodes(a, b, n=20000):

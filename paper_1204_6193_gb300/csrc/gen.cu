@@ -231,6 +231,7 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
     uint32_t xacc = 0;
     float facc = 0.0f;
     uint32_t pending = 0;  // tempered first word of a normal pair split across refills
+    const bool out_even = (reinterpret_cast<uintptr_t>(out_) & 7) == 0;
     bool twisted = false;
     uint64_t k = 0;
     while (k < K) {
@@ -269,14 +270,18 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
             const int avail = cnt + off;
             const int pairs = avail / 2;
             for (int t = lane; t < pairs; t += 32) {
-                const int i0 = mti - off + 2 * t;  // state index of the pair's first word (-1: pending)
-                const uint32_t a = i0 < mti ? pending : mt_temper(mt[i0]);
+                const int i0 = mti - off + 2 * t;  // state index of the pair's first word (mti - 1: pending)
+                const uint32_t a = i0 < mti ? pending : mt_temper(mt[i0 < mti ? mti : i0]);  // no read below mti
                 const uint32_t b = mt_temper(mt[i0 + 1]);
                 float z0, z1;
                 box_muller(a, b, z0, z1);
                 if (LAYOUT == RNG_XOR_REDUCE) {
                     facc += z0;
                     facc += z1;
+                } else if (LAYOUT == RNG_INSTANCE_MAJOR && out_even) {
+                    // gidx K + d0 + 2t is even (K and d0 even): one 8-byte store
+                    __stcs(reinterpret_cast<float2 *>(static_cast<float *>(out_) + out_index(d0 + 2 * t)),
+                           make_float2(z0, z1));
                 } else {
                     float *out = static_cast<float *>(out_);
                     __stcs(out + out_index(d0 + 2 * t), z0);

@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(Lfib<R, S>::kBlock) k_generate_lfib(DevParams 
     uint32_t xacc = 0;
     float facc = 0.0f;
     uint32_t head = head0;
+    const bool out_even = (reinterpret_cast<uintptr_t>(out_) & 7) == 0;
     for (uint64_t k = 0; k < K;) {
         const int cnt = static_cast<int>(K - k < static_cast<uint64_t>(STEP) ? K - k : STEP);
         // word pos+k+j (slot head+j) = word -r (slot head+j+s) + word -s (slot head+j+r)
@@ -107,6 +108,10 @@ __global__ void __launch_bounds__(Lfib<R, S>::kBlock) k_generate_lfib(DevParams 
                 if (LAYOUT == RNG_XOR_REDUCE) {
                     facc += z0;
                     facc += z1;
+                } else if (LAYOUT == RNG_INSTANCE_MAJOR && out_even) {
+                    // g K + k + 2t is even (K and the step even): one 8-byte store
+                    __stcs(reinterpret_cast<float2 *>(static_cast<float *>(out_) + out_index(k + 2 * t)),
+                           make_float2(z0, z1));
                 } else {
                     float *out = static_cast<float *>(out_);
                     __stcs(out + out_index(k + 2 * t), z0);
