@@ -378,6 +378,27 @@ int rng_server_stats(rng_server_t s, uint64_t *submitted, uint64_t *completed, u
                      uint32_t *max_concurrent);
 int rng_server_destroy(rng_server_t s);
 
+/* ------------------------------------------------------------- allocator */
+
+/* Device memory the library owns for its handles (generator state,
+ * lattices, plans, scratch, server request buffers) comes from
+ * cudaMallocAsync / cudaFreeAsync on the handle's stream unless an
+ * allocator is installed here, e.g. a framework's caching allocator
+ * (process-lifetime tables -- MWC multipliers, GF(2) sub-stream matrices,
+ * the server's skip ladders -- stay on cudaMalloc).  alloc: *ptr = `bytes` of device memory on the current
+ * device, usable on `cuda_stream` (stream-ordered), returns 0 on success and
+ * nonzero on failure (reported as RNG_ENOMEM); free: releases a pointer from
+ * alloc, ordered after work on `cuda_stream`.  The hooks may be called from
+ * the request server's worker thread.  Process-wide; alloc = free = NULL
+ * restores the default.  Returns RNG_EBUSY while any memory from the
+ * previous allocator is outstanding (install it before creating handles and
+ * change it only after destroying them), RNG_EINVAL if exactly one hook is
+ * NULL.  Not part of the paper: an integration point for the caller's
+ * memory management. */
+typedef int (*rng_alloc_fn)(void **ptr, size_t bytes, void *cuda_stream, void *ctx);
+typedef void (*rng_free_fn)(void *ptr, void *cuda_stream, void *ctx);
+int rng_set_allocator(rng_alloc_fn alloc, rng_free_fn free, void *ctx);
+
 /* ----------------------------------------------------------------- errors */
 
 const char *rng_strerror(int status);

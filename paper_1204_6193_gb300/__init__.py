@@ -93,6 +93,16 @@ _lib.rng_last_error.argtypes = []
 _lib.rng_last_error.restype = ctypes.c_char_p
 
 
+# Allocator hooks (rng_set_allocator): int alloc(void **ptr, size_t bytes,
+# void *stream, void *ctx) and void free(void *ptr, void *stream, void *ctx).
+RNG_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t, ctypes.c_void_p,
+                                ctypes.c_void_p)
+RNG_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_lib.rng_set_allocator.argtypes = [RNG_ALLOC_FN, RNG_FREE_FN, _p]
+_lib.rng_set_allocator.restype = _i32
+_allocator_keepalive = None  # the installed ctypes callbacks must outlive their use
+
+
 def _call(name: str, *args) -> None:
     st = getattr(_lib, name)(*args)
     if st != RNG_OK:
@@ -107,6 +117,49 @@ def _stream(stream) -> int | None:
 
 def library() -> ctypes.CDLL:
     return _lib
+
+
+def rng_set_allocator(alloc=None, free=None) -> None:
+    """Installs Python callables as the library's device allocator:
+    alloc(nbytes, stream) -> device pointer (int), free(ptr, stream).  With
+    no arguments the library returns to cudaMallocAsync."""
+    global _allocator_keepalive
+    if alloc is None and free is None:
+        _call("rng_set_allocator", RNG_ALLOC_FN(), RNG_FREE_FN(), None)
+        _allocator_keepalive = None
+        return
+
+    def _a(pp, nbytes, stream, _ctx):
+        try:
+            ptr = int(alloc(int(nbytes), int(stream or 0)))
+        except Exception:  # reported to the caller of the library as RNG_ENOMEM
+            return 1
+        pp[0] = ptr
+        return 0 if ptr else 1
+
+    def _f(ptr, stream, _ctx):
+        free(int(ptr), int(stream or 0))
+
+    cbs = (RNG_ALLOC_FN(_a), RNG_FREE_FN(_f))
+    _call("rng_set_allocator", cbs[0], cbs[1], None)
+    _allocator_keepalive = cbs
+
+
+def use_torch_allocator(enable: bool = True) -> None:
+    """Routes the library's device memory through PyTorch's caching
+    allocator (or, with enable=False, back to cudaMallocAsync)."""
+    if not enable:
+        rng_set_allocator()
+        return
+    import torch
+
+    def alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, torch.cuda.current_device(), stream)
+
+    def free(ptr, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    rng_set_allocator(alloc, free)
 
 
 def rng_strerror(status: int) -> str:

@@ -1,8 +1,10 @@
 // rng.cu -- the C ABI for generator handles: creation, seeding, skip-ahead,
 // generation, checkpoint and errors.
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "internal.h"
@@ -27,22 +29,55 @@ int cuda_fail(cudaError_t e, const char *what)
     return e == cudaErrorMemoryAllocation ? RNG_ENOMEM : RNG_ECUDA;
 }
 
+namespace {
+// The installed allocator (none: cudaMallocAsync) and the number of
+// library allocations it still has outstanding.
+struct Allocator {
+    rng_alloc_fn alloc = nullptr;
+    rng_free_fn free = nullptr;
+    void *ctx = nullptr;
+};
+std::mutex g_alloc_mu;
+Allocator g_alloc;
+std::atomic<int64_t> g_outstanding{0};
+
+Allocator current_allocator()
+{
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    return g_alloc;
+}
+}  // namespace
+
 int dalloc(void **p, size_t bytes, cudaStream_t s)
 {
     *p = nullptr;
     if (bytes == 0) return RNG_OK;
-    cudaError_t e = cudaMallocAsync(p, bytes, s);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        *p = nullptr;
-        return cuda_fail(e, "cudaMallocAsync");
+    const Allocator a = current_allocator();
+    if (a.alloc) {
+        if (a.alloc(p, bytes, s, a.ctx) != 0 || !*p) {
+            *p = nullptr;
+            set_error("the installed allocator failed to provide %zu bytes", bytes);
+            return RNG_ENOMEM;
+        }
+    } else {
+        cudaError_t e = cudaMallocAsync(p, bytes, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            return cuda_fail(e, "cudaMallocAsync");
+        }
     }
+    g_outstanding.fetch_add(1);
     return RNG_OK;
 }
 
 void dfree(void *p, cudaStream_t s)
 {
-    if (p) cudaFreeAsync(p, s);
+    if (!p) return;
+    const Allocator a = current_allocator();
+    if (a.free) a.free(p, s, a.ctx);
+    else cudaFreeAsync(p, s);
+    g_outstanding.fetch_sub(1);
 }
 
 namespace {
@@ -382,6 +417,24 @@ int rng_info(rng_t h, int *kind, uint64_t *n_instances, uint64_t *first, uint64_
     if (n_instances) *n_instances = h->g.n;
     if (first) *first = h->g.first;
     if (position) *position = h->g.pos;
+    return RNG_OK;
+}
+
+int rng_set_allocator(rng_alloc_fn alloc, rng_free_fn free_fn, void *ctx)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr)) {
+        set_error("rng_set_allocator: give both hooks or neither");
+        return RNG_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (g_outstanding.load() != 0) {
+        set_error("rng_set_allocator: %lld allocations of the current allocator are still live",
+                  static_cast<long long>(g_outstanding.load()));
+        return RNG_EBUSY;
+    }
+    g_alloc.alloc = alloc;
+    g_alloc.free = free_fn;
+    g_alloc.ctx = ctx;
     return RNG_OK;
 }
 
