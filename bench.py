@@ -133,20 +133,32 @@ def file_hash(paths):
     return h.hexdigest()[:16]
 
 
-GEN_SOURCES = ["paper_1204_6193_gb300/csrc/gen.cu", "paper_1204_6193_gb300/csrc/gen_device.cuh"]
+GEN_SOURCES = ["paper_1204_6193_gb300/csrc/gen.cu", "paper_1204_6193_gb300/csrc/gen_device.cuh",
+               "paper_1204_6193_gb300/csrc/lfib.cu", "paper_1204_6193_gb300/csrc/normal_poly.h"]
 
 
-def ncu_traffic(kernel_key: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel
-    sources are unchanged since it was captured."""
+def _ncu_summary():
+    """The committed ncu summary of the generation kernels, if their sources
+    are unchanged since it was captured."""
     p = os.path.join(ROOT, "profiles", "gen_bulk_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    if d.get("source_hash") != file_hash(GEN_SOURCES):
-        return None
-    v = d.get("traffic_bytes_per_launch", {}).get(kernel_key)
+    return d if d.get("source_hash") == file_hash(GEN_SOURCES) else None
+
+
+def ncu_traffic(kernel_key: str):
+    """DRAM bytes per launch (ncu), scaled to the bench's launch."""
+    d = _ncu_summary()
+    v = d.get("traffic_bytes_per_launch", {}).get(kernel_key) if d else None
+    return float(v) if v is not None else None
+
+
+def ncu_inst_per_output(kernel_key: str):
+    """Thread instructions executed per output (ncu smsp__thread_inst_executed)."""
+    d = _ncu_summary()
+    v = d.get("thread_inst_per_output", {}).get(kernel_key) if d else None
     return float(v) if v is not None else None
 
 
@@ -211,6 +223,8 @@ def run_gpu(args):
     peaks = load_peaks()
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
+    # pipe throughputs of this GPU, measured outside the timed region
+    issue_peaks = R.rng_issue_peaks(sptr)
     bulk = Bulk(R, torch, rank, world)
     calls = bulk.calls()
 
@@ -253,6 +267,17 @@ def run_gpu(args):
     total_outputs = outputs_per_step_rank * world * args.steps
     value = total_outputs / (elapsed_ms * 1e-3) / 1e9
 
+    def issue_of(name, c, avg_ms):
+        ipo = ncu_inst_per_output(name)
+        if ipo is None or not issue_peaks:
+            return None
+        ach = ipo * c[4] * c[5] / (avg_ms * 1e-3) / 1e12
+        peak = issue_peaks["ffma"] / 1e12
+        return {"inst_per_output": round(ipo, 2), "achieved_tinst_s": round(ach, 2), "peak_tinst_s": round(peak, 2),
+                "frac": round(ach / peak, 3),
+                "source": "thread instructions per output from profiles/gen_bulk_traffic.json (ncu); issue peak "
+                          "= measured FFMA rate (rng_issue_peaks), one warp-instruction per scheduler and cycle"}
+
     detail = {}
     best = None
     for name, d in per.items():
@@ -262,6 +287,9 @@ def run_gpu(args):
         gb = bulk.algorithmic_bytes(c) / (avg * 1e-3) / 1e9
         detail[name] = {"ms": round(avg, 4), "gnum_s": round(c[4] * c[5] / (avg * 1e-3) / 1e9, 1),
                         "gb_s": round(gb, 1), "frac_hbm": round(gb / peaks["hbm_gbs"], 3)}
+        iss = issue_of(name, c, avg)
+        if iss:
+            detail[name]["issue_frac"] = iss["frac"]
         if best is None or tot > best[1]:
             best = (name, tot, avg, c)
     name, tot, avg, c = best
@@ -280,6 +308,7 @@ def run_gpu(args):
         "share_of_step": round(tot / step_ms_total, 3),
         "algorithmic_bytes_per_launch": bulk.algorithmic_bytes(c),
         "traffic": ncu_traffic(name),
+        "issue": issue_of(name, c, avg),
     }
 
     # end to end through the C ABI with host buffers: each step reseeds from a
@@ -390,6 +419,8 @@ def run_gpu(args):
                 "parallelism": f"instance shards x{world}",
             },
             "roofline": roofline,
+            "issue_peaks": {k: round(v / 1e12, 2) for k, v in issue_peaks.items()} | {
+                "unit": "T thread-instructions/s (whole GPU)", "source": "rng_issue_peaks microbenchmark"},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,
@@ -700,40 +731,65 @@ def serve_section(R, torch, args):
 
 
 # ------------------------------------------------------------ CPU oracle arm
-def oracle_sample(per_form: int):
+def oracle_sample(per_form: int, threads: int = 1):
     """Times the oracle on a bounded sample of the bulk workload: for every
-    kind and form, per_form outputs (instances x draws like the GPU call)."""
+    kind and form, per_form outputs (instances x draws like the GPU call).
+    With threads > 1 the instances of each call are split into that many
+    ranges run concurrently (the C oracle releases the interpreter lock)."""
+    from concurrent.futures import ThreadPoolExecutor
+
     import numpy as np
 
     import oracle as O
 
     O.mwc_multipliers(8192)  # multiplier table outside the timed region
+    pool = ThreadPoolExecutor(max_workers=threads) if threads > 1 else None
+
+    def run(kind, form, n, K, i_lo, i_hi):
+        r = O.generate(kind, SEED, n, K, i_lo=i_lo, i_hi=i_hi)
+        if form == "f32":
+            return O.to_f32(r)
+        if form == "normal":
+            return O.box_muller(r)
+        if form == "u32_xor":
+            return np.bitwise_xor.reduce(r, axis=1)
+        return r
+
     total = 0
     t0 = time.perf_counter()
     for kind in range(N_KINDS):
-        if kind in SHARED:
-            n, K = 4, per_form // 4
-        else:
-            n, K = 256, per_form // 256
+        n = max(threads, 4 if kind in SHARED else 256)
+        K = per_form // n
         for form in FORMS:
-            r = O.generate(kind, SEED, n, K)
-            if form == "f32":
-                O.to_f32(r)
-            elif form == "normal":
-                O.box_muller(r)
-            elif form == "u32_xor":
-                np.bitwise_xor.reduce(r, axis=1)
+            if pool is None:
+                run(kind, form, n, K, 0, n)
+            else:
+                cuts = [n * t // threads for t in range(threads + 1)]
+                list(pool.map(lambda t: run(kind, form, n, K, cuts[t], cuts[t + 1]), range(threads)))
             total += n * K
     dt = time.perf_counter() - t0
+    if pool is not None:
+        pool.shutdown()
     return total, dt
+
+
+def host_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def cpu_baseline(args):
     per_form = args.cpu_sample
-    total, dt = oracle_sample(per_form)
-    return {"value": round(total / dt / 1e9, 4), "unit": "Gnum/s", "cores": 1, "kind": "oracle",
+    cores = host_threads()
+    total1, dt1 = oracle_sample(per_form // 4)
+    total, dt = oracle_sample(per_form, cores)
+    return {"value": round(total / dt / 1e9, 4), "unit": "Gnum/s", "cores": cores, "kind": "oracle",
+            "single_thread": {"value": round(total1 / dt1 / 1e9, 4), "cores": 1,
+                              "sample": f"{per_form // 4} outputs per kind and form, {dt1:.1f} s"},
             "sample": f"{per_form} outputs per kind and form ({N_KINDS} kinds x 4 forms = {total} outputs), "
-                      f"single-threaded C oracle, {dt:.1f} s"}
+                      f"C oracle, instances split over {cores} threads, {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -741,22 +797,25 @@ def run_reference(args):
     if rank != 0:
         return None
     per_form = args.cpu_sample
-    oracle_sample(per_form // 8)  # warm-up (builds and loads the oracle)
+    cores = host_threads()
+    oracle_sample(per_form // 8, cores)  # warm-up (builds and loads the oracle)
     times, total = [], 0
     for _ in range(args.warmup):
-        oracle_sample(per_form // 4)
+        oracle_sample(per_form // 4, cores)
     for _ in range(args.steps):
-        tot, dt = oracle_sample(per_form // 4)
+        tot, dt = oracle_sample(per_form // 4, cores)
         times.append(dt)
         total += tot
     v = total / sum(times) / 1e9
     return {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "Gnum/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / len(times), 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "bulk generation sample (CPU oracle): 7 generators x {u32, f32, normal, u32 "
-                                   "xor} on a bounded sample per step", "outputs_per_step": total // len(times)},
-            "cpu_baseline": {"value": round(v, 4), "unit": "Gnum/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{per_form // 4} outputs per kind and form per step"},
+            "config": {"workload": f"bulk generation sample (CPU oracle): {N_KINDS} generators x {{u32, f32, "
+                                   f"normal, u32 xor}} on a bounded sample per step",
+                       "outputs_per_step": total // len(times)},
+            "cpu_baseline": {"value": round(v, 4), "unit": "Gnum/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_form // 4} outputs per kind and form per step, instances split "
+                                       f"over {cores} threads"},
             "e2e": {"value": round(v, 4), "unit": "Gnum/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

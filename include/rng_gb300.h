@@ -378,6 +378,18 @@ int rng_server_stats(rng_server_t s, uint64_t *submitted, uint64_t *completed, u
                      uint32_t *max_concurrent);
 int rng_server_destroy(rng_server_t s);
 
+/* ----------------------------------------------------------- measurement */
+
+/* Throughput of the SM pipes on the current device, in thread-instructions
+ * per second over the whole GPU: 32-bit logic (LOP3), integer multiply-add
+ * (IMAD), warp shuffle (SHFL) and float FMA (FFMA; its full rate equals the
+ * issue rate of one warp-instruction per scheduler and cycle).  Each is
+ * timed on eight independent chains per thread at full occupancy, best of
+ * three runs with CUDA events on cuda_stream (synchronises it).  Any output
+ * pointer may be NULL.  Not part of the paper: the denominators of the
+ * instruction-issue rooflines of the consume-in-register and normal modes. */
+int rng_issue_peaks(double *lop3, double *imad, double *shfl, double *ffma, void *cuda_stream);
+
 /* ------------------------------------------------------------- allocator */
 
 /* Device memory the library owns for its handles (generator state,

@@ -82,6 +82,7 @@ _SIGS = {
     "rng_server_fetch": [_p, _u64, _p, _u64],
     "rng_server_stats": [_p, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u32)],
     "rng_server_destroy": [_p],
+    "rng_issue_peaks": [_p, _p, _p, _p, _p],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -160,6 +161,13 @@ def use_torch_allocator(enable: bool = True) -> None:
         torch.cuda.caching_allocator_delete(ptr)
 
     rng_set_allocator(alloc, free)
+
+
+def rng_issue_peaks(stream=None) -> dict:
+    """Measured pipe throughputs (thread-instructions per second, whole GPU)."""
+    v = [ctypes.c_double() for _ in range(4)]
+    _call("rng_issue_peaks", *[ctypes.byref(x) for x in v], _stream(stream))
+    return {"lop3": v[0].value, "imad": v[1].value, "shfl": v[2].value, "ffma": v[3].value}
 
 
 def rng_strerror(status: int) -> str:
