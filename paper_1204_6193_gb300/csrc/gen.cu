@@ -496,7 +496,7 @@ int launch_kind_out(const GenState &g, void *out, uint64_t K, int layout, cudaSt
         default: k_generate<KIND, OUT, RNG_XOR_REDUCE><<<grid, kBlock, 0, s>>>(p, out, K); break;
         }
     }
-    RNGX_CHECK_CUDA(cudaGetLastError());
+    RNGX_CHECK_LAUNCH();
     return RNG_OK;
 }
 
@@ -543,7 +543,7 @@ int launch_u32_to_normal(const uint32_t *in, float *out, uint64_t n_pairs, cudaS
     const uint64_t quads = (n_pairs + 1) / 2;
     const unsigned blocks = static_cast<unsigned>(std::min<uint64_t>((quads + 255) / 256, static_cast<uint64_t>(sms) * 8));
     k_u32_to_normal<<<blocks, 256, 0, s>>>(in, out, n_pairs);
-    RNGX_CHECK_CUDA(cudaGetLastError());
+    RNGX_CHECK_LAUNCH();
     return RNG_OK;
 }
 

@@ -87,7 +87,7 @@ int gf2_one_step(int kind, uint32_t *d_m, cudaStream_t s)
 {
     if (kind == RNG_XS1024W) k_one_step_xs<<<128, 256, 0, s>>>(d_m);
     else k_one_step_xorwow<<<1, 160, 0, s>>>(d_m);
-    RNGX_CHECK_CUDA(cudaGetLastError());
+    RNGX_CHECK_LAUNCH();
     return RNG_OK;
 }
 
@@ -95,7 +95,7 @@ int gf2_mul(int n, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_c, cuda
 {
     const int warps_per_block = 8;
     k_mul<<<(n + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(n, d_a, d_b, d_c);
-    RNGX_CHECK_CUDA(cudaGetLastError());
+    RNGX_CHECK_LAUNCH();
     return RNG_OK;
 }
 
@@ -105,7 +105,7 @@ int gf2_pow(int kind, uint64_t t, uint32_t *d_out, uint32_t *d_sq, uint32_t *d_t
     const int n = kind == RNG_XS1024W ? 1024 : 160;
     const int words = n * (n / 32);
     k_identity<<<(words + 255) / 256, 256, 0, s>>>(d_out, n);
-    RNGX_CHECK_CUDA(cudaGetLastError());
+    RNGX_CHECK_LAUNCH();
     RNGX_CHECK(gf2_one_step(kind, d_sq, s));
     while (t) {
         if (t & 1) {

@@ -244,7 +244,7 @@ int launch_seed(GenState &g, uint64_t seed, cudaStream_t s)
     case RNG_LFIB1279: return launch_seed_lfib(g, seed, s);
     default: set_error("launch_seed: unknown kind %d", g.kind); return RNG_EINVAL;
     }
-    RNGX_CHECK_CUDA(cudaGetLastError());
+    RNGX_CHECK_LAUNCH();
     return RNG_OK;
 }
 
@@ -255,7 +255,7 @@ int launch_matrix_apply(int kind, const DevParams &p, const uint32_t *M, uint64_
     const unsigned nb = blocks_for(p.n);
     if (kind == RNG_XS1024W) k_skip_xs<<<nb, kBlock, 0, s>>>(p, M);
     else k_skip_xorwow<<<nb, kBlock, 0, s>>>(p, M, t);
-    RNGX_CHECK_CUDA(cudaGetLastError());
+    RNGX_CHECK_LAUNCH();
     return RNG_OK;
 }
 
@@ -295,7 +295,7 @@ int launch_skipahead(GenState &g, uint64_t t, cudaStream_t s)
         set_error("rng_skipahead: not defined for the block-shared generators (MT19937, lagged Fibonacci)");
         return RNG_EUNSUPPORTED;
     }
-    RNGX_CHECK_CUDA(cudaGetLastError());
+    RNGX_CHECK_LAUNCH();
     g.pos += t;
     return RNG_OK;
 }

@@ -36,6 +36,24 @@ int cuda_fail(cudaError_t e, const char *what);
         if (_s != RNG_OK) return _s;  \
     } while (0)
 
+// ---------------------------------------------------- fault injection
+// Host-side failures for testing error paths without any GPU fault, chosen
+// by the environment variable RNG_FAULT (read at every check, so a process
+// may change it): "oom" fails every library allocation with RNG_ENOMEM,
+// "oom:N" only the N-th from now; "launch" reports every kernel launch as
+// failed (RNG_ECUDA) after it was issued; "timeout" makes the next status
+// check of an Ising handle report a timed-out neighbour wait (RNG_ETIMEOUT).
+bool fault_oom();
+bool fault_launch();
+bool fault_timeout();
+int injected(const char *what, int status);
+
+#define RNGX_CHECK_LAUNCH()                                                          \
+    do {                                                                             \
+        if (::rngx::fault_launch()) return ::rngx::injected("kernel launch", RNG_ECUDA); \
+        RNGX_CHECK_CUDA(cudaGetLastError());                                         \
+    } while (0)
+
 // ---------------------------------------------------- device allocation
 // Stream-ordered device memory owned by the library.
 int dalloc(void **p, size_t bytes, cudaStream_t s);

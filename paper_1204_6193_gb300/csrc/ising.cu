@@ -303,7 +303,7 @@ int lat_create(IsingLat &t, uint32_t L, double beta, int layout, int kind, uint3
         k_init_ms<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(static_cast<uint32_t *>(t.spins), L, t.W,
                                                                           seed2);
     }
-    RNGX_CHECK_CUDA(cudaGetLastError());
+    RNGX_CHECK_LAUNCH();
     return RNG_OK;
 }
 
@@ -649,7 +649,7 @@ int enqueue_persistent(ising_t h, std::vector<Plan> &plans, uint64_t n_units, ui
             if (n_meas) k_meas_finalize<<<1, 256, 0, s>>>(t.meas, static_cast<uint32_t>(n_meas), t.acc);
             k_add_u64<<<1, 1, 0, s>>>(t.pos_dev, 2 * t.G * sweeps_per_unit * chunk);
         }
-        RNGX_CHECK_CUDA(cudaGetLastError());
+        RNGX_CHECK_LAUNCH();
         done += chunk;
     }
     return RNG_OK;
@@ -669,6 +669,7 @@ int check_err(ising_t h)
 {
     int err = 0;
     RNGX_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+    if (fault_timeout()) return injected("a neighbour wait of the persistent sweep", RNG_ETIMEOUT);
     RNGX_CHECK_CUDA(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
         set_error("Ising: a persistent sweep gave up waiting for a neighbouring strip (status %d)", err);
@@ -699,7 +700,7 @@ int observe(ising_t h, uint32_t idx, int64_t *E, int64_t *M, int64_t acc[4], uin
     RNGX_CHECK_CUDA(cudaMemsetAsync(t.acc + 5, 0, 2 * sizeof(int64_t), h->stream));
     const uint64_t n = t.layout == ISING_INT8 ? static_cast<uint64_t>(t.L) * t.L : static_cast<uint64_t>(t.L) * t.W;
     k_energy<<<static_cast<unsigned>((n + 255) / 256), 256, 0, h->stream>>>(lat_dev(t));
-    RNGX_CHECK_CUDA(cudaGetLastError());
+    RNGX_CHECK_LAUNCH();
     int64_t host[8];
     RNGX_CHECK_CUDA(cudaStreamSynchronize(h->stream));
     RNGX_CHECK_CUDA(cudaMemcpy(host, t.acc, sizeof(host), cudaMemcpyDeviceToHost));
@@ -886,7 +887,7 @@ int ising_sweep_plain(ising_t h, uint64_t n_sweeps, uint32_t measure_every, void
             }
         }
         k_set_u64<<<1, 1, 0, s>>>(t.pos_dev, t.rng->g.pos);
-        RNGX_CHECK_CUDA(cudaGetLastError());
+        RNGX_CHECK_LAUNCH();
     }
     return RNG_OK;
 }

@@ -158,7 +158,7 @@ int launch_out(const GenState &g, void *out, uint64_t K, int layout, cudaStream_
         break;
     default: k_generate_lfib<R, S, OUT, RNG_XOR_REDUCE><<<grid, Lfib<R, S>::kBlock, 0, s>>>(p, out, K); break;
     }
-    RNGX_CHECK_CUDA(cudaGetLastError());
+    RNGX_CHECK_LAUNCH();
     return RNG_OK;
 }
 
@@ -187,7 +187,7 @@ int launch_seed_lfib(GenState &g, uint64_t seed, cudaStream_t s)
     const unsigned blocks = static_cast<unsigned>((g.n * 32 + threads - 1) / threads);
     if (g.kind == RNG_LFIB521) k_seed_lfib<521><<<blocks, threads, 0, s>>>(p, seed, g.first);
     else k_seed_lfib<1279><<<blocks, threads, 0, s>>>(p, seed, g.first);
-    RNGX_CHECK_CUDA(cudaGetLastError());
+    RNGX_CHECK_LAUNCH();
     return RNG_OK;
 }
 

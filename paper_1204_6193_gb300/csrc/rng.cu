@@ -2,6 +2,8 @@
 // generation, checkpoint and errors.
 #include <atomic>
 #include <cstdarg>
+#include <cstdlib>
+#include <string>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -48,10 +50,45 @@ Allocator current_allocator()
 }
 }  // namespace
 
+namespace {
+std::mutex g_fault_mu;
+std::string g_fault_seen;   // the RNG_FAULT value the countdown belongs to
+long long g_fault_left = 0;  // "oom:N": allocations left before the failing one
+
+std::string fault_env()
+{
+    const char *v = std::getenv("RNG_FAULT");
+    return v ? std::string(v) : std::string();
+}
+}  // namespace
+
+bool fault_oom()
+{
+    const std::string v = fault_env();
+    if (v == "oom") return true;
+    if (v.rfind("oom:", 0) != 0) return false;
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    if (v != g_fault_seen) {  // a new setting restarts the countdown
+        g_fault_seen = v;
+        g_fault_left = std::atoll(v.c_str() + 4);
+    }
+    return g_fault_left > 0 && --g_fault_left == 0;
+}
+
+bool fault_launch() { return fault_env() == "launch"; }
+bool fault_timeout() { return fault_env() == "timeout"; }
+
+int injected(const char *what, int status)
+{
+    set_error("%s failed (injected by RNG_FAULT=%s)", what, fault_env().c_str());
+    return status;
+}
+
 int dalloc(void **p, size_t bytes, cudaStream_t s)
 {
     *p = nullptr;
     if (bytes == 0) return RNG_OK;
+    if (fault_oom()) return injected("device allocation", RNG_ENOMEM);
     const Allocator a = current_allocator();
     if (a.alloc) {
         if (a.alloc(p, bytes, s, a.ctx) != 0 || !*p) {

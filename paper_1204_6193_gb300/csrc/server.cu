@@ -219,7 +219,7 @@ int launch_draw(rng_server_s *S, ServerReq *q)
             if (r.kind == RNG_XS1024W)
                 k_ladder_xs<<<nb, 256, 0, s>>>(static_cast<uint32_t *>(w->state), w->g.n, S->ladder_xs, r.offset);
             else k_ladder_xorwow<<<nb, 256, 0, s>>>(static_cast<uint32_t *>(w->state), w->g.n, S->ladder_xw, r.offset);
-            RNGX_CHECK_CUDA(cudaGetLastError());
+            RNGX_CHECK_LAUNCH();
             w->g.pos = r.offset;
         } else {
             RNGX_CHECK(launch_skipahead(w->g, r.offset, s));
