@@ -270,6 +270,12 @@ int ising_observables(ising_t h, int64_t *E, int64_t *M, int64_t acc[4], uint64_
  * order is fixed by the site numbering alone. */
 int ising_set_launch(ising_t h, uint32_t threads, int ctas_per_sm, uint32_t min_sites_per_block);
 
+/* The launch shape last set by ising_set_launch or chosen by
+ * ising_autotune (zeros: heuristic), so that a tuned shape can be stored
+ * and set again on a handle of the same lattices.  Any pointer may be
+ * NULL. */
+int ising_get_launch(ising_t h, uint32_t *threads, int *ctas_per_sm, uint32_t *min_sites_per_block);
+
 /* Times the persistent kernel on a clone of the handle (same lattices and
  * seeds; the handle itself does not advance) for a few launch shapes,
  * probe_sweeps sweeps each, and applies the fastest (reported through the

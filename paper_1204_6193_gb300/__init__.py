@@ -68,6 +68,7 @@ _SIGS = {
     "ising_set_spins": [_p, _p],
     "ising_get_rng": [_p, _pp],
     "ising_set_launch": [_p, _u32, _i32, _u32],
+    "ising_get_launch": [_p, _p, _p, _p],
     "ising_autotune": [_p, _u32, _p, _p],
     "ising_info": [_p, _u32, _p, _p, _p, _p, _p],
     "ising_batch_create": [_pp, _u32, _p, _p, _p, _u64, _u32, _p],
@@ -320,6 +321,61 @@ def ising_autotune(h: int, probe_sweeps: int = 64) -> dict:
     t, c = _u32(), _i32()
     _call("ising_autotune", h, probe_sweeps, ctypes.byref(t), ctypes.byref(c))
     return {"threads": t.value, "ctas_per_sm": c.value}
+
+
+def ising_get_launch(h: int) -> dict:
+    t, c, m = _u32(), _i32(), _u32()
+    _call("ising_get_launch", h, ctypes.byref(t), ctypes.byref(c), ctypes.byref(m))
+    return {"threads": t.value, "ctas_per_sm": c.value, "min_sites": m.value}
+
+
+AUTOTUNE_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "rng_gb300", "autotune.json")
+
+
+def _device_name() -> str:
+    import torch
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return f"{p.name}/{p.multi_processor_count}"
+
+
+def _autotune_key(h: int, device: str) -> str:
+    import hashlib
+    n = ising_info(h, 0)["n_lattices"]
+    sig = []
+    for i in range(n):
+        d = ising_info(h, i)
+        sig.append((d["L"], d["layout"], d["kind"]))
+    return hashlib.sha1(repr((device, sig)).encode()).hexdigest()
+
+
+def ising_autotune_cached(h: int, probe_sweeps: int = 64, path: str | None = None, device: str | None = None) -> dict:
+    """ising_autotune with a cache of tuned launch shapes (default
+    ~/.cache/rng_gb300/autotune.json), keyed by the device and the handle's
+    lattices (size, layout, generator kind of each): a hit sets the stored
+    shape without timing anything.  Results never depend on the shape."""
+    import json
+    path = path or AUTOTUNE_CACHE
+    key = _autotune_key(h, device or _device_name())
+    cache = {}
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    if key in cache:
+        c = cache[key]
+        ising_set_launch(h, c["threads"], c["ctas_per_sm"], c["min_sites"])
+        return dict(c, cached=True)
+    ising_autotune(h, probe_sweeps)
+    c = ising_get_launch(h)
+    cache[key] = c
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1)
+    os.replace(tmp, path)
+    return dict(c, cached=False)
 
 
 def ising_batch_create(L, beta, rng_kind, seed: int = 0, G: int = 2, stream=None) -> int:

@@ -947,6 +947,15 @@ int ising_get_rng(ising_t h, rng_t *rng)
     return RNG_OK;
 }
 
+int ising_get_launch(ising_t h, uint32_t *threads, int *ctas_per_sm, uint32_t *min_sites_per_block)
+{
+    RNGX_CHECK(valid(h));
+    if (threads) *threads = h->cfg_threads;
+    if (ctas_per_sm) *ctas_per_sm = h->cfg_ctas_per_sm;
+    if (min_sites_per_block) *min_sites_per_block = h->cfg_min_sites;
+    return RNG_OK;
+}
+
 int ising_set_launch(ising_t h, uint32_t threads, int ctas_per_sm, uint32_t min_sites_per_block)
 {
     RNGX_CHECK(valid(h));
