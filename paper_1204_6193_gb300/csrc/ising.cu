@@ -217,7 +217,6 @@ struct Plan {
     SegDev *d_segs = nullptr;
     uint32_t *d_cta = nullptr;
     uint8_t *d_halo = nullptr;
-    uint32_t *d_flags = nullptr;
     // per strip: 2 slots x 2 rows x 2 colours of (tag, data) words
     size_t halo_bytes() const { return static_cast<size_t>(nsegs) * 8 * halo_row_bytes; }
 };
@@ -354,7 +353,6 @@ void free_plans(ising_t h)
             dfree(p.d_segs, h->stream);
             dfree(p.d_cta, h->stream);
             dfree(p.d_halo, h->stream);
-            dfree(p.d_flags, h->stream);
         }
     h->plans.clear();
     h->mh_plans.clear();
@@ -528,7 +526,6 @@ int materialize_plan(ising_t h, int kind, int layout, const std::vector<std::vec
     RNGX_CHECK(dalloc(reinterpret_cast<void **>(&P.d_segs), segs.size() * sizeof(SegDev), h->stream));
     RNGX_CHECK(dalloc(reinterpret_cast<void **>(&P.d_cta), cta.size() * sizeof(uint32_t), h->stream));
     RNGX_CHECK(dalloc(reinterpret_cast<void **>(&P.d_halo), P.halo_bytes(), h->stream));
-    RNGX_CHECK(dalloc(reinterpret_cast<void **>(&P.d_flags), P.nsegs * sizeof(uint32_t), h->stream));
     RNGX_CHECK_CUDA(cudaStreamSynchronize(h->stream));
     RNGX_CHECK_CUDA(cudaMemcpy(P.d_segs, segs.data(), segs.size() * sizeof(SegDev), cudaMemcpyHostToDevice));
     RNGX_CHECK_CUDA(cudaMemcpy(P.d_cta, cta.data(), cta.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
@@ -635,7 +632,6 @@ int enqueue_persistent(ising_t h, std::vector<Plan> &plans, uint64_t n_units, ui
             a.cta_seg = P.d_cta;
             a.halo = P.d_halo;
             a.halo_row_bytes = P.halo_row_bytes;
-            a.flags = P.d_flags;
             a.err = h->d_err;
             a.n_sweeps = chunk;
             a.measure_every = measure_every;
@@ -847,7 +843,6 @@ int ising_sweep_multihit(ising_t h, uint64_t n_rounds, uint32_t k, uint32_t n_st
             dfree(p.d_segs, h->stream);
             dfree(p.d_cta, h->stream);
             dfree(p.d_halo, h->stream);
-            dfree(p.d_flags, h->stream);
         }
         h->mh_plans.clear();
         h->mh_strips = 0;

@@ -10,7 +10,9 @@
 // once per launch).  After each half-sweep a strip publishes its two
 // boundary rows of the colour just updated and waits (bounded) only for
 // the strips above and below it; a strip that holds a whole lattice
-// refreshes its halo from itself.
+// refreshes its halo from itself.  In multi-hit mode (k_hits > 0) the
+// strips of one coarse colour take k sweeps of their own rows between two
+// exchanges, which then carry both colours of the boundary rows.
 #pragma once
 
 #include "ising_common.cuh"
@@ -24,9 +26,8 @@ struct PersistArgs {
     const LatDev *lats;
     const SegDev *segs;
     const uint32_t *cta_seg;   // segments of block b: [cta_seg[b], cta_seg[b+1])
-    uint8_t *halo;             // per segment: 2 parities x 2 rows x halo_row_bytes
+    uint8_t *halo;             // per segment: 2 slots x 2 rows (first, last) x 2 colours x halo_row_bytes
     uint32_t halo_row_bytes;
-    uint32_t *flags;           // per segment: half-sweeps published (zeroed per launch)
     int *err;
     uint64_t n_sweeps;
     uint64_t sweep0;           // sweeps of the same call before this launch
@@ -408,12 +409,19 @@ __device__ __forceinline__ bool poll_rows(uint8_t *smem, const SegLocal &sg, con
     for (uint32_t i = threadIdx.x; i < 2 * words; i += blockDim.x) {
         const uint64_t *src = i < words ? up_last + i : dn_first + (i - words);
         uint64_t v;
+        uint32_t spins = 0;
         while (((v = ld_relaxed_u64(src)) >> 32) != tag) {
-            __nanosleep(20);  // light backoff: many blocks poll the L2 at once
-            if (global_ns() - t0 > a.wait_budget_ns || static_cast<uint64_t>(clock64() - c0) > 4 * a.wait_budget_ns ||
-                ld_acquire(reinterpret_cast<const uint32_t *>(a.err)) != 0) {
-                atomicCAS(a.err, 0, RNG_ETIMEOUT);
-                return false;
+            // tight re-reads first (the word is usually one L2 round trip
+            // away); every 32nd miss checks the clocks and the abort flag
+            // and backs off briefly
+            if ((++spins & 31u) == 0) {
+                if (global_ns() - t0 > a.wait_budget_ns ||
+                    static_cast<uint64_t>(clock64() - c0) > 4 * a.wait_budget_ns ||
+                    ld_acquire(reinterpret_cast<const uint32_t *>(a.err)) != 0) {
+                    atomicCAS(a.err, 0, RNG_ETIMEOUT);
+                    return false;
+                }
+                __nanosleep(32);
             }
         }
         (i < words ? top[i] : bot[i - words]) = static_cast<uint32_t>(v);
@@ -447,7 +455,8 @@ __device__ void measure_strips(uint8_t *smem, const SegLocal *S, uint32_t nseg, 
 // at most 512 threads; the multi-hit kernel also runs two slots (one stream
 // in each coarse colour) with up to 1024 threads.
 template <int KIND, int LAYOUT, int SMAX, bool MH>
-__global__ void __launch_bounds__(SMAX >= (MH ? 4 : 2) ? 512 : 1024) k_ising_persist(PersistArgs a)
+__global__ void __launch_bounds__(SMAX >= (MH ? 4 : 2) ? 512 : 1024, (!MH && SMAX == 2) ? 2 : 1)
+    k_ising_persist(PersistArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ SegLocal S[kPersistMaxSegs];
