@@ -227,9 +227,12 @@ int ising_create(ising_t *out, uint32_t L, double beta, int layout, int rng_kind
  * With measure_every > 0 the energy E and magnetisation M are measured
  * after every measure_every-th sweep and accumulated (see
  * ising_observables).  Persistent fused kernel: random numbers never leave
- * registers and the lattice stays on chip between half-sweeps.  Asynchronous:
- * a timed-out wait between row strips (RNG_ETIMEOUT) is reported by the
- * next ising_observables / ising_get_spins. */
+ * registers and the lattice stays on chip between half-sweeps.  A lattice
+ * too large for any plan of co-resident row strips (beyond about 4096^2
+ * int8 or 8192^2 multispin on a GB300) runs the per-half-sweep kernels of
+ * ising_sweep_plain instead, with the same result.  Asynchronous: a
+ * timed-out wait between row strips (RNG_ETIMEOUT) is reported by the next
+ * ising_observables / ising_get_spins. */
 int ising_sweep(ising_t h, uint64_t n_sweeps, uint32_t measure_every, void *cuda_stream);
 
 /* n_rounds rounds of the multi-hit (double checkerboard) update, Sec. 2

@@ -230,6 +230,7 @@ struct ising_s {
     int *d_err = nullptr;
     std::vector<Plan> plans;
     bool planned = false;
+    bool plan_unfit = false;     // no persistent plan fits: sweeps run the per-half-sweep kernels
     std::vector<Plan> mh_plans;  // the multi-hit plan (one lattice) and its strip count
     uint32_t mh_strips = 0;
     unsigned cfg_threads = 0;    // 0: heuristic
@@ -811,6 +812,18 @@ int ising_sweep(ising_t h, uint64_t n_sweeps, uint32_t measure_every, void *cuda
     RNGX_CHECK(valid(h));
     if (n_sweeps == 0) return RNG_OK;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (h->plan_unfit) return ising_sweep_plain(h, n_sweeps, measure_every, cuda_stream);
+    if (!h->batch && !h->planned) {
+        const int st = ensure_plan(h);
+        if (st == RNG_EUNSUPPORTED) {
+            h->plan_unfit = true;
+            // no row-strip plan fits the device (a lattice too large for
+            // co-resident blocks): the per-half-sweep kernels give the same
+            // result
+            return ising_sweep_plain(h, n_sweeps, measure_every, cuda_stream);
+        }
+        RNGX_CHECK(st);
+    }
     RNGX_CHECK(ensure_plan(h));
     RNGX_CHECK(ensure_meas(h, measure_every ? std::max<uint64_t>(1, kChunkSweeps / measure_every + 1) : 1));
     // the device copy of the draw position follows the host's (which a
@@ -964,6 +977,7 @@ int ising_set_launch(ising_t h, uint32_t threads, int ctas_per_sm, uint32_t min_
     }
     RNGX_CHECK_CUDA(cudaStreamSynchronize(h->stream));
     free_plans(h);
+    h->plan_unfit = false;
     h->cfg_threads = threads;
     h->cfg_ctas_per_sm = ctas_per_sm;
     h->cfg_min_sites = min_sites_per_block;
