@@ -399,3 +399,47 @@ def test_full_size_sampled(R, torch_cuda, kind):
 def test_mwc_full_table_matches_oracle(R, torch_cuda):
     n = 1 << 20
     assert np.array_equal(R.rng_mwc_multipliers(0, n), O.mwc_multipliers(n))
+
+
+# ---------------------------------------------------- empty and tiny inputs
+@pytest.mark.parametrize("kind", ALL_KINDS)
+def test_zero_draws_and_single_instance(R, torch_cuda, kind):
+    # K = 0 is a no-op that leaves the position alone; one instance (one
+    # warp-shared state for XS1024W: 32 lanes) is the smallest handle
+    torch = torch_cuda
+    n = 32 if kind == O.XS1024W else 1
+    h = R.rng_create(kind, n)
+    try:
+        R.rng_seed(h, SEED)
+        sentinel = torch.full((n * 8,), -7, dtype=torch.int32, device="cuda")
+        for fn in (R.rng_generate_u32, R.rng_generate_f32, R.rng_generate_normal):
+            fn(h, sentinel.data_ptr(), 0, R.RNG_INSTANCE_MAJOR)
+        if kind not in SHARED_KINDS:
+            R.rng_skipahead(h, 0)
+        torch.cuda.synchronize()
+        assert torch.all(sentinel == -7) and R.rng_info(h)["position"] == 0
+        R.rng_generate_u32(h, sentinel.data_ptr(), 8, R.RNG_INSTANCE_MAJOR)
+        torch.cuda.synchronize()
+        got = sentinel.cpu().numpy().view(np.uint32).reshape(n, 8)
+        assert np.array_equal(got, O.generate(kind, SEED, n, 8))
+    finally:
+        R.rng_destroy(h)
+
+
+def test_zero_sweeps_and_smallest_lattice(R, torch_cuda):
+    # 0 sweeps change nothing; L = 4 (two streams per colour row pair) is
+    # the smallest lattice, a whole lattice in one strip
+    h = R.ising_create(4, 0.4, 0, O.XORWOW, 0, SEED, 2)
+    try:
+        init = R.ising_get_spins(h)
+        R.ising_sweep(h, 0)
+        R.ising_sweep_plain(h, 0)
+        assert np.array_equal(R.ising_get_spins(h), init)
+        assert np.array_equal(init, O.ising_init_spins(4, SEED))
+        R.ising_sweep(h, 25, 5)
+        ref, acc, nm = O.ising_run(4, 0.4, O.XORWOW, SEED, 25, measure_every=5)
+        obs = R.ising_observables(h)
+        assert np.array_equal(R.ising_get_spins(h), ref)
+        assert obs["acc"] == acc.tolist() and obs["n_meas"] == nm
+    finally:
+        R.ising_destroy(h)
