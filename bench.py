@@ -487,7 +487,21 @@ def ising_section(R, torch, args):
                 finally:
                     R.ising_destroy(h)
     out["multihit"] = multihit_section(R, torch, n)
+    if not args.no_cpu:
+        out["cpu_oracle"] = ising_oracle_rate()
     return out
+
+
+def ising_oracle_rate(sweeps: int = 20):
+    """The CPU oracle's checkerboard sweep of the 1024^2 lattice at beta_c
+    (xorwow, G = 2), single-threaded: flips/ns beside the GPU's."""
+    import oracle as O
+    O.ising_run(64, BETA_C, 3, SEED, 2)  # loads the oracle
+    t0 = time.perf_counter()
+    O.ising_run(1024, BETA_C, 3, SEED, sweeps)
+    dt = time.perf_counter() - t0
+    return {"flips_per_ns": round(1024 * 1024 * sweeps / (dt * 1e9), 4), "cores": 1,
+            "sample": f"{sweeps} sweeps of L=1024 int8, xorwow, {dt:.2f} s"}
 
 
 def _time_rounds(R, torch, h, rounds, k, strips):
