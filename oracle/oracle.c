@@ -21,6 +21,16 @@
  * Everything is written for clarity, not speed: generators are stepped one
  * draw at a time, matrices over GF(2) are multiplied row by row, and the
  * Ising update visits sites in plain loops.
+ *
+ * Parity unpinned: the conventions the paper leaves open have no value in
+ * the paper to check them against, and the tests can only confirm that they
+ * are applied consistently -- the seed-word mapping of every kind (including
+ * the lagged Fibonacci rings and the intrinsic Philox key (i, low half of
+ * the seed)), the XS1024W Weyl reading (y_0 = 0, one value for all lanes),
+ * the initial spins, the Ising draw order (stream s owns sites sG..sG+G-1
+ * of both colours) and the multi-hit strip and phase order.  Everything
+ * built on them (recurrences, skip-ahead, the Metropolis step, the exact
+ * Ising values) is pinned by the tests.
  */
 #include <math.h>
 #include <stdint.h>
