@@ -4,6 +4,7 @@
 // registers once, stepped K times and stored once (the paper's concern
 // about state load/store overhead, Sec. 2 and the caption of Table 2).
 #include <algorithm>
+#include <type_traits>
 
 #include "gen_device.cuh"
 
@@ -147,134 +148,113 @@ __global__ void __launch_bounds__(kBlock) k_generate(DevParams p, void *out_, ui
 }
 
 // ------------------------------------------------------------- MT19937
-// One generator per warp: its 624-word state is staged in shared memory
-// (Sec. 5: the state is shared by the threads that refill it) and the warp
-// refills it in 20 chunks of 32 consecutive words.  In the sequential
-// recurrence word i reads word i+1 (not yet rewritten) and word i+397 mod
-// 624, which for i < 227 is not yet rewritten and for i >= 227 was
-// rewritten 227 positions earlier, i.e. in an earlier chunk; so a chunk
-// reads its inputs into registers, syncs the warp and writes -- no block
-// barriers.  Uniform outputs are tempered and written as the refill makes
-// them; normals pair the refilled state words afterwards (tempering them as
-// they are read), so the warp needs no buffer beside its state.
+// One generator per warp (Sec. 5: one state shared by the threads that
+// refill it).  The warp keeps the 624-word state in registers: lane l holds
+// word 32j + l in x[j] (j < 20; x[19] only in lanes 0..15).  A refill is 20
+// chunks of 32 words, chunk j making words 32j .. 32j+31 at once.  In the
+// sequential recurrence word i reads word i+1 (not yet rewritten; for i =
+// 623 the new word 0) and word i+397 mod 624, which for i < 227 is not yet
+// rewritten and for i >= 227 is the new word i-227, made in an earlier
+// chunk.  Both come by one warp shuffle each: the sending lane picks the
+// register the receiving lane needs (the two receivers of a sender never
+// need different registers, except in the chunk that crosses i = 227).
+// Uniform outputs are tempered and stored as they are made; normals stage
+// the tempered words of a block in shared memory and pair them from there.
 constexpr int kMtWarps = 8;
 constexpr int kMtBlock = 32 * kMtWarps;
+constexpr int kMtRegs = (MT_N + 31) / 32;  // 20
 
 __device__ __forceinline__ uint32_t mt_mix(uint32_t cur, uint32_t nxt, uint32_t far)
 {
     const uint32_t y = (cur & 0x80000000u) | (nxt & 0x7fffffffu);
-    return far ^ (y >> 1) ^ ((y & 1u) ? 0x9908B0DFu : 0u);
+    return far ^ (y >> 1) ^ ((nxt & 1u) * 0x9908B0DFu);
 }
 
-// Refills the state and hands each new word i (in order) to emit(i, word).
-template <typename Emit>
-__device__ __forceinline__ void mt_twist_warp(uint32_t *mt, int lane, Emit emit)
+// One refill of the register-resident state (all 32 lanes call it).
+__device__ __forceinline__ void mt_twist_regs(uint32_t (&x)[kMtRegs], int lane)
 {
-    // chunks with i + 397 < 624 (far word not yet rewritten)
-#pragma unroll 1
-    for (int b = 0; b < 224; b += 32) {
-        const int i = b + lane;
-        const uint32_t v = mt_mix(mt[i], mt[i + 1], mt[i + MT_M]);
-        __syncwarp();
-        mt[i] = v;
-        emit(i, v);
-        __syncwarp();
-    }
-    {  // the chunk that crosses i = 227
-        const int i = 224 + lane;
-        const uint32_t v = mt_mix(mt[i], mt[i + 1], mt[i < MT_N - MT_M ? i + MT_M : i - (MT_N - MT_M)]);
-        __syncwarp();
-        mt[i] = v;
-        emit(i, v);
-        __syncwarp();
-    }
-    // chunks whose far word i - 227 was rewritten in an earlier chunk
-#pragma unroll 1
-    for (int b = 256; b < 608; b += 32) {
-        const int i = b + lane;
-        const uint32_t v = mt_mix(mt[i], mt[i + 1], mt[i - (MT_N - MT_M)]);
-        __syncwarp();
-        mt[i] = v;
-        emit(i, v);
-        __syncwarp();
-    }
-    {  // the last 16 words; word 623 pairs with the new word 0
-        const int i = 608 + lane;
-        uint32_t v = 0;
-        if (i < MT_N) v = mt_mix(mt[i], mt[i + 1 == MT_N ? 0 : i + 1], mt[i - (MT_N - MT_M)]);
-        __syncwarp();
-        if (i < MT_N) {
-            mt[i] = v;
-            emit(i, v);
+    constexpr unsigned FULL = 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < kMtRegs; j++) {
+        // word i + 1: lane l + 1 of the same register; lane 31 takes lane 0's
+        // next register; word 623 (lane 15 of x[19]) the new word 0
+        uint32_t nxt;
+        if (j < kMtRegs - 1) nxt = __shfl_sync(FULL, lane == 0 ? x[j + 1] : x[j], (lane + 1) & 31);
+        else nxt = __shfl_sync(FULL, lane == 0 ? x[0] : x[j], lane == 15 ? 0 : (lane + 1) & 31);
+        // word i + 397 = 32(j + 12) + l + 13 (old), or the new word i - 227 =
+        // 32(j - 8) + l + 29
+        uint32_t far;
+        if (j < 7) {
+            far = __shfl_sync(FULL, lane >= 13 ? x[j + 12] : x[j + 13], (lane + 13) & 31);
+        } else if (j == 7) {
+            const uint32_t fo = __shfl_sync(FULL, x[19], (lane + 13) & 31);  // i = 224..226: words 621..623
+            const uint32_t fn = __shfl_sync(FULL, x[0], (lane + 29) & 31);   // i >= 227: new words 0..28
+            far = lane < 3 ? fo : fn;
+        } else {
+            far = __shfl_sync(FULL, lane >= 29 ? x[j - 8] : x[j - 7], (lane + 29) & 31);
         }
-        __syncwarp();
+        x[j] = mt_mix(x[j], nxt, far);
     }
 }
 
 template <int OUT, int LAYOUT>
 __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out_, uint64_t K)
 {
-    __shared__ uint32_t mt_s[kMtWarps][MT_N];
+    __shared__ __align__(16) uint32_t tb_s[OUT == OUT_NORMAL ? kMtWarps : 1][MT_N + 2];  // normals: tempered words, pair-aligned
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t gidx = static_cast<uint64_t>(blockIdx.x) * kMtWarps + w;
     const uint64_t n = p.n;
     if (gidx >= n) return;  // whole warps only: no block-wide barriers below
-    uint32_t *mt = mt_s[w];
     uint32_t *st = static_cast<uint32_t *>(p.s[0]) + gidx * MT_N;
-    for (int t = lane; t < MT_N; t += 32) mt[t] = st[t];
-    int mti = p.pos == 0 ? MT_N : static_cast<int>((p.pos - 1) % MT_N) + 1;
-    __syncwarp();
+    uint32_t x[kMtRegs];
+#pragma unroll
+    for (int j = 0; j < kMtRegs - 1; j++) x[j] = st[32 * j + lane];
+    x[kMtRegs - 1] = lane < MT_N - 32 * (kMtRegs - 1) ? st[32 * (kMtRegs - 1) + lane] : 0u;
+    // words of the current block already consumed (MT_N: refill first)
+    const int mti = p.pos == 0 ? MT_N : static_cast<int>((p.pos - 1) % MT_N) + 1;
 
     auto out_index = [&](uint64_t d) -> uint64_t {
         return LAYOUT == RNG_INSTANCE_MAJOR ? gidx * K + d : d * n + gidx;
     };
     uint32_t xacc = 0;
     float facc = 0.0f;
-    uint32_t pending = 0;  // tempered first word of a normal pair split across refills
+    uint32_t *tb = tb_s[OUT == OUT_NORMAL ? w : 0];
+    uint32_t pending = 0;  // normals: tempered word waiting for its partner (odd call index)
     const bool out_even = (reinterpret_cast<uintptr_t>(out_) & 7) == 0;
-    bool twisted = false;
-    uint64_t k = 0;
-    while (k < K) {
-        const bool refill = mti == MT_N;
-        const int cnt = static_cast<int>(K - k < static_cast<uint64_t>(MT_N - (refill ? 0 : mti))
-                                             ? K - k
-                                             : MT_N - (refill ? 0 : mti));
+
+    // Hands the words lo .. hi-1 of the state (call index kb for word lo) to
+    // the output.  FULL: the whole block (lo = 0, hi = MT_N).
+    auto emit = [&](auto full, int lo, int hi, uint64_t kb) {
+        constexpr bool FULLB = decltype(full)::value;
         if (OUT != OUT_NORMAL) {
-            auto put = [&](int t, uint32_t word) {
-                const uint32_t r = mt_temper(word);
-                const uint32_t bits = OUT == OUT_U32 ? r : __float_as_uint(u32_to_unit(r));
-                if (LAYOUT == RNG_XOR_REDUCE) xacc ^= bits;
-                else __stcs(static_cast<uint32_t *>(out_) + out_index(k + t), bits);
-            };
-            if (refill) {  // the refill emits its new words as they are made
-                mt_twist_warp(mt, lane, [&](int i, uint32_t v) {
-                    if (i < cnt) put(i, v);
-                });
-                mti = 0;
-                twisted = true;
-            } else {
-                for (int t = lane; t < cnt; t += 32) put(t, mt[mti + t]);
+#pragma unroll
+            for (int j = 0; j < kMtRegs; j++) {
+                const int wd = 32 * j + lane;
+                const bool in = FULLB ? (j < kMtRegs - 1 || wd < MT_N) : (wd >= lo && wd < hi);
+                if (in) {
+                    const uint32_t r = mt_temper(x[j]);
+                    const uint32_t bits = OUT == OUT_U32 ? r : __float_as_uint(u32_to_unit(r));
+                    if (LAYOUT == RNG_XOR_REDUCE) xacc ^= bits;
+                    else __stcs(static_cast<uint32_t *>(out_) + out_index(kb + (wd - lo)), bits);
+                }
             }
         } else {
-            // pairs come straight from the state words (tempered here): draw
-            // k - off + 2t and the next, off = 1 when a pair began in the
-            // previous chunk (its tempered first word is `pending`)
-            if (refill) {
-                mt_twist_warp(mt, lane, [](int, uint32_t) {});
-                mti = 0;
-                twisted = true;
+            // pairs start at even call indices: an odd kb continues the pending word
+            const int off = static_cast<int>(kb & 1);
+            if (off && lane == 0) tb[0] = pending;
+#pragma unroll
+            for (int j = 0; j < kMtRegs; j++) {
+                const int wd = 32 * j + lane;
+                const bool in = FULLB ? (j < kMtRegs - 1 || wd < MT_N) : (wd >= lo && wd < hi);
+                if (in) tb[off + wd - lo] = mt_temper(x[j]);
             }
             __syncwarp();
-            const int off = static_cast<int>(k & 1);
-            const uint64_t d0 = k - off;  // even draw index of the first pair
-            const int avail = cnt + off;
-            const int pairs = avail / 2;
-            for (int t = lane; t < pairs; t += 32) {
-                const int i0 = mti - off + 2 * t;  // state index of the pair's first word (mti - 1: pending)
-                const uint32_t a = i0 < mti ? pending : mt_temper(mt[i0 < mti ? mti : i0]);  // no read below mti
-                const uint32_t b = mt_temper(mt[i0 + 1]);
+            const int avail = off + hi - lo;
+            const uint64_t d0 = kb - off;  // call index of tb[0]
+            for (int t = lane; t < avail / 2; t += 32) {
+                const uint2 pr = reinterpret_cast<const uint2 *>(tb)[t];
                 float z0, z1;
-                box_muller(a, b, z0, z1);
+                box_muller(pr.x, pr.y, z0, z1);
                 if (LAYOUT == RNG_XOR_REDUCE) {
                     facc += z0;
                     facc += z1;
@@ -288,11 +268,29 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
                     __stcs(out + out_index(d0 + 2 * t + 1), z1);
                 }
             }
-            if (avail & 1) pending = mt_temper(mt[mti + cnt - 1]);  // same value in every lane
+            if (avail & 1) pending = tb[avail - 1];  // the same value in every lane
             __syncwarp();
         }
-        k += cnt;
-        mti += cnt;
+    };
+
+    uint64_t k = 0;
+    bool twisted = false;
+    if (K > 0 && mti < MT_N) {  // the rest of the current block
+        const int cnt = K < static_cast<uint64_t>(MT_N - mti) ? static_cast<int>(K) : MT_N - mti;
+        emit(std::false_type{}, mti, mti + cnt, 0);
+        k = cnt;
+    }
+#pragma unroll 1
+    while (K - k >= static_cast<uint64_t>(MT_N)) {
+        mt_twist_regs(x, lane);
+        twisted = true;
+        emit(std::true_type{}, 0, MT_N, k);
+        k += MT_N;
+    }
+    if (k < K) {
+        mt_twist_regs(x, lane);
+        twisted = true;
+        emit(std::false_type{}, 0, static_cast<int>(K - k), k);
     }
     if (LAYOUT == RNG_XOR_REDUCE) {
         if (OUT == OUT_NORMAL) {
@@ -304,8 +302,9 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
         }
     }
     if (twisted) {
-        __syncwarp();
-        for (int t = lane; t < MT_N; t += 32) st[t] = mt[t];
+#pragma unroll
+        for (int j = 0; j < kMtRegs - 1; j++) st[32 * j + lane] = x[j];
+        if (lane < MT_N - 32 * (kMtRegs - 1)) st[32 * (kMtRegs - 1) + lane] = x[kMtRegs - 1];
     }
 }
 

@@ -9,7 +9,9 @@
 // parallel (word n+j needs x_(n+j-r) and x_(n+j-s), both older than n for
 // j < s, Sec. 4).  With r + s slots the s new words never overwrite a word
 // another lane still reads in the same step, so a step needs no barrier
-// beyond the warp sync between steps.
+// beyond the warp sync between steps.  When the position is a multiple of
+// 32 a chunked form of the same recurrence runs instead (below): the same
+// words, fewer instructions per word.
 //
 // State in HBM: r words per generator, x_m in slot m mod r for the r most
 // recent m; the handle's position counts the words produced.
@@ -145,10 +147,165 @@ __global__ void __launch_bounds__(Lfib<R, S>::kBlock) k_generate_lfib(DevParams 
     }
 }
 
+// ----------------------------------------------------------- chunked form
+// The same recurrence computed in chunks of 32 consecutive words, one word
+// per lane: word m + j (j < 32) reads x_(m+j-r) and x_(m+j-s), made at least
+// s - 31 words earlier, so chunks need no step structure, and the U chunks
+// of a group (32U <= s) are mutually independent.  The ring has RS = 2^k >=
+// r + 32U slots (x_m at slot m mod RS) followed by a mirror of its first
+// 32U slots, written together with them: a group starting at a slot that
+// is a multiple of 32U then reads both operand windows and writes its words
+// with immediate offsets from three bases, without modular indices.  The
+// words it writes replace x_(m-RS), older than every word it reads (RS >=
+// r + 32U).  Used when the position is a multiple of 32; otherwise the
+// step form above runs.
+template <int R, int S>
+struct LfibChunked {
+    static constexpr int kU = 8;                       // chunks per group
+    static constexpr int kG = 32 * kU;                 // words per group
+    static_assert(kG <= S, "the chunks of a group must be independent");
+    static constexpr int kRS = R + kG <= 1024 ? 1024 : (R + kG <= 2048 ? 2048 : 4096);
+    static constexpr int kBuf = kRS + kG;              // ring and mirror
+    static constexpr int kWarps = 4;                   // generators per block
+    static constexpr int kBlock = 32 * kWarps;
+};
+
+template <int R, int S, int OUT, int LAYOUT>
+__global__ void __launch_bounds__(LfibChunked<R, S>::kBlock) k_generate_lfib_chunked(DevParams p, void *out_,
+                                                                                    uint64_t K)
+{
+    using F = LfibChunked<R, S>;
+    constexpr int RS = F::kRS, G = F::kG, U = F::kU, W = F::kWarps;
+    constexpr uint32_t MASK = RS - 1;
+    __shared__ __align__(16) uint32_t ring_s[W][F::kBuf];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t g = static_cast<uint64_t>(blockIdx.x) * W + w;
+    const uint64_t n = p.n;
+    if (g >= n) return;  // whole warps only
+    uint32_t *ring = ring_s[w];
+    uint32_t *st = static_cast<uint32_t *>(p.s[0]) + g * R;
+
+    // x_(pos-r+t) from state slot (pos + t) mod r to ring slot (pos - r + t) mod RS
+    const uint32_t q0 = static_cast<uint32_t>((p.pos + RS - R) & MASK);
+    const uint32_t sr0 = static_cast<uint32_t>(p.pos % R);
+    for (int t = lane; t < R; t += 32) {
+        const uint32_t q = (q0 + t) & MASK;
+        uint32_t b = sr0 + t;
+        b = b >= R ? b - R : b;
+        const uint32_t v = st[b];
+        ring[q] = v;
+        if (q < G) ring[q + RS] = v;
+    }
+    __syncwarp();
+
+    auto out_index = [&](uint64_t d) -> uint64_t {
+        return LAYOUT == RNG_INSTANCE_MAJOR ? g * K + d : d * n + g;
+    };
+    uint32_t xacc = 0;
+    float facc = 0.0f;
+    const bool out_even = (reinterpret_cast<uintptr_t>(out_) & 7) == 0;
+    auto put = [&](uint64_t d, uint32_t v) {
+        const uint32_t bits = OUT == OUT_U32 ? v : __float_as_uint(u32_to_unit(v));
+        if (LAYOUT == RNG_XOR_REDUCE) xacc ^= bits;
+        else __stcs(static_cast<uint32_t *>(out_) + out_index(d), bits);
+    };
+    // normal pair t of the words just written at slots pc.. (call index k..)
+    auto put_pair = [&](uint32_t pc, uint64_t k, int t) {
+        const uint2 pr = *reinterpret_cast<const uint2 *>(ring + pc + 2 * t);
+        float z0, z1;
+        box_muller(pr.x, pr.y, z0, z1);
+        if (LAYOUT == RNG_XOR_REDUCE) {
+            facc += z0;
+            facc += z1;
+        } else if (LAYOUT == RNG_INSTANCE_MAJOR && out_even) {
+            __stcs(reinterpret_cast<float2 *>(static_cast<float *>(out_) + out_index(k + 2 * t)), make_float2(z0, z1));
+        } else {
+            float *out = static_cast<float *>(out_);
+            __stcs(out + out_index(k + 2 * t), z0);
+            __stcs(out + out_index(k + 2 * t + 1), z1);
+        }
+    };
+
+    uint32_t pc = static_cast<uint32_t>(p.pos & MASK);  // slot of the next word, a multiple of 32
+    uint64_t k = 0;
+    while (k < K) {
+        if ((pc & (G - 1)) == 0 && K - k >= static_cast<uint64_t>(G)) {
+            const uint32_t *ra = ring + ((pc + RS - R) & MASK) + lane;
+            const uint32_t *rb = ring + ((pc + RS - S) & MASK) + lane;
+            uint32_t v[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) v[u] = ra[32 * u] + rb[32 * u];
+            uint32_t *rc = ring + pc + lane;
+#pragma unroll
+            for (int u = 0; u < U; u++) rc[32 * u] = v[u];
+            if (pc == 0) {
+#pragma unroll
+                for (int u = 0; u < U; u++) rc[RS + 32 * u] = v[u];
+            }
+            if (OUT != OUT_NORMAL) {
+#pragma unroll
+                for (int u = 0; u < U; u++) put(k + 32 * u + lane, v[u]);
+            }
+            __syncwarp();
+            if (OUT == OUT_NORMAL) {
+#pragma unroll
+                for (int u = 0; u < U / 2; u++) put_pair(pc, k, 32 * u + lane);
+            }
+            pc = (pc + G) & MASK;
+            k += G;
+        } else {  // one chunk: aligning the slot to a group, or the tail
+            const int cnt = K - k < 32 ? static_cast<int>(K - k) : 32;
+            const uint32_t v = ring[((pc + RS - R) & MASK) + lane] + ring[((pc + RS - S) & MASK) + lane];
+            if (lane < cnt) {
+                ring[pc + lane] = v;
+                if (pc < G) ring[RS + pc + lane] = v;
+                if (OUT != OUT_NORMAL) put(k + lane, v);
+            }
+            __syncwarp();
+            if (OUT == OUT_NORMAL && 2 * lane < cnt) put_pair(pc, k, lane);  // cnt is even for normals
+            pc = (pc + 32) & MASK;
+            k += cnt;
+        }
+    }
+    __syncwarp();
+    if (LAYOUT == RNG_XOR_REDUCE) {
+        if (OUT == OUT_NORMAL) {
+            for (int o = 16; o > 0; o >>= 1) facc += __shfl_down_sync(0xffffffffu, facc, o);
+            if (lane == 0) static_cast<float *>(out_)[g] = facc;
+        } else {
+            for (int o = 16; o > 0; o >>= 1) xacc ^= __shfl_down_sync(0xffffffffu, xacc, o);
+            if (lane == 0) static_cast<uint32_t *>(out_)[g] = xacc;
+        }
+    }
+    // x_(pos+K-r+t) from ring slot (pos + K - r + t) mod RS to state slot (pos + K + t) mod r
+    const uint32_t qK = static_cast<uint32_t>((p.pos + K + RS - R) & MASK);
+    const uint32_t srK = static_cast<uint32_t>((p.pos + K) % R);
+    for (int t = lane; t < R; t += 32) {
+        uint32_t b = srK + t;
+        b = b >= R ? b - R : b;
+        st[b] = ring[(qK + t) & MASK];
+    }
+}
+
 template <int R, int S, int OUT>
 int launch_out(const GenState &g, void *out, uint64_t K, int layout, cudaStream_t s)
 {
     const DevParams p = dev_params(g);
+    if ((g.pos & 31) == 0) {
+        using F = LfibChunked<R, S>;
+        const dim3 grid(static_cast<unsigned>((g.n + F::kWarps - 1) / F::kWarps));
+        switch (layout) {
+        case RNG_STEP_MAJOR:
+            k_generate_lfib_chunked<R, S, OUT, RNG_STEP_MAJOR><<<grid, F::kBlock, 0, s>>>(p, out, K);
+            break;
+        case RNG_INSTANCE_MAJOR:
+            k_generate_lfib_chunked<R, S, OUT, RNG_INSTANCE_MAJOR><<<grid, F::kBlock, 0, s>>>(p, out, K);
+            break;
+        default: k_generate_lfib_chunked<R, S, OUT, RNG_XOR_REDUCE><<<grid, F::kBlock, 0, s>>>(p, out, K); break;
+        }
+        RNGX_CHECK_LAUNCH();
+        return RNG_OK;
+    }
     constexpr int W = Lfib<R, S>::kWarps;
     const dim3 grid(static_cast<unsigned>((g.n + W - 1) / W));
     switch (layout) {

@@ -91,6 +91,55 @@ def test_lfib_64_generators_x_65536_bit_exact(R, torch_cuda, kind):
     assert np.array_equal(np.concatenate(g, axis=1), o)
 
 
+@pytest.mark.parametrize("kind", SHARED_KINDS)
+@pytest.mark.parametrize("layout", [0, 1, 2])
+def test_block_shared_mixed_forms_and_positions(R, torch_cuda, kind, layout):
+    # one handle, calls of every form in turn: positions that are multiples
+    # of 32 (the chunked lagged Fibonacci form, entered on and off its
+    # 256-word groups) and positions that are not (its step form); MT19937
+    # blocks entered part-way, normal pairs split across two refills
+    torch = torch_cuda
+    n = 5
+    calls = [("u32", 32), ("normal", 4160), ("f32", 96), ("normal", 1250), ("u32", 37), ("normal", 626),
+             ("u32", 27), ("normal", 2048), ("f32", 1311), ("normal", 8)]
+    o = O.generate(kind, SEED, n, sum(K for _, K in calls))
+    h = R.rng_create(kind, n)
+    try:
+        R.rng_seed(h, SEED)
+        start = 0
+        for form, K in calls:
+            ref = o[:, start:start + K]
+            start += K
+            dt = torch.int32 if form == "u32" else torch.float32
+            buf = torch.empty(n if layout == 2 else n * K, dtype=dt, device="cuda")
+            fn = {"u32": R.rng_generate_u32, "f32": R.rng_generate_f32, "normal": R.rng_generate_normal}[form]
+            fn(h, buf.data_ptr(), K, layout)
+            torch.cuda.synchronize()
+            a = buf.cpu().numpy()
+            if layout == 2:
+                if form == "u32":
+                    assert np.array_equal(a.view(np.uint32), np.bitwise_xor.reduce(ref, axis=1)), (form, K)
+                elif form == "f32":
+                    assert np.array_equal(a.view(np.uint32),
+                                          np.bitwise_xor.reduce(as_f32_oracle(ref).view(np.uint32), axis=1)), (form, K)
+                else:
+                    z = O.box_muller(ref)
+                    u = 2.0**-24
+                    tol = K * NORMAL_TOL + (K - 1) * u / (1 - (K - 1) * u) * np.abs(z).sum(axis=1) * 2
+                    assert np.all(np.abs(a.astype(np.float64) - z.sum(axis=1)) <= tol), (form, K)
+                continue
+            a = a.reshape(K, n).T if layout == 0 else a.reshape(n, K)
+            if form == "u32":
+                assert np.array_equal(a.view(np.uint32), ref), (form, K)
+            elif form == "f32":
+                assert np.array_equal(a, as_f32_oracle(ref)), (form, K)
+            else:
+                assert np.abs(a.astype(np.float64) - O.box_muller(ref)).max() <= NORMAL_TOL, (form, K)
+        assert R.rng_info(h)["position"] == start
+    finally:
+        R.rng_destroy(h)
+
+
 # ------------------------------------------------------ layouts and forms
 def ragged_n(kind):
     if kind == O.XS1024W:
