@@ -10,10 +10,11 @@ Lawson, 1961: iteratively reweighted least squares converging to the
 minimax fit) on Chebyshev nodes, in double precision, then rounded to
 float:
 
-  ln(1 + t), t in [sqrt(1/2) - 1, sqrt(2) - 1]   (after u = 2^e (1 + t),
-      the argument reduction of Cody and Waite, "Software Manual for the
-      Elementary Functions", 1980):  ln(1 + t) = t - t^2/2 + t^3 P(t),
-      fitted for relative error;
+  -2 ln(1 + t) = t Q(t), t in [sqrt(1/2) - 1, sqrt(2) - 1] (after u =
+      2^e (1 + t), the argument reduction of Cody and Waite, "Software
+      Manual for the Elementary Functions", 1980), Q(t) = -2 + t R(t) with
+      the constant term fixed at -2 and R fitted for relative error of Q
+      (the factor -2 of the Box-Muller radius is folded in);
   sin(2 pi x) = x S(x^2), cos(2 pi x) = C(x^2), x in [-1/8, 1/8] (after
       removing the nearest multiple of 1/4 from u2, an exact step on its 24
       fraction bits), fitted for absolute error.
@@ -28,7 +29,7 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LN_DEG, SIN_DEG, COS_DEG = 6, 3, 3  # degrees of P(t), S(y), C(y)
+LN_DEG, SIN_DEG, COS_DEG = 7, 3, 3  # degrees of R(t), S(y), C(y)
 
 
 def chebyshev_nodes(a, b, n=20000):
@@ -54,9 +55,10 @@ def lawson(target, basis, xs, scale, iters=80):
 def fit():
     t = chebyshev_nodes(np.sqrt(0.5) - 1, np.sqrt(2) - 1)
     t = t[np.abs(t) > 1e-6]
-    ln_c, ln_e = lawson(lambda t: (np.log1p(t) - t + t * t / 2) / t**3,
-                        [lambda t, k=k: t**k for k in range(LN_DEG + 1)], t,
-                        lambda t: np.abs(np.log1p(t)) / np.abs(t)**3)
+    r_c, ln_e = lawson(lambda t: (-2 * np.log1p(t) / t + 2) / t,
+                       [lambda t, k=k: t**k for k in range(LN_DEG + 1)], t,
+                       lambda t: np.abs(2 * np.log1p(t) / t) / np.abs(t))
+    ln_c = np.concatenate([[-2.0], r_c])
     x = chebyshev_nodes(0.0, 0.125)
     sin_c, sin_e = lawson(lambda x: np.sin(2 * np.pi * x) / x,
                           [lambda x, k=k: x**(2 * k) for k in range(SIN_DEG + 1)], x, lambda x: 1 / x)
@@ -75,7 +77,7 @@ def main():
     lines = [
         "// normal_poly.h -- written by fit_normal_poly.py (do not edit): polynomial",
         "// coefficients of the Box-Muller transform, fitted by Lawson's algorithm.",
-        f"// ln(1+t) = t - t^2/2 + t^3 P(t), t in [sqrt(1/2)-1, sqrt(2)-1]: max rel. error {ln_e:.2e}",
+        f"// -2 ln(1+t) = t Q(t), t in [sqrt(1/2)-1, sqrt(2)-1]: max rel. error of Q {ln_e:.2e}",
         f"// sin(2 pi x) = x S(x^2), x in [-1/8, 1/8]: max abs. error {sin_e:.2e}",
         f"// cos(2 pi x) = C(x^2), x in [-1/8, 1/8]: max abs. error {cos_e:.2e}",
         "// (errors of the double-precision polynomials; coefficients of increasing degree)",
@@ -84,7 +86,7 @@ def main():
         "namespace rngx {",
         "",
     ]
-    for name, c in (("kLnP", ln_c), ("kSinS", sin_c), ("kCosC", cos_c)):
+    for name, c in (("kLnQ", ln_c), ("kSinS", sin_c), ("kCosC", cos_c)):
         lines.append(f"constexpr int {name}Len = {len(c)};")
         lines.append(f"__device__ constexpr float {name}[{len(c)}] = {{")
         lines += [f"    {as_float_literal(v)}," for v in c]
@@ -93,7 +95,7 @@ def main():
     lines.append("}  // namespace rngx")
     with open(os.path.join(HERE, "normal_poly.h"), "w") as f:
         f.write("\n".join(lines) + "\n")
-    print(f"ln rel {ln_e:.2e}, sin abs {sin_e:.2e}, cos abs {cos_e:.2e}")
+    print(f"-2 ln rel {ln_e:.2e}, sin abs {sin_e:.2e}, cos abs {cos_e:.2e}")
 
 
 if __name__ == "__main__":

@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(kBlock) k_generate(DevParams p, void *out_, ui
     if (LAYOUT == RNG_STEP_MAJOR) {
         if (OUT == OUT_NORMAL) {
             float *out = static_cast<float *>(out_);
+#pragma unroll 2
             for (uint64_t k = 0; k < K; k += 2) {
                 const uint32_t r0 = g.next(), r1 = g.next();
                 float z0, z1;
@@ -164,10 +165,27 @@ constexpr int kMtWarps = 8;
 constexpr int kMtBlock = 32 * kMtWarps;
 constexpr int kMtRegs = (MT_N + 31) / 32;  // 20
 
+// Powers of two for the left shifts of the tempering, read from constant
+// memory so that the compiler keeps them as integer multiplies (y << b = y
+// 2^b), which issue to the FMA pipe: the refill and the tempering are
+// otherwise all shifts and logic operations on the ALU pipe, which they
+// saturate.  (Right shifts as high words of products measured slower.)
+__constant__ uint32_t c_mt_pow2[2] = {1u << 7, 1u << 15};
+
 __device__ __forceinline__ uint32_t mt_mix(uint32_t cur, uint32_t nxt, uint32_t far)
 {
     const uint32_t y = (cur & 0x80000000u) | (nxt & 0x7fffffffu);
-    return far ^ (y >> 1) ^ ((nxt & 1u) * 0x9908B0DFu);
+    return far ^ (y >> 1) ^ ((nxt & 1u) * 0x9908B0DFu);  // far ^ (y >> 1) ^ mag01[y & 1]
+}
+
+// MT19937 tempering (the left shifts as multiplies, see above).
+__device__ __forceinline__ uint32_t mt_temper_mul(uint32_t y)
+{
+    y ^= y >> 11;
+    y ^= (y * c_mt_pow2[0]) & 0x9D2C5680u;  // (y << 7) & b
+    y ^= (y * c_mt_pow2[1]) & 0xEFC60000u;  // (y << 15) & c
+    y ^= y >> 18;
+    return y;
 }
 
 // One refill of the register-resident state (all 32 lanes call it).
@@ -232,7 +250,7 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
                 const int wd = 32 * j + lane;
                 const bool in = FULLB ? (j < kMtRegs - 1 || wd < MT_N) : (wd >= lo && wd < hi);
                 if (in) {
-                    const uint32_t r = mt_temper(x[j]);
+                    const uint32_t r = mt_temper_mul(x[j]);
                     const uint32_t bits = OUT == OUT_U32 ? r : __float_as_uint(u32_to_unit(r));
                     if (LAYOUT == RNG_XOR_REDUCE) xacc ^= bits;
                     else __stcs(static_cast<uint32_t *>(out_) + out_index(kb + (wd - lo)), bits);
@@ -246,7 +264,7 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
             for (int j = 0; j < kMtRegs; j++) {
                 const int wd = 32 * j + lane;
                 const bool in = FULLB ? (j < kMtRegs - 1 || wd < MT_N) : (wd >= lo && wd < hi);
-                if (in) tb[off + wd - lo] = mt_temper(x[j]);
+                if (in) tb[off + wd - lo] = mt_temper_mul(x[j]);
             }
             __syncwarp();
             const int avail = off + hi - lo;
@@ -469,6 +487,22 @@ __global__ void __launch_bounds__(kXsBlock) k_generate_xs_reg(DevParams p, void 
     }
 }
 
+// Normals of the 1024-bit generator take the one-thread-per-state form only
+// when there are states enough for about 200 per SM (6 warps): each thread
+// then has 32 independent Box-Muller pairs per two steps, which costs less
+// than the six shuffles per word of the lane-per-instance form; with fewer
+// threads that form's parallelism wins (measured on GB300: 2^20 instances,
+// 1.66 against 1.83 ms per 2^30 normals; 2^18 instances, 4.8 against 1.8
+// ms per 2^30).
+inline bool xs_reg_normals(uint64_t n)
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return false;
+    return n / 32 >= 200ull * static_cast<uint64_t>(sms);
+}
+
 template <int KIND, int OUT>
 int launch_kind_out(const GenState &g, void *out, uint64_t K, int layout, cudaStream_t s)
 {
@@ -480,10 +514,8 @@ int launch_kind_out(const GenState &g, void *out, uint64_t K, int layout, cudaSt
         case RNG_INSTANCE_MAJOR: k_generate_mt<OUT, RNG_INSTANCE_MAJOR><<<grid, kMtBlock, 0, s>>>(p, out, K); break;
         default: k_generate_mt<OUT, RNG_XOR_REDUCE><<<grid, kMtBlock, 0, s>>>(p, out, K); break;
         }
-    } else if (KIND == RNG_XS1024W && OUT != OUT_NORMAL && layout != RNG_INSTANCE_MAJOR &&
-               (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
-        // (normals stay on the lane-per-instance form: 32 Box-Muller pairs per
-        // thread and step leave too few threads to hide their latency)
+    } else if (KIND == RNG_XS1024W && layout != RNG_INSTANCE_MAJOR &&
+               (reinterpret_cast<uintptr_t>(out) & 15) == 0 && (OUT != OUT_NORMAL || xs_reg_normals(g.n))) {
         const dim3 grid(static_cast<unsigned>((g.n / 32 + kXsBlock - 1) / kXsBlock));
         if (layout == RNG_STEP_MAJOR) k_generate_xs_reg<OUT, RNG_STEP_MAJOR><<<grid, kXsBlock, 0, s>>>(p, out, K);
         else k_generate_xs_reg<OUT, RNG_XOR_REDUCE><<<grid, kXsBlock, 0, s>>>(p, out, K);

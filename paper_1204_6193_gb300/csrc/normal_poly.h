@@ -1,6 +1,6 @@
 // normal_poly.h -- written by fit_normal_poly.py (do not edit): polynomial
 // coefficients of the Box-Muller transform, fitted by Lawson's algorithm.
-// ln(1+t) = t - t^2/2 + t^3 P(t), t in [sqrt(1/2)-1, sqrt(2)-1]: max rel. error 3.15e-08
+// -2 ln(1+t) = t Q(t), t in [sqrt(1/2)-1, sqrt(2)-1]: max rel. error of Q 3.00e-08
 // sin(2 pi x) = x S(x^2), x in [-1/8, 1/8]: max abs. error 1.21e-09
 // cos(2 pi x) = C(x^2), x in [-1/8, 1/8]: max abs. error 2.76e-08
 // (errors of the double-precision polynomials; coefficients of increasing degree)
@@ -8,15 +8,17 @@
 
 namespace rngx {
 
-constexpr int kLnPLen = 7;
-__device__ constexpr float kLnP[7] = {
-    0x1.5556d80000000p-2f /* 0.333339095 */,
-    -0x1.0003820000000p-2f /* -0.250013381 */,
-    0x1.98d7f20000000p-3f /* 0.199630633 */,
-    -0x1.53824a0000000p-3f /* -0.16577585 */,
-    0x1.3174640000000p-3f /* 0.149147779 */,
-    -0x1.2432b00000000p-3f /* -0.142674804 */,
-    0x1.645e3e0000000p-4f /* 0.0870039389 */,
+constexpr int kLnQLen = 9;
+__device__ constexpr float kLnQ[9] = {
+    -0x1.0000000000000p+1f /* -2 */,
+    0x1.fffffa0000000p-1f /* 0.999999821 */,
+    -0x1.5556f40000000p-1f /* -0.666679025 */,
+    0x1.00049a0000000p-1f /* 0.500035107 */,
+    -0x1.98d2c00000000p-2f /* -0.399241447 */,
+    0x1.535d340000000p-2f /* 0.331410229 */,
+    -0x1.3185300000000p-2f /* -0.298359632 */,
+    0x1.2504820000000p-2f /* 0.286150008 */,
+    -0x1.65c6ee0000000p-3f /* -0.174695835 */,
 };
 
 constexpr int kSinSLen = 4;

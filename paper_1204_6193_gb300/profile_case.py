@@ -4,6 +4,13 @@ Ising launch, for profiling a single kernel under a profiler on a small case.
     python -m paper_1204_6193_gb300.profile_case --kind xs1024w --form u32 --n 262144 --K 256 --reps 3
     python -m paper_1204_6193_gb300.profile_case --kind xorwow --ising 1024 --sweeps 200
     python -m paper_1204_6193_gb300.profile_case --kind xorwow --ising 1024 --sweeps 2 --hits 100 --strips 256
+    python -m paper_1204_6193_gb300.profile_case --all --outputs 268435456
+
+--all runs one call of every generator kind and form of the bulk workload
+with its instance count (per-thread kinds 2^20 instances step-major,
+block-shared kinds 2^15 generators instance-major, one per warp) and
+--outputs / instances draws, in the order kinds x (u32, f32, normal, u32
+XOR-reduced).
 """
 import argparse
 
@@ -25,7 +32,12 @@ def main():
     ap.add_argument("--sweeps", type=int, default=200, help="sweeps (or multi-hit rounds)")
     ap.add_argument("--hits", type=int, default=0, help="k > 0: multi-hit rounds of k sweeps per strip phase")
     ap.add_argument("--strips", type=int, default=256, help="row strips of the multi-hit update")
+    ap.add_argument("--all", action="store_true", help="one call of every kind and form")
+    ap.add_argument("--outputs", type=int, default=1 << 28, help="outputs per call with --all")
     a = ap.parse_args()
+    if a.all:
+        run_all(a.outputs)
+        return
     kind = {v: k for k, v in R.KIND_NAMES.items()}[a.kind]
     if a.ising:
         layout = R.ISING_INT8 if a.spins == "int8" else R.ISING_MULTISPIN32
@@ -53,6 +65,24 @@ def main():
             R.rng_generate_u32(h, out.data_ptr(), a.K, R.RNG_XOR_REDUCE)
     torch.cuda.synchronize()
     R.rng_destroy(h)
+    print("ok")
+
+
+def run_all(outputs: int) -> None:
+    shared = {R.RNG_MT19937_SHARED, R.RNG_LFIB521, R.RNG_LFIB1279}
+    out = torch.empty(outputs, dtype=torch.int32, device="cuda")
+    for kind in sorted(R.KIND_NAMES):
+        n = 1 << 15 if kind in shared else 1 << 20
+        K = outputs // n
+        layout = R.RNG_INSTANCE_MAJOR if kind in shared else R.RNG_STEP_MAJOR
+        h = R.rng_create(kind, n)
+        R.rng_seed(h, 12345)
+        R.rng_generate_u32(h, out.data_ptr(), K, layout)
+        R.rng_generate_f32(h, out.data_ptr(), K, layout)
+        R.rng_generate_normal(h, out.data_ptr(), K, layout)
+        R.rng_generate_u32(h, out.data_ptr(), K, R.RNG_XOR_REDUCE)
+        torch.cuda.synchronize()
+        R.rng_destroy(h)
     print("ok")
 
 

@@ -445,6 +445,33 @@ def test_full_size_sampled(R, torch_cuda, kind):
         R.rng_destroy(h)
 
 
+@pytest.mark.parametrize("kind", THREAD_KINDS)
+def test_full_size_normals_sampled(R, torch_cuda, kind):
+    """Normals with the bench's 2^20 instances (the 1024-bit generator then
+    takes its one-thread-per-state form), on sampled instances."""
+    torch = torch_cuda
+    n, K = 1 << 20, 16
+    flags = O.SEED_SUBSTREAM if kind == O.XS1024W else 0
+    h = R.rng_create(kind, n, flags)
+    try:
+        R.rng_seed(h, SEED)
+        R.rng_generate_u32(h, torch.empty(n * 2, dtype=torch.int32, device="cuda").data_ptr(), 2, 0)
+        buf = torch.empty(n * K, dtype=torch.float32, device="cuda")
+        R.rng_generate_normal(h, buf.data_ptr(), K, R.RNG_STEP_MAJOR)
+        red = torch.empty(n, dtype=torch.float32, device="cuda")
+        R.rng_generate_normal(h, red.data_ptr(), K, R.RNG_XOR_REDUCE)
+        torch.cuda.synchronize()
+        view = buf.view(K, n)
+        rng = np.random.default_rng(100 + kind)
+        for i in sorted({0, 31, 32, n - 1, *rng.integers(0, n, 12).tolist()}):
+            o = O.generate(kind, SEED, n, 2 + 2 * K, flags=flags, i_lo=i, i_hi=i + 1)[0]
+            assert np.abs(view[:, i].cpu().numpy().astype(np.float64) - O.box_muller(o[2:2 + K])).max() <= NORMAL_TOL, i
+            z = O.box_muller(o[2 + K:])
+            assert abs(float(red[i]) - z.sum()) <= K * NORMAL_TOL + 1e-5 * np.abs(z).sum(), i
+    finally:
+        R.rng_destroy(h)
+
+
 def test_mwc_full_table_matches_oracle(R, torch_cuda):
     n = 1 << 20
     assert np.array_equal(R.rng_mwc_multipliers(0, n), O.mwc_multipliers(n))
