@@ -162,6 +162,21 @@ def ncu_inst_per_output(kernel_key: str):
     return float(v) if v is not None else None
 
 
+def bulk_config(world: int) -> dict:
+    """The bulk workload, as both arms name it."""
+    return {
+        "workload": "bulk generation: 2^20 resident instances x 1024 draws per call (MT19937 and the "
+                    "lagged Fibonacci (521, 353), (1279, 861): 32768 warp-shared generators x 2^15), "
+                    "10 generators x {u32, f32, normal} written to HBM + u32 consumed in registers "
+                    "(XOR reduce); 40 calls per step",
+        "instances_per_gpu": N_INST, "draws_per_call": K_DRAWS,
+        "outputs_per_step_per_gpu": N_KINDS * len(FORMS) * N_INST * K_DRAWS,
+        "layout": "step-major (block-shared kinds: instance-major)",
+        "l2": "no flush: every write call streams 4 GiB (> 129 MB L2)", "seed": hex(SEED),
+        "parallelism": f"instance shards x{world}",
+    }
+
+
 # ------------------------------------------------------------------ GPU arm
 class Bulk:
     def __init__(self, R, torch, rank, world):
@@ -408,16 +423,7 @@ def run_gpu(args):
             "vs_baseline": None,
             "dtype": "u32",
             "data": "synthetic",
-            "config": {
-                "workload": "bulk generation: 2^20 resident instances x 1024 draws per call (MT19937 and the "
-                            "lagged Fibonacci (521, 353), (1279, 861): 32768 warp-shared generators x 2^15), "
-                            "10 generators x {u32, f32, normal} written to HBM + u32 consumed in registers "
-                            "(XOR reduce); 40 calls per step",
-                "instances_per_gpu": N_INST, "draws_per_call": K_DRAWS, "outputs_per_step_per_gpu":
-                    outputs_per_step_rank, "layout": "step-major (block-shared kinds: instance-major)",
-                "l2": "no flush: every write call streams 4 GiB (> 129 MB L2)", "seed": hex(SEED),
-                "parallelism": f"instance shards x{world}",
-            },
+            "config": bulk_config(world),
             "roofline": roofline,
             "issue_peaks": {k: round(v / 1e12, 2) for k, v in issue_peaks.items()} | {
                 "unit": "T thread-instructions/s (whole GPU)", "source": "rng_issue_peaks microbenchmark"},
@@ -828,12 +834,11 @@ def run_reference(args):
     return {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "Gnum/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / len(times), 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"bulk generation sample (CPU oracle): {N_KINDS} generators x {{u32, f32, "
-                                   f"normal, u32 xor}} on a bounded sample per step",
-                       "outputs_per_step": total // len(times)},
+            "config": bulk_config(world),
             "cpu_baseline": {"value": round(v, 4), "unit": "Gnum/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{per_form // 4} outputs per kind and form per step, instances split "
-                                       f"over {cores} threads"},
+                             "sample": f"each step {per_form // 4} outputs per kind and form of the bulk workload "
+                                       f"({total // len(times)} outputs), C oracle, instances split over {cores} "
+                                       f"threads"},
             "e2e": {"value": round(v, 4), "unit": "Gnum/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
