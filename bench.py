@@ -853,7 +853,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ising", action="store_true")
-    ap.add_argument("--ising-sweeps", type=int, default=2000)
+    ap.add_argument("--ising-sweeps", type=int, default=100000)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-sweeps", type=int, default=10000)
     ap.add_argument("--no-serve", action="store_true")

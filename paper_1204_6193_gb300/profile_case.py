@@ -32,6 +32,7 @@ def main():
     ap.add_argument("--sweeps", type=int, default=200, help="sweeps (or multi-hit rounds)")
     ap.add_argument("--hits", type=int, default=0, help="k > 0: multi-hit rounds of k sweeps per strip phase")
     ap.add_argument("--strips", type=int, default=256, help="row strips of the multi-hit update")
+    ap.add_argument("--launch", default="", help="threads,ctas_per_sm,min_sites_per_block of the Ising launch")
     ap.add_argument("--all", action="store_true", help="one call of every kind and form")
     ap.add_argument("--outputs", type=int, default=1 << 28, help="outputs per call with --all")
     a = ap.parse_args()
@@ -42,6 +43,8 @@ def main():
     if a.ising:
         layout = R.ISING_INT8 if a.spins == "int8" else R.ISING_MULTISPIN32
         h = R.ising_create(a.ising, 0.4406867935097715, layout, kind, 0, 12345, 2)
+        if a.launch:
+            R.ising_set_launch(h, *(int(v) for v in a.launch.split(",")))
         if a.hits:
             R.ising_sweep_multihit(h, a.sweeps, a.hits, a.strips)
         else:
