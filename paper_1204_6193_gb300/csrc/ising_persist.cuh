@@ -35,6 +35,7 @@ struct PersistArgs {
     int32_t mute_seg;          // test hook: this segment never publishes (-1: none)
     uint64_t wait_budget_ns;   // limit of one neighbour wait
     uint32_t k_hits;           // 0: exact checkerboard; k > 0: multi-hit rounds of k sweeps per strip phase
+    uint32_t mh_aligned;       // multi-hit plan with one resident stream of each coarse colour per thread
 };
 
 struct SegLocal {              // per-segment constants held in shared memory
@@ -369,6 +370,17 @@ __device__ __forceinline__ void update_pass(uint8_t *smem, const SegLocal *S, ui
     }
 }
 
+// Resident states: a pass updates the slots whose warp it selects (sel as
+// in warp_selected).
+template <int KIND, int LAYOUT, int SMAX>
+__device__ __forceinline__ void update_resident(uint8_t *smem, const SegLocal *S, Gen<KIND> (&gen)[SMAX],
+                                                const StreamSlot (&slot)[SMAX], int c, int lane, int sel)
+{
+#pragma unroll
+    for (int k = 0; k < SMAX; k++)
+        if (warp_selected(slot[k], sel)) update_slot<KIND, LAYOUT>(smem, S[slot[k].seg], slot[k], gen[k], c, lane);
+}
+
 // Halo buffer: per strip, 2 slots x 2 rows (first, last) x 2 colours.
 __device__ __forceinline__ uint64_t *halo_row(const PersistArgs &a, int gid, uint32_t slot, int row, int colour)
 {
@@ -449,15 +461,20 @@ __device__ void measure_strips(uint8_t *smem, const SegLocal *S, uint32_t nseg, 
     }
 }
 
-// MH selects the multi-hit round loop (a.k_hits > 0) at compile time, so
-// that the exact-checkerboard kernel keeps its own register allocation.
-// Launch bounds: the exact-checkerboard kernel runs multi-slot shapes with
-// at most 512 threads; the multi-hit kernel also runs two slots (one stream
-// in each coarse colour) with up to 1024 threads.
-template <int KIND, int LAYOUT, int SMAX, bool MH>
-__global__ void __launch_bounds__(SMAX >= (MH ? 4 : 2) ? 512 : 1024, (!MH && SMAX == 2) ? 2 : 1)
+// MODE selects the exact checkerboard (0) or the multi-hit round loop
+// (a.k_hits > 0) at compile time, so that each keeps its own register
+// allocation: MODE 1 handles any slot layout, MODE 2 (SMAX = 2 only) the
+// usual multi-hit plan, where thread slot 0 is a stream of coarse colour 0
+// and slot 1 one of coarse colour 1, so that a phase updates one fixed slot
+// with no per-slot selection (with 1024 threads the general loop would not
+// fit the 64 registers a thread has).  Launch bounds: the exact-checkerboard
+// kernel runs multi-slot shapes with at most 512 threads; the multi-hit
+// kernel also runs two slots with up to 1024 threads.
+template <int KIND, int LAYOUT, int SMAX, int MODE>
+__global__ void __launch_bounds__(SMAX >= (MODE ? 4 : 2) ? 512 : 1024, (!MODE && SMAX == 2) ? 2 : 1)
     k_ising_persist(PersistArgs a)
 {
+    constexpr bool MH = MODE != 0;
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ SegLocal S[kPersistMaxSegs];
     __shared__ uint64_t prefix_end;
@@ -531,8 +548,9 @@ __global__ void __launch_bounds__(SMAX >= (MH ? 4 : 2) ? 512 : 1024, (!MH && SMA
                 const uint32_t h = static_cast<uint32_t>(2 * t + c);
                 const uint64_t pos_off = (2 * t + c) * static_cast<uint64_t>(S[0].G);
                 // warps that hold a strip's first or last row go first ...
-                update_pass<KIND, LAYOUT, SMAX>(smem, S, nseg, prefix_end, resident, gen, slot, pos_off, c, lane,
-                                                SEL_BOUNDARY);
+                if (resident) update_resident<KIND, LAYOUT, SMAX>(smem, S, gen, slot, c, lane, SEL_BOUNDARY);
+                else update_pass<KIND, LAYOUT, SMAX>(smem, S, nseg, prefix_end, false, gen, slot, pos_off, c, lane,
+                                                     SEL_BOUNDARY);
                 __syncthreads();
                 // ... their rows are published (a whole lattice copies them into
                 // its own halo rows) ...
@@ -555,8 +573,9 @@ __global__ void __launch_bounds__(SMAX >= (MH ? 4 : 2) ? 512 : 1024, (!MH && SMA
                     }
                 }
                 // ... the interior rows are updated while those words travel ...
-                update_pass<KIND, LAYOUT, SMAX>(smem, S, nseg, prefix_end, resident, gen, slot, pos_off, c, lane,
-                                                SEL_INTERIOR);
+                if (resident) update_resident<KIND, LAYOUT, SMAX>(smem, S, gen, slot, c, lane, SEL_INTERIOR);
+                else update_pass<KIND, LAYOUT, SMAX>(smem, S, nseg, prefix_end, false, gen, slot, pos_off, c, lane,
+                                                     SEL_INTERIOR);
                 // ... and the neighbours' rows are polled into the halo rows
                 if (any_split) {
                     const uint64_t t0 = global_ns();
@@ -580,6 +599,18 @@ __global__ void __launch_bounds__(SMAX >= (MH ? 4 : 2) ? 512 : 1024, (!MH && SMA
         // strips stay fixed; then they publish both colours of their first
         // and last rows, which the other strips poll before their phase
         const uint32_t k = a.k_hits;
+        if constexpr (MODE == 2) {
+            // the host chose this kernel for a plan with one resident slot of
+            // each coarse colour per thread, slot 0 in colour 0: check it
+            bool ok = resident;
+#pragma unroll
+            for (int kk = 0; kk < SMAX; kk++)
+                if ((slot[kk].flags & SL_IN) && ((slot[kk].flags & SL_COARSE) != 0) != (kk == 1)) ok = false;
+            if (!__syncthreads_and(ok)) {
+                if (threadIdx.x == 0) atomicCAS(a.err, 0, RNG_EINVAL);
+                goto done;
+            }
+        }
         for (uint64_t t = 0; t < a.n_sweeps; t++) {
             for (int C = 0; C < 2; C++) {
                 const uint32_t ph = static_cast<uint32_t>(2 * t + C);
@@ -595,12 +626,38 @@ __global__ void __launch_bounds__(SMAX >= (MH ? 4 : 2) ? 512 : 1024, (!MH && SMA
                     __syncthreads();
                     if (s_abort) goto done;
                 }
-                for (uint32_t hit = 0; hit < k; hit++) {
-                    for (int c = 0; c < 2; c++) {
-                        const uint64_t pos_off = (2 * (t * k + hit) + c) * static_cast<uint64_t>(S[0].G);
-                        update_pass<KIND, LAYOUT, SMAX>(smem, S, nseg, prefix_end, resident, gen, slot, pos_off, c,
-                                                        lane, SEL_COARSE0 + C);
-                        __syncthreads();
+                if constexpr (MODE == 2) {
+                    // slot C is the thread's stream of coarse colour C
+                    if (C == 0) {
+                        const bool act = (slot[0].flags & SL_WARP_IN) != 0;
+                        const SegLocal &sg = S[slot[0].seg];
+                        for (uint32_t hit = 0; hit < k; hit++) {
+                            if (act) update_slot<KIND, LAYOUT>(smem, sg, slot[0], gen[0], 0, lane);
+                            __syncthreads();
+                            if (act) update_slot<KIND, LAYOUT>(smem, sg, slot[0], gen[0], 1, lane);
+                            __syncthreads();
+                        }
+                    } else {
+                        const bool act = (slot[SMAX - 1].flags & SL_WARP_IN) != 0;
+                        const SegLocal &sg = S[slot[SMAX - 1].seg];
+                        for (uint32_t hit = 0; hit < k; hit++) {
+                            if (act) update_slot<KIND, LAYOUT>(smem, sg, slot[SMAX - 1], gen[SMAX - 1], 0, lane);
+                            __syncthreads();
+                            if (act) update_slot<KIND, LAYOUT>(smem, sg, slot[SMAX - 1], gen[SMAX - 1], 1, lane);
+                            __syncthreads();
+                        }
+                    }
+                } else {
+                    for (uint32_t hit = 0; hit < k; hit++) {
+                        for (int c = 0; c < 2; c++) {
+                            const uint64_t pos_off = (2 * (t * k + hit) + c) * static_cast<uint64_t>(S[0].G);
+                            if (resident)
+                                update_resident<KIND, LAYOUT, SMAX>(smem, S, gen, slot, c, lane, SEL_COARSE0 + C);
+                            else
+                                update_pass<KIND, LAYOUT, SMAX>(smem, S, nseg, prefix_end, false, gen, slot, pos_off,
+                                                                c, lane, SEL_COARSE0 + C);
+                            __syncthreads();
+                        }
                     }
                 }
                 for (uint32_t j = 0; j < nseg; j++)

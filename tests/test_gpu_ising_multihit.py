@@ -101,6 +101,28 @@ def test_launch_chunks_and_split_calls(R):
             assert obs["acc"] == acc.tolist() and obs["n_meas"] == nm
 
 
+@pytest.mark.parametrize("kind", [O.XORWOW, O.XS1024W, O.PHILOX4X32_7])
+@pytest.mark.parametrize("layout", [0, 1])
+def test_fixed_slot_and_general_phase_loops_agree(R, kind, layout):
+    # the usual plan (one stream of each coarse colour per thread: 16 strips
+    # of 1024 streams, two per block) runs the fixed-slot phase loop; a set
+    # launch shape of 256 threads runs the general loop, its states streamed
+    # through L2: same spins and accumulators as the oracle
+    L, k, n_strips = 256, 5, 16
+    ref, acc, nm = O.ising_run_multihit(L, 0.43, kind, SEED, 3, k=k, n_strips=n_strips, measure_every=1)
+    for shape in (None, (256, 1, 0)):
+        h = R.ising_create(L, 0.43, layout, kind, 0, SEED, 2)
+        try:
+            if shape:
+                R.ising_set_launch(h, *shape)
+            R.ising_sweep_multihit(h, 3, k, n_strips, 1)
+            obs = R.ising_observables(h)
+            assert np.array_equal(R.ising_get_spins(h), ref), shape
+            assert obs["acc"] == acc.tolist() and obs["n_meas"] == nm, shape
+        finally:
+            R.ising_destroy(h)
+
+
 def test_degenerate_temperatures(R):
     # beta = 0 accepts every proposal: a round of odd k flips every site
     spins, _ = gpu_multihit(R, 64, 0.0, O.XORWOW, 1, k=3, n_strips=4, layout=1)
