@@ -43,6 +43,8 @@ struct SegLocal {              // per-segment constants held in shared memory
     uint32_t pstride;          // plane 1 - plane 0 offset in shared memory
     int32_t up, down, gid;
     uint64_t s0, prefix, T4, T8;
+    uint32_t t4, t8;           // T4, T8 below 2^32 (beta > 0)
+    int32_t a_max;             // flips with a <= a_max always: 0, or 2 / 4 where T4 / T8 = 2^32
     uint64_t n_valid, n_inst;  // streams with sites; generator instances
     DevParams rng;             // the lattice's generator (position at launch start)
 };
@@ -197,6 +199,8 @@ enum : uint32_t {
     SL_WARP_BND = 8u,   // some lane of the warp holds a first or last row of the strip
     SL_COARSE = 16u,    // the strip's coarse colour is 1 (multi-hit phases)
     SL_ODD_ROW = 32u,   // the sites' row is odd
+    SL_ROW_FIRST = 64u, // the slot's sites start its row (left neighbour wraps)
+    SL_ROW_LAST = 128u, // the slot's sites end its row (right neighbour wraps)
 };
 
 template <int LAYOUT>
@@ -209,7 +213,8 @@ __device__ __forceinline__ void finish_slot(const SegLocal &sg, bool in, bool va
     const bool wi = __any_sync(0xffffffffu, in);
     const bool wb = __any_sync(0xffffffffu, in && (row == sg.y0 || row + 1 == sg.y0 + sg.R));
     o.flags = (in ? SL_IN : 0u) | (val ? SL_VAL : 0u) | (wi ? SL_WARP_IN : 0u) | (wb ? SL_WARP_BND : 0u) |
-              (sg.coarse ? SL_COARSE : 0u) | ((row & 1u) ? SL_ODD_ROW : 0u);
+              (sg.coarse ? SL_COARSE : 0u) | ((row & 1u) ? SL_ODD_ROW : 0u) | (o.xh0 == 0 ? SL_ROW_FIRST : 0u) |
+              (o.xh0 + sg.G == sg.half ? SL_ROW_LAST : 0u);
 }
 
 template <int LAYOUT>
@@ -252,15 +257,20 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
             // neighbour; draws are taken in site order before either update
             const uint32_t r0 = gen.next(), r1 = gen.next();
             if (!sl.val()) return;
-            const uint32_t xh = sl.xh0;
-            const uint32_t li = p ? xh : (xh == 0 ? half - 1 : xh - 1);      // left of site xh
-            const uint32_t ri = p ? (xh + 2 == half ? 0 : xh + 2) : xh + 1;  // right of site xh + 1
-            const int mid = o[xh + p];
-            const int s0 = own[xh], s1 = own[xh + 1];
-            const int a0 = s0 * (o[li] + mid + ou[xh] + od[xh]);
-            const int a1 = s1 * (mid + o[ri] + ou[xh + 1] + od[xh + 1]);
-            if (accept_a(a0, r0, T4, T8)) own[xh] = static_cast<int8_t>(-s0);
-            if (accept_a(a1, r1, T4, T8)) own[xh + 1] = static_cast<int8_t>(-s1);
+            const int8_t *ox = o + sl.xh0;
+            int8_t *ow = own + sl.xh0;
+            const int hf = static_cast<int>(half);
+            const int dl = p ? 0 : ((sl.flags & SL_ROW_FIRST) ? hf - 1 : -1);
+            const int dr = p ? ((sl.flags & SL_ROW_LAST) ? 2 - hf : 2) : 1;
+            const int mid = ox[p];
+            const int s0 = ow[0], s1 = ow[1];
+            const int a0 = s0 * (ox[dl] + mid + ox[-hf] + ox[hf]);
+            const int a1 = s1 * (mid + ox[dr] + ox[1 - hf] + ox[1 + hf]);
+            // a <= 0 always flips (and every a where T = 2^32, beta = 0)
+            const int am = sg.a_max;
+            const uint32_t t4 = sg.t4, t8 = sg.t8;
+            if (a0 <= am || r0 < (a0 == 2 ? t4 : t8)) ow[0] = static_cast<int8_t>(-s0);
+            if (a1 <= am || r1 < (a1 == 2 ? t4 : t8)) ow[1] = static_cast<int8_t>(-s1);
             return;
         }
         for (uint32_t g = 0; g < G; g++) {
@@ -501,6 +511,9 @@ __global__ void __launch_bounds__(SMAX >= (MODE ? 4 : 2) ? 512 : 1024, (!MODE &&
         s.s0 = d.s0;
         s.T4 = l.T4;
         s.T8 = l.T8;
+        s.t4 = static_cast<uint32_t>(l.T4 > 0xffffffffull ? 0xffffffffull : l.T4);
+        s.t8 = static_cast<uint32_t>(l.T8 > 0xffffffffull ? 0xffffffffull : l.T8);
+        s.a_max = l.T8 > 0xffffffffull ? 4 : (l.T4 > 0xffffffffull ? 2 : 0);
         s.n_valid = l.nstreams;
         s.n_inst = l.rng.n;
         s.rng = l.rng;
