@@ -211,7 +211,7 @@ struct IsingLat {
 // Persistent launch plan of one group of lattices of one generator kind.
 struct Plan {
     int kind = 0, layout = 0, smax = 1;
-    bool mh_aligned = false;  // multi-hit: one resident stream of each coarse colour per thread
+    bool fixed_slots = false;  // each thread slot has a fixed role (see the kernel's modes 2 and 3)
     unsigned nblocks = 0, threads = 0;
     size_t smem = 0;
     uint32_t nsegs = 0, halo_row_bytes = 0;
@@ -511,7 +511,7 @@ int materialize_plan(ising_t h, int kind, int layout, const std::vector<std::vec
         threads = 512;
         spt = std::min<uint64_t>(4, (max_streams + threads - 1) / threads);
     }
-    bool mh_aligned = false;
+    bool fixed = false;  // fixed slot roles (the kernel's modes 2 and 3)
     if (multihit && !h->cfg_threads && max_streams <= 2048) {
         // one stream of each coarse colour per thread: every thread works
         // in both phases (the multi-hit kernel runs two slots at up to 1024)
@@ -519,20 +519,36 @@ int materialize_plan(ising_t h, int kind, int layout, const std::vector<std::vec
         spt = 2;
         // blocks hold a coarse-0 strip then a coarse-1 strip of `threads`
         // streams each: slot 0 and slot 1 of every thread, in that order
-        mh_aligned = true;
-        for (size_t b = 0; b < blocks.size() && mh_aligned; b++) {
+        fixed = true;
+        for (size_t b = 0; b < blocks.size() && fixed; b++) {
             const auto &blk = blocks[b];
-            if (blk.size() != 2) mh_aligned = false;
-            for (size_t i = 0; i < blk.size() && mh_aligned; i++) {
+            if (blk.size() != 2) fixed = false;
+            for (size_t i = 0; i < blk.size() && fixed; i++) {
                 const SegDev &d = segs[cta[b] + i];
-                if (d.coarse != i || d.s1 - d.s0 != threads) mh_aligned = false;
+                if (d.coarse != i || d.s1 - d.s0 != threads) fixed = false;
             }
         }
     }
     P.kind = kind;
     P.layout = layout;
     P.smax = spt <= 1 ? 1 : (spt <= 2 ? 2 : 4);
-    P.mh_aligned = mh_aligned && P.smax == 2;
+    if (!multihit && P.smax == 2) {
+        // exact checkerboard: one strip per block whose first and last rows
+        // fill at most one slot of every thread and the rows between another
+        fixed = true;
+        for (size_t b = 0; b < blocks.size() && fixed; b++) {
+            if (blocks[b].size() != 1) {
+                fixed = false;
+                break;
+            }
+            const SegDev &d = segs[cta[b]];
+            const IsingLat &t = h->lats[d.lat];
+            const uint64_t spr = t.L / 2 / t.G, R = d.y1 - d.y0;
+            if (R < 2 || spr % 32 || 2 * spr > threads || (R - 2) * spr > threads || d.s1 - d.s0 != R * spr)
+                fixed = false;
+        }
+    }
+    P.fixed_slots = fixed && P.smax == 2;
     P.threads = threads;
     P.nblocks = static_cast<unsigned>(blocks.size());
     P.smem = std::max<size_t>(smem_max, 16);
@@ -548,7 +564,7 @@ int materialize_plan(ising_t h, int kind, int layout, const std::vector<std::vec
     PersistArgs dummy;
     memset(&dummy, 0, sizeof(dummy));
     dummy.k_hits = multihit ? 1 : 0;  // selects the kernel whose occupancy is asked
-    dummy.mh_aligned = P.mh_aligned ? 1 : 0;
+    dummy.fixed_slots = P.fixed_slots ? 1 : 0;
     RNGX_CHECK(dispatch_persist(kind, layout, P.smax, dummy, 0, P.threads, P.smem, h->stream, &max_blocks));
     if (static_cast<int>(P.nblocks) > max_blocks) {
         set_error("Ising: plan needs %u co-resident blocks, device holds %d", P.nblocks, max_blocks);
@@ -655,7 +671,7 @@ int enqueue_persistent(ising_t h, std::vector<Plan> &plans, uint64_t n_units, ui
             a.mute_seg = h->mute_seg;
             a.wait_budget_ns = h->wait_budget_ns;
             a.k_hits = k_hits;
-            a.mh_aligned = k_hits && P.mh_aligned ? 1 : 0;
+            a.fixed_slots = P.fixed_slots ? 1 : 0;
             RNGX_CHECK(dispatch_persist(P.kind, P.layout, P.smax, a, P.nblocks, P.threads, P.smem, s, nullptr));
         }
         for (auto &t : h->lats) {

@@ -35,7 +35,7 @@ struct PersistArgs {
     int32_t mute_seg;          // test hook: this segment never publishes (-1: none)
     uint64_t wait_budget_ns;   // limit of one neighbour wait
     uint32_t k_hits;           // 0: exact checkerboard; k > 0: multi-hit rounds of k sweeps per strip phase
-    uint32_t mh_aligned;       // multi-hit plan with one resident stream of each coarse colour per thread
+    uint32_t fixed_slots;      // the plan fixes each slot's role (kernel modes 2 and 3)
 };
 
 struct SegLocal {              // per-segment constants held in shared memory
@@ -471,20 +471,26 @@ __device__ void measure_strips(uint8_t *smem, const SegLocal *S, uint32_t nseg, 
     }
 }
 
-// MODE selects the exact checkerboard (0) or the multi-hit round loop
-// (a.k_hits > 0) at compile time, so that each keeps its own register
-// allocation: MODE 1 handles any slot layout, MODE 2 (SMAX = 2 only) the
-// usual multi-hit plan, where thread slot 0 is a stream of coarse colour 0
-// and slot 1 one of coarse colour 1, so that a phase updates one fixed slot
-// with no per-slot selection (with 1024 threads the general loop would not
-// fit the 64 registers a thread has).  Launch bounds: the exact-checkerboard
-// kernel runs multi-slot shapes with at most 512 threads; the multi-hit
-// kernel also runs two slots with up to 1024 threads.
+// MODE selects the loop at compile time, so that each keeps its own
+// register allocation: 0 the exact checkerboard and 1 the multi-hit rounds
+// (a.k_hits > 0), both for any slot layout; 2 and 3 (SMAX = 2 only) the same
+// for plans that fix each slot's role, so that a pass updates one slot with
+// no per-slot selection (with 1024 threads, or two blocks of 512 per SM, the
+// general loops do not fit the 64 registers a thread has):
+//   2: multi-hit, thread slot 0 a stream of coarse colour 0, slot 1 one of
+//      coarse colour 1 (block = a coarse-0 strip and a coarse-1 strip);
+//   3: exact checkerboard, one strip per block, slot 0 the streams of its
+//      first and last rows (the boundary pass), slot 1 those of the rows
+//      between (the interior pass).
+// Launch bounds: the exact-checkerboard kernel runs multi-slot shapes with
+// at most 512 threads; the multi-hit kernel also runs two slots with up to
+// 1024 threads.
 template <int KIND, int LAYOUT, int SMAX, int MODE>
-__global__ void __launch_bounds__(SMAX >= (MODE ? 4 : 2) ? 512 : 1024, (!MODE && SMAX == 2) ? 2 : 1)
+__global__ void __launch_bounds__(SMAX >= ((MODE == 1 || MODE == 2) ? 4 : 2) ? 512 : 1024,
+                                  ((MODE == 0 || MODE == 3) && SMAX == 2) ? 2 : 1)
     k_ising_persist(PersistArgs a)
 {
-    constexpr bool MH = MODE != 0;
+    constexpr bool MH = MODE == 1 || MODE == 2;
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ SegLocal S[kPersistMaxSegs];
     __shared__ uint64_t prefix_end;
@@ -545,7 +551,25 @@ __global__ void __launch_bounds__(SMAX >= (MODE ? 4 : 2) ? 512 : 1024, (!MODE &&
     if (resident) {
 #pragma unroll
         for (int k = 0; k < SMAX; k++) {
-            setup_slot<LAYOUT>(S, nseg, prefix_end, threadIdx.x + static_cast<uint64_t>(k) * blockDim.x, slot[k]);
+            if constexpr (MODE == 3) {
+                // slot 0: rows 0 and R-1 of the block's strip; slot 1: rows 1 .. R-2
+                const SegLocal &sg = S[0];
+                const uint32_t spr = sg.half / sg.G, t = threadIdx.x;
+                bool in;
+                uint64_t f;
+                if (k == 0) {
+                    in = t < 2 * spr;
+                    f = t < spr ? t : static_cast<uint64_t>(sg.R - 1) * spr + (t - spr);
+                } else {
+                    in = t < (sg.R - 2) * spr;
+                    f = spr + static_cast<uint64_t>(t);
+                }
+                slot[k].seg = 0;
+                slot[k].s = static_cast<uint32_t>(sg.s0 + (in ? f : 0));
+                finish_slot<LAYOUT>(sg, in, in && slot[k].s < sg.n_valid, slot[k]);
+            } else {
+                setup_slot<LAYOUT>(S, nseg, prefix_end, threadIdx.x + static_cast<uint64_t>(k) * blockDim.x, slot[k]);
+            }
             const SegLocal &sg = S[slot[k].seg];
             gen[k].load(sg.rng, slot[k].s < sg.n_inst ? slot[k].s : sg.n_inst - 1);
         }
@@ -554,6 +578,17 @@ __global__ void __launch_bounds__(SMAX >= (MODE ? 4 : 2) ? 512 : 1024, (!MODE &&
 
     uint64_t meas_idx = 0;
     const int lane = threadIdx.x & 31;
+    if constexpr (MODE == 3) {
+        // the host chose this kernel for one strip per block whose boundary
+        // rows fill at most slot 0 and whose interior rows slot 1: check it
+        const uint32_t spr = S[0].half / S[0].G;
+        const bool ok = resident && nseg == 1 && S[0].R >= 2 && spr % 32 == 0 && 2 * spr <= blockDim.x &&
+                        (S[0].R - 2) * spr <= blockDim.x && prefix_end == static_cast<uint64_t>(S[0].R) * spr;
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) atomicCAS(a.err, 0, RNG_EINVAL);
+            goto done;
+        }
+    }
     if constexpr (!MH) {
         // ---------------- exact checkerboard: all strips, every half-sweep
         for (uint64_t t = 0; t < a.n_sweeps; t++) {
@@ -561,9 +596,14 @@ __global__ void __launch_bounds__(SMAX >= (MODE ? 4 : 2) ? 512 : 1024, (!MODE &&
                 const uint32_t h = static_cast<uint32_t>(2 * t + c);
                 const uint64_t pos_off = (2 * t + c) * static_cast<uint64_t>(S[0].G);
                 // warps that hold a strip's first or last row go first ...
-                if (resident) update_resident<KIND, LAYOUT, SMAX>(smem, S, gen, slot, c, lane, SEL_BOUNDARY);
-                else update_pass<KIND, LAYOUT, SMAX>(smem, S, nseg, prefix_end, false, gen, slot, pos_off, c, lane,
-                                                     SEL_BOUNDARY);
+                if constexpr (MODE == 3) {
+                    if (slot[0].flags & SL_WARP_IN) update_slot<KIND, LAYOUT>(smem, S[0], slot[0], gen[0], c, lane);
+                } else if (resident) {
+                    update_resident<KIND, LAYOUT, SMAX>(smem, S, gen, slot, c, lane, SEL_BOUNDARY);
+                } else {
+                    update_pass<KIND, LAYOUT, SMAX>(smem, S, nseg, prefix_end, false, gen, slot, pos_off, c, lane,
+                                                    SEL_BOUNDARY);
+                }
                 __syncthreads();
                 // ... their rows are published (a whole lattice copies them into
                 // its own halo rows) ...
@@ -586,9 +626,15 @@ __global__ void __launch_bounds__(SMAX >= (MODE ? 4 : 2) ? 512 : 1024, (!MODE &&
                     }
                 }
                 // ... the interior rows are updated while those words travel ...
-                if (resident) update_resident<KIND, LAYOUT, SMAX>(smem, S, gen, slot, c, lane, SEL_INTERIOR);
-                else update_pass<KIND, LAYOUT, SMAX>(smem, S, nseg, prefix_end, false, gen, slot, pos_off, c, lane,
-                                                     SEL_INTERIOR);
+                if constexpr (MODE == 3) {
+                    if (slot[SMAX - 1].flags & SL_WARP_IN)
+                        update_slot<KIND, LAYOUT>(smem, S[0], slot[SMAX - 1], gen[SMAX - 1], c, lane);
+                } else if (resident) {
+                    update_resident<KIND, LAYOUT, SMAX>(smem, S, gen, slot, c, lane, SEL_INTERIOR);
+                } else {
+                    update_pass<KIND, LAYOUT, SMAX>(smem, S, nseg, prefix_end, false, gen, slot, pos_off, c, lane,
+                                                    SEL_INTERIOR);
+                }
                 // ... and the neighbours' rows are polled into the halo rows
                 if (any_split) {
                     const uint64_t t0 = global_ns();

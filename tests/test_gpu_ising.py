@@ -175,6 +175,26 @@ def test_launch_shape_does_not_change_results(R):
         R.ising_destroy(h)
 
 
+@pytest.mark.parametrize("L", [1024, 512])
+@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("kind,flags", [(O.XORWOW, 0), (O.XS1024W, 0), (O.PHILOX4X32_7, O.PHILOX_INTRINSIC_KEY)])
+def test_fixed_slot_exact_checkerboard(R, L, layout, kind, flags):
+    # two blocks of 512 per SM: one strip of 2 to 4 rows per block, whose
+    # first and last rows fill every thread's slot 0 and the rows between its
+    # slot 1 (the fixed-slot kernel); the default shape runs the general loop
+    ref, acc, nm = O.ising_run(L, BETA_C, kind, SEED, 30, flags=flags, measure_every=3)
+    for shape in ((512, 2, 0), (0, 0, 0)):
+        h = R.ising_create(L, BETA_C, layout, kind, flags, SEED, 2)
+        try:
+            R.ising_set_launch(h, *shape)
+            R.ising_sweep(h, 30, 3)
+            obs = R.ising_observables(h)
+            assert np.array_equal(R.ising_get_spins(h), ref), shape
+            assert obs["acc"] == acc.tolist() and obs["n_meas"] == nm, shape
+        finally:
+            R.ising_destroy(h)
+
+
 @pytest.mark.parametrize("layout", [0, 1])
 def test_streamed_generator_state(R, layout):
     # 256 threads x 4 slots per block cannot hold a 1024^2 strip's streams:
