@@ -331,11 +331,13 @@ __device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p)
 // strip, the others, or all warps of the strips of one coarse colour
 // (multi-hit phases).  A warp is classified as a whole, so warp-wide steps
 // see all 32 lanes.
-enum { SEL_BOUNDARY = 0, SEL_INTERIOR = 1, SEL_COARSE0 = 2, SEL_COARSE1 = 3 };
+// SEL_ALL: every warp (blocks that hold whole lattices only).
+enum { SEL_BOUNDARY = 0, SEL_INTERIOR = 1, SEL_COARSE0 = 2, SEL_COARSE1 = 3, SEL_ALL = 4 };
 
 __device__ __forceinline__ bool warp_selected(const StreamSlot &sl, int sel)
 {
     if (!(sl.flags & SL_WARP_IN)) return false;
+    if (sel == SEL_ALL) return true;
     if (sel >= SEL_COARSE0) return ((sl.flags & SL_COARSE) != 0) == (sel == SEL_COARSE1);
     return ((sl.flags & SL_WARP_BND) != 0) == (sel == SEL_BOUNDARY);
 }
@@ -360,7 +362,8 @@ __device__ __forceinline__ void update_pass(uint8_t *smem, const SegLocal *S, ui
     // strips' stream counts are multiples of 32, so warps never straddle two)
     for (uint32_t j = 0; j < nseg; j++) {
         const SegLocal &sg = S[j];
-        if (sel >= SEL_COARSE0 && sg.coarse != static_cast<uint32_t>(sel - SEL_COARSE0)) continue;
+        if ((sel == SEL_COARSE0 || sel == SEL_COARSE1) && sg.coarse != static_cast<uint32_t>(sel - SEL_COARSE0))
+            continue;
         const uint64_t count = (j + 1 < nseg ? S[j + 1].prefix : prefix_end) - sg.prefix;
         for (uint64_t base = 0; base < count; base += blockDim.x) {
             const uint64_t f = base + threadIdx.x;
@@ -591,7 +594,39 @@ __global__ void __launch_bounds__(SMAX >= ((MODE == 1 || MODE == 2) ? 4 : 2) ? 5
     }
     if constexpr (!MH) {
         // ---------------- exact checkerboard: all strips, every half-sweep
-        for (uint64_t t = 0; t < a.n_sweeps; t++) {
+        // A block of whole lattices exchanges nothing with other blocks: a
+        // half-sweep is one pass over all its warps, then the halo rows are
+        // copied from the edge rows (no boundary-first pass).
+        bool all_whole = MODE == 0;
+        for (uint32_t j = 0; j < nseg; j++) all_whole = all_whole && S[j].up < 0;
+        for (uint64_t t = 0; t < a.n_sweeps && all_whole; t++) {
+            for (int c = 0; c < 2; c++) {
+                if (resident) {
+                    update_resident<KIND, LAYOUT, SMAX>(smem, S, gen, slot, c, lane, SEL_ALL);
+                } else {
+                    update_pass<KIND, LAYOUT, SMAX>(smem, S, nseg, prefix_end, false, gen, slot,
+                                                    (2 * t + c) * static_cast<uint64_t>(S[0].G), c, lane, SEL_ALL);
+                }
+                __syncthreads();
+                for (uint32_t j = 0; j < nseg; j++) {
+                    const SegLocal &sg = S[j];
+                    const uint32_t rb = row_bytes<LAYOUT>(sg);
+                    uint8_t *top = plane_row<LAYOUT>(smem, sg, c, -1), *bot = plane_row<LAYOUT>(smem, sg, c, sg.R);
+                    const uint8_t *last = plane_row<LAYOUT>(smem, sg, c, sg.R - 1);
+                    const uint8_t *first = plane_row<LAYOUT>(smem, sg, c, 0);
+                    for (uint32_t i = threadIdx.x; i < rb; i += blockDim.x) {
+                        top[i] = last[i];
+                        bot[i] = first[i];
+                    }
+                }
+                __syncthreads();
+            }
+            if (a.measure_every && (a.sweep0 + t + 1) % a.measure_every == 0) {
+                measure_strips<LAYOUT>(smem, S, nseg, a, meas_idx, red);
+                meas_idx++;
+            }
+        }
+        for (uint64_t t = 0; t < a.n_sweeps && !all_whole; t++) {
             for (int c = 0; c < 2; c++) {
                 const uint32_t h = static_cast<uint32_t>(2 * t + c);
                 const uint64_t pos_off = (2 * t + c) * static_cast<uint64_t>(S[0].G);
