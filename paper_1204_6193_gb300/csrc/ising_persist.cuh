@@ -288,17 +288,42 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
         const uint32_t *ou = o - W, *od = o + W;
         const uint32_t lq0 = lane * G;
         uint32_t c_lo = 0, c_hi = 0;
-        for (uint32_t g = 0; g < G; g++) {
-            const uint32_t rr = gen.next();
-            if (!sl.val()) continue;
-            const uint32_t xh = sl.xh0 + g;
-            const int nn = bit_spin(o, col_left(xh, p, half)) + bit_spin(o, col_right(xh, p, half)) +
-                           bit_spin(ou, xh) + bit_spin(od, xh);
-            const int sp = bit_spin(own, xh);
-            if (accept_a(sp * nn, rr, T4, T8)) {
-                const uint32_t lq = lq0 + g;
-                if ((lq >> 5) == (lq0 >> 5)) c_lo |= 1u << (lq & 31);
-                else c_hi |= 1u << (lq & 31);
+        if (G == 2) {
+            // both sites in one word: the anti-aligned neighbours of all 32
+            // sites of the word are counted at once, bit-sliced, from the
+            // word, its row neighbours (shifted by one site) and the words
+            // above and below
+            const uint32_t r0 = gen.next(), r1 = gen.next();
+            if (sl.val()) {
+                const uint32_t wi = sl.xh0 >> 5, b0 = sl.xh0 & 31u;
+                const uint32_t ow = own[wi], mw = o[wi];
+                const uint32_t n2 = p ? (mw >> 1) | (o[wi + 1 == W ? 0 : wi + 1] << 31)
+                                      : (mw << 1) | (o[wi == 0 ? W - 1 : wi - 1] >> 31);
+                const uint32_t a1 = ow ^ mw, a2 = ow ^ n2, a3 = ow ^ ou[wi], a4 = ow ^ od[wi];
+                const uint32_t s1 = a1 ^ a2, c1 = a1 & a2, s2 = a3 ^ a4, c2 = a3 & a4;
+                const uint32_t k0 = s1 ^ s2, t = s1 & s2;
+                const uint32_t k1 = c1 ^ c2 ^ t, k2 = (c1 & c2) | ((c1 ^ c2) & t);
+                // site bit b: k anti-aligned neighbours, s_i sum s_j = 4 - 2k
+                auto flips = [&](uint32_t b, uint32_t r) -> uint32_t {
+                    const int k = static_cast<int>(((k0 >> b) & 1u) | (((k1 >> b) & 1u) << 1) | (((k2 >> b) & 1u) << 2));
+                    const int a = 4 - 2 * k;
+                    return (a <= sg.a_max || r < (a == 2 ? sg.t4 : sg.t8)) ? 1u : 0u;
+                };
+                c_lo = (flips(b0, r0) << b0) | (flips(b0 + 1, r1) << (b0 + 1));
+            }
+        } else {
+            for (uint32_t g = 0; g < G; g++) {
+                const uint32_t rr = gen.next();
+                if (!sl.val()) continue;
+                const uint32_t xh = sl.xh0 + g;
+                const int nn = bit_spin(o, col_left(xh, p, half)) + bit_spin(o, col_right(xh, p, half)) +
+                               bit_spin(ou, xh) + bit_spin(od, xh);
+                const int sp = bit_spin(own, xh);
+                if (accept_a(sp * nn, rr, T4, T8)) {
+                    const uint32_t lq = lq0 + g;
+                    if ((lq >> 5) == (lq0 >> 5)) c_lo |= 1u << (lq & 31);
+                    else c_hi |= 1u << (lq & 31);
+                }
             }
         }
         // the warp's 32 G sites are G consecutive words of plane c
