@@ -211,7 +211,7 @@ struct IsingLat {
 // Persistent launch plan of one group of lattices of one generator kind.
 struct Plan {
     int kind = 0, layout = 0, smax = 1;
-    bool fixed_slots = false;  // each thread slot has a fixed role (see the kernel's modes 2 and 3)
+    int fixed_slots = 0;  // 1: each thread slot has a fixed role (kernel modes 2, 3); 2: whole lattices (mode 4)
     unsigned nblocks = 0, threads = 0;
     size_t smem = 0;
     uint32_t nsegs = 0, halo_row_bytes = 0;
@@ -553,7 +553,14 @@ int materialize_plan(ising_t h, int kind, int layout, const std::vector<std::vec
                 fixed = false;
         }
     }
-    P.fixed_slots = fixed && P.smax == 2;
+    P.fixed_slots = fixed && P.smax == 2 ? 1 : 0;
+    if (!multihit && P.smax == 1 && max_streams <= threads) {
+        // every block one whole lattice whose streams fit one slot per thread
+        bool whole = true;
+        for (size_t b = 0; b < blocks.size() && whole; b++)
+            if (blocks[b].size() != 1 || segs[cta[b]].up >= 0) whole = false;
+        if (whole) P.fixed_slots = 2;
+    }
     P.threads = threads;
     P.nblocks = static_cast<unsigned>(blocks.size());
     P.smem = std::max<size_t>(smem_max, 16);
@@ -569,7 +576,7 @@ int materialize_plan(ising_t h, int kind, int layout, const std::vector<std::vec
     PersistArgs dummy;
     memset(&dummy, 0, sizeof(dummy));
     dummy.k_hits = multihit ? 1 : 0;  // selects the kernel whose occupancy is asked
-    dummy.fixed_slots = P.fixed_slots ? 1 : 0;
+    dummy.fixed_slots = static_cast<uint32_t>(P.fixed_slots);
     RNGX_CHECK(dispatch_persist(kind, layout, P.smax, dummy, 0, P.threads, P.smem, h->stream, &max_blocks));
     if (static_cast<int>(P.nblocks) > max_blocks) {
         set_error("Ising: plan needs %u co-resident blocks, device holds %d", P.nblocks, max_blocks);
@@ -676,7 +683,7 @@ int enqueue_persistent(ising_t h, std::vector<Plan> &plans, uint64_t n_units, ui
             a.mute_seg = h->mute_seg;
             a.wait_budget_ns = h->wait_budget_ns;
             a.k_hits = k_hits;
-            a.fixed_slots = P.fixed_slots ? 1 : 0;
+            a.fixed_slots = static_cast<uint32_t>(P.fixed_slots);
             RNGX_CHECK(dispatch_persist(P.kind, P.layout, P.smax, a, P.nblocks, P.threads, P.smem, s, nullptr));
         }
         for (auto &t : h->lats) {

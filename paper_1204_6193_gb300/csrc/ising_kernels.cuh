@@ -86,12 +86,14 @@ template <int KIND, int LAYOUT, int SMAX>
 int launch_persist_t(const PersistArgs &a, unsigned nblocks, unsigned threads, size_t smem, cudaStream_t s,
                      int *max_blocks)
 {
-    // kernel modes: 0 exact, 1 multi-hit, 2 / 3 the same with fixed slot roles (SMAX = 2)
-    const bool fixed = SMAX == 2 && a.fixed_slots;
+    // kernel modes: 0 exact, 1 multi-hit, 2 / 3 the same with fixed slot roles
+    // (SMAX = 2), 4 exact with one whole resident lattice per block (SMAX = 1)
+    const bool fixed = SMAX == 2 && a.fixed_slots == 1, whole = SMAX == 1 && a.fixed_slots == 2;
     auto kern = a.k_hits ? (fixed ? k_ising_persist<KIND, LAYOUT, SMAX, SMAX == 2 ? 2 : 1>
                                   : k_ising_persist<KIND, LAYOUT, SMAX, 1>)
                          : (fixed ? k_ising_persist<KIND, LAYOUT, SMAX, SMAX == 2 ? 3 : 0>
-                                  : k_ising_persist<KIND, LAYOUT, SMAX, 0>);
+                                  : (whole ? k_ising_persist<KIND, LAYOUT, SMAX, SMAX == 1 ? 4 : 0>
+                                           : k_ising_persist<KIND, LAYOUT, SMAX, 0>));
     RNGX_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     int per_sm = 0, dev = 0, sms = 0;
     RNGX_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));

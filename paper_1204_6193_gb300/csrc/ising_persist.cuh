@@ -35,7 +35,7 @@ struct PersistArgs {
     int32_t mute_seg;          // test hook: this segment never publishes (-1: none)
     uint64_t wait_budget_ns;   // limit of one neighbour wait
     uint32_t k_hits;           // 0: exact checkerboard; k > 0: multi-hit rounds of k sweeps per strip phase
-    uint32_t fixed_slots;      // the plan fixes each slot's role (kernel modes 2 and 3)
+    uint32_t fixed_slots;      // 1: the plan fixes each slot's role (kernel modes 2, 3); 2: one whole lattice per block (mode 4)
 };
 
 struct SegLocal {              // per-segment constants held in shared memory
@@ -201,6 +201,8 @@ enum : uint32_t {
     SL_ODD_ROW = 32u,   // the sites' row is odd
     SL_ROW_FIRST = 64u, // the slot's sites start its row (left neighbour wraps)
     SL_ROW_LAST = 128u, // the slot's sites end its row (right neighbour wraps)
+    SL_DUP_DOWN = 256u, // whole lattice, first row: its flips also go to the halo row below the last
+    SL_DUP_UP = 512u,   // whole lattice, last row: its flips also go to the halo row above the first
 };
 
 template <int LAYOUT>
@@ -214,7 +216,8 @@ __device__ __forceinline__ void finish_slot(const SegLocal &sg, bool in, bool va
     const bool wb = __any_sync(0xffffffffu, in && (row == sg.y0 || row + 1 == sg.y0 + sg.R));
     o.flags = (in ? SL_IN : 0u) | (val ? SL_VAL : 0u) | (wi ? SL_WARP_IN : 0u) | (wb ? SL_WARP_BND : 0u) |
               (sg.coarse ? SL_COARSE : 0u) | ((row & 1u) ? SL_ODD_ROW : 0u) | (o.xh0 == 0 ? SL_ROW_FIRST : 0u) |
-              (o.xh0 + sg.G == sg.half ? SL_ROW_LAST : 0u);
+              (o.xh0 + sg.G == sg.half ? SL_ROW_LAST : 0u) | (sg.up < 0 && row == sg.y0 ? SL_DUP_DOWN : 0u) |
+              (sg.up < 0 && row + 1 == sg.y0 + sg.R ? SL_DUP_UP : 0u);
 }
 
 template <int LAYOUT>
@@ -238,7 +241,9 @@ __device__ __forceinline__ bool accept_a(int a, uint32_t r, uint64_t T4, uint64_
 
 // Draws G numbers from the slot's generator and updates its G colour-c
 // sites in shared memory (all 32 lanes of the warp call this together).
-template <int KIND, int LAYOUT>
+// DUP: a whole lattice's edge rows also write their flips into the halo
+// rows (the other edge's copy), so that no copy pass is needed.
+template <int KIND, int LAYOUT, bool DUP = false>
 __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, const StreamSlot &sl, Gen<KIND> &gen,
                                             int c, int lane)
 {
@@ -269,8 +274,16 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
             // a <= 0 always flips (and every a where T = 2^32, beta = 0)
             const int am = sg.a_max;
             const uint32_t t4 = sg.t4, t8 = sg.t8;
-            if (a0 <= am || r0 < (a0 == 2 ? t4 : t8)) ow[0] = static_cast<int8_t>(-s0);
-            if (a1 <= am || r1 < (a1 == 2 ? t4 : t8)) ow[1] = static_cast<int8_t>(-s1);
+            const bool f0 = a0 <= am || r0 < (a0 == 2 ? t4 : t8), f1 = a1 <= am || r1 < (a1 == 2 ? t4 : t8);
+            if (f0) ow[0] = static_cast<int8_t>(-s0);
+            if (f1) ow[1] = static_cast<int8_t>(-s1);
+            if constexpr (DUP) {
+                if (sl.flags & (SL_DUP_DOWN | SL_DUP_UP)) {
+                    const int d = static_cast<int>(sg.R * half) * ((sl.flags & SL_DUP_DOWN) ? 1 : -1);
+                    if (f0) ow[d] = static_cast<int8_t>(-s0);
+                    if (f1) ow[d + 1] = static_cast<int8_t>(-s1);
+                }
+            }
             return;
         }
         for (uint32_t g = 0; g < G; g++) {
@@ -279,7 +292,14 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
             const uint32_t xh = sl.xh0 + g;
             const int nn = o[col_left(xh, p, half)] + o[col_right(xh, p, half)] + ou[xh] + od[xh];
             const int sp = own[xh];
-            if (accept_a(sp * nn, rr, T4, T8)) own[xh] = static_cast<int8_t>(-sp);
+            if (accept_a(sp * nn, rr, T4, T8)) {
+                own[xh] = static_cast<int8_t>(-sp);
+                if constexpr (DUP) {
+                    if (sl.flags & (SL_DUP_DOWN | SL_DUP_UP))
+                        own[xh + static_cast<int>(sg.R * half) * ((sl.flags & SL_DUP_DOWN) ? 1 : -1)] =
+                            static_cast<int8_t>(-sp);
+                }
+            }
         }
     } else {
         const uint32_t W = sg.W;
@@ -335,7 +355,13 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
         for (uint32_t m = 0; m < G; m++) {
             const uint32_t mine = ((lq0 >> 5) == m ? c_lo : 0u) | ((lq0 >> 5) + 1 == m ? c_hi : 0u);
             const uint32_t word = __reduce_or_sync(0xffffffffu, mine);
-            if (lane == 0 && word && wbase + m < own_words) plane_c[wbase + m] ^= word;
+            if (lane == 0 && word && wbase + m < own_words) {
+                plane_c[wbase + m] ^= word;
+                if constexpr (DUP) {  // the halo copies of the whole lattice's edge rows
+                    if (wbase + m < W) plane_c[wbase + m + own_words] ^= word;
+                    if (wbase + m >= own_words - W) plane_c[wbase + m - own_words] ^= word;
+                }
+            }
         }
     }
 }
@@ -509,16 +535,20 @@ __device__ void measure_strips(uint8_t *smem, const SegLocal *S, uint32_t nseg, 
 //      coarse colour 1 (block = a coarse-0 strip and a coarse-1 strip);
 //   3: exact checkerboard, one strip per block, slot 0 the streams of its
 //      first and last rows (the boundary pass), slot 1 those of the rows
-//      between (the interior pass).
+//      between (the interior pass);
+//   4: (SMAX = 1 only) exact checkerboard, every block one whole lattice
+//      with resident states: a half-sweep is one pass and one barrier, the
+//      edge rows writing their flips into the halo rows as well.
 // Launch bounds: the exact-checkerboard kernel runs multi-slot shapes with
 // at most 512 threads; the multi-hit kernel also runs two slots with up to
 // 1024 threads.
 template <int KIND, int LAYOUT, int SMAX, int MODE>
 __global__ void __launch_bounds__(SMAX >= ((MODE == 1 || MODE == 2) ? 4 : 2) ? 512 : 1024,
-                                  ((MODE == 0 || MODE == 3) && SMAX == 2) ? 2 : 1)
+                                  ((MODE == 0 || MODE == 3 || MODE == 4) && SMAX == 2) ? 2 : 1)
     k_ising_persist(PersistArgs a)
 {
     constexpr bool MH = MODE == 1 || MODE == 2;
+    constexpr bool EXACT_LOOPS = MODE == 0 || MODE == 3;
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ SegLocal S[kPersistMaxSegs];
     __shared__ uint64_t prefix_end;
@@ -606,6 +636,24 @@ __global__ void __launch_bounds__(SMAX >= ((MODE == 1 || MODE == 2) ? 4 : 2) ? 5
 
     uint64_t meas_idx = 0;
     const int lane = threadIdx.x & 31;
+    if constexpr (MODE == 4) {
+        // the host chose this kernel for blocks of one whole resident lattice
+        const bool ok = resident && nseg == 1 && S[0].up < 0;
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) atomicCAS(a.err, 0, RNG_EINVAL);
+            goto done;
+        }
+        for (uint64_t t = 0; t < a.n_sweeps; t++) {
+            for (int c = 0; c < 2; c++) {
+                if (slot[0].flags & SL_WARP_IN) update_slot<KIND, LAYOUT, true>(smem, S[0], slot[0], gen[0], c, lane);
+                __syncthreads();
+            }
+            if (a.measure_every && (a.sweep0 + t + 1) % a.measure_every == 0) {
+                measure_strips<LAYOUT>(smem, S, nseg, a, meas_idx, red);
+                meas_idx++;
+            }
+        }
+    }
     if constexpr (MODE == 3) {
         // the host chose this kernel for one strip per block whose boundary
         // rows fill at most slot 0 and whose interior rows slot 1: check it
@@ -617,7 +665,7 @@ __global__ void __launch_bounds__(SMAX >= ((MODE == 1 || MODE == 2) ? 4 : 2) ? 5
             goto done;
         }
     }
-    if constexpr (!MH) {
+    if constexpr (EXACT_LOOPS) {
         // ---------------- exact checkerboard: all strips, every half-sweep
         // A block of whole lattices exchanges nothing with other blocks: a
         // half-sweep is one pass over all its warps, then the halo rows are
@@ -712,7 +760,7 @@ __global__ void __launch_bounds__(SMAX >= ((MODE == 1 || MODE == 2) ? 4 : 2) ? 5
                 meas_idx++;
             }
         }
-    } else {
+    } else if constexpr (MH) {
         // ---------------- multi-hit rounds (double checkerboard): the strips
         // of coarse colour C take k sweeps of their own rows while the other
         // strips stay fixed; then they publish both colours of their first

@@ -175,6 +175,25 @@ def test_launch_shape_does_not_change_results(R):
         R.ising_destroy(h)
 
 
+@pytest.mark.parametrize("L,layout", [(64, 0), (64, 1), (32, 0), (128, 1)])
+@pytest.mark.parametrize("kind", [O.XORWOW, O.XS1024W, O.LCG64])
+def test_whole_lattice_in_one_block(R, L, layout, kind):
+    # one block holds the whole lattice, one stream per thread: a half-sweep
+    # is one pass and one barrier, the edge rows also writing their halo
+    # copies; the default shape splits the lattice into strips instead
+    ref, acc, nm = O.ising_run(L, 0.43, kind, SEED, 40, measure_every=4)
+    for shape in ((1024, 1, 1 << 16), (0, 0, 0)):
+        h = R.ising_create(L, 0.43, layout, kind, 0, SEED, 2)
+        try:
+            R.ising_set_launch(h, *shape)
+            R.ising_sweep(h, 40, 4)
+            obs = R.ising_observables(h)
+            assert np.array_equal(R.ising_get_spins(h), ref), shape
+            assert obs["acc"] == acc.tolist() and obs["n_meas"] == nm, shape
+        finally:
+            R.ising_destroy(h)
+
+
 @pytest.mark.parametrize("L", [1024, 512])
 @pytest.mark.parametrize("layout", [0, 1])
 @pytest.mark.parametrize("kind,flags", [(O.XORWOW, 0), (O.XS1024W, 0), (O.PHILOX4X32_7, O.PHILOX_INTRINSIC_KEY)])
