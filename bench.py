@@ -282,16 +282,29 @@ def run_gpu(args):
     total_outputs = outputs_per_step_rank * world * args.steps
     value = total_outputs / (elapsed_ms * 1e-3) / 1e9
 
+    # instruction-issue roof: one warp instruction per scheduler and cycle,
+    # 4 schedulers per SM, at the highest SM clock sampled during the timed
+    # region (the measured FFMA rate of rng_issue_peaks when no clock was read)
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    if clk and clk.get("sm_max_mhz"):
+        issue_peak = n_sms * 4 * 32 * clk["sm_max_mhz"] * 1e6 / 1e12
+        issue_src = f"{n_sms} SMs x 4 schedulers x 32 threads x {clk['sm_max_mhz']:.0f} MHz (one warp instruction " \
+                    "per scheduler and cycle)"
+    elif issue_peaks:
+        issue_peak = issue_peaks["ffma"] / 1e12
+        issue_src = "measured FFMA rate (rng_issue_peaks)"
+    else:
+        issue_peak, issue_src = None, None
+
     def issue_of(name, c, avg_ms):
         ipo = ncu_inst_per_output(name)
-        if ipo is None or not issue_peaks:
+        if ipo is None or issue_peak is None:
             return None
         ach = ipo * c[4] * c[5] / (avg_ms * 1e-3) / 1e12
-        peak = issue_peaks["ffma"] / 1e12
-        return {"inst_per_output": round(ipo, 2), "achieved_tinst_s": round(ach, 2), "peak_tinst_s": round(peak, 2),
-                "frac": round(ach / peak, 3),
-                "source": "thread instructions per output from profiles/gen_bulk_traffic.json (ncu); issue peak "
-                          "= measured FFMA rate (rng_issue_peaks), one warp-instruction per scheduler and cycle"}
+        return {"inst_per_output": round(ipo, 2), "achieved_tinst_s": round(ach, 2),
+                "peak_tinst_s": round(issue_peak, 2), "frac": round(ach / issue_peak, 3), "peak_source": issue_src,
+                "source": "thread instructions per output from profiles/gen_bulk_traffic.json (ncu) x outputs / "
+                          "CUDA-event time"}
 
     detail = {}
     best = None
@@ -308,23 +321,32 @@ def run_gpu(args):
         if best is None or tot > best[1]:
             best = (name, tot, avg, c)
     name, tot, avg, c = best
-    is_write = not name.endswith("u32_xor")
     ach = bulk.algorithmic_bytes(c) / (avg * 1e-3) / 1e9
     step_ms_total = sum(sum(d["ms"]) for d in per.values())
-    roofline = {
-        "kernel": name,
-        "bound": "hbm" if is_write else "alu",
+    hbm = {
         "achieved": round(ach, 1),
         "peak": peaks["hbm_gbs"],
         "unit": "GB/s",
         "frac": round(ach / peaks["hbm_gbs"], 4),
         "peak_source": f"{peaks['source']} (MEASURED_PEAKS.json hbm_gbs)" if peaks["source"] == "measured"
         else "fallback 6.8 TB/s",
+    }
+    iss = issue_of(name, c, avg)
+    # the roof that binds: instruction issue when the kernel is closer to it
+    # than to HBM bandwidth (the normal-deviate kernels), else HBM
+    roofline = {"kernel": name}
+    if iss is not None and iss["frac"] > hbm["frac"]:
+        roofline.update({"bound": "alu", "achieved": iss["achieved_tinst_s"], "peak": iss["peak_tinst_s"],
+                         "unit": "T thread-instructions/s", "frac": iss["frac"], "peak_source": iss["peak_source"]})
+    else:
+        roofline.update({"bound": "hbm", **hbm})
+    roofline.update({
         "share_of_step": round(tot / step_ms_total, 3),
         "algorithmic_bytes_per_launch": bulk.algorithmic_bytes(c),
         "traffic": ncu_traffic(name),
-        "issue": issue_of(name, c, avg),
-    }
+        "hbm": hbm,
+        "issue": iss,
+    })
 
     # end to end through the C ABI with host buffers: each step reseeds from a
     # host seed and every output ends in pinned host memory, either written

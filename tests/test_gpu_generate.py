@@ -472,6 +472,37 @@ def test_full_size_normals_sampled(R, torch_cuda, kind):
         R.rng_destroy(h)
 
 
+def test_xs1024w_thread_form_normals_ragged_whole(R, torch_cuda):
+    """Every normal of the 1024-bit generator in its one-thread-per-state
+    forms (step-major: two warps per 32 states), with the fewest states that
+    select them plus a ragged 5 (the last block has 5 of 32 states), then u32
+    draws that continue the streams."""
+    torch = torch_cuda
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nstates = 200 * sms + 37
+    n, K = 32 * nstates, 6
+    assert nstates % 32 == 5
+    h = R.rng_create(O.XS1024W, n, 0)
+    try:
+        R.rng_seed(h, SEED)
+        buf = torch.empty(n * K, dtype=torch.float32, device="cuda")
+        R.rng_generate_normal(h, buf.data_ptr(), K, R.RNG_STEP_MAJOR)
+        red = torch.empty(n, dtype=torch.float32, device="cuda")
+        R.rng_generate_normal(h, red.data_ptr(), 2, R.RNG_XOR_REDUCE)
+        tail = torch.empty(n * 3, dtype=torch.int32, device="cuda")
+        R.rng_generate_u32(h, tail.data_ptr(), 3, R.RNG_STEP_MAJOR)
+        torch.cuda.synchronize()
+        o = O.generate(O.XS1024W, SEED, n, K + 5)
+        got = buf.view(K, n).T.cpu().numpy().astype(np.float64)
+        assert np.abs(got - O.box_muller(o[:, :K])).max() <= NORMAL_TOL
+        z = O.box_muller(o[:, K:K + 2])
+        err = np.abs(red.cpu().numpy().astype(np.float64) - z.sum(1))
+        assert (err <= 2 * NORMAL_TOL + 1e-5 * np.abs(z).sum(1)).all()
+        assert np.array_equal(tail.view(3, n).T.cpu().numpy().view(np.uint32), o[:, K + 2:])
+    finally:
+        R.rng_destroy(h)
+
+
 def test_mwc_full_table_matches_oracle(R, torch_cuda):
     n = 1 << 20
     assert np.array_equal(R.rng_mwc_multipliers(0, n), O.mwc_multipliers(n))
