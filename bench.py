@@ -148,6 +148,17 @@ def _ncu_summary():
     return d if d.get("source_hash") == file_hash(GEN_SOURCES) else None
 
 
+def binding_roof(hbm: dict, issue: dict | None) -> dict:
+    """The roof that binds a kernel: instruction issue (bound "alu") when its
+    fraction of the issue roof is higher than its fraction of HBM bandwidth,
+    as for the normal-deviate kernels; else HBM.  Without instruction counts
+    (sources changed since the ncu capture) only HBM can be stated."""
+    if issue is not None and issue["frac"] > hbm["frac"]:
+        return {"bound": "alu", "achieved": issue["achieved_tinst_s"], "peak": issue["peak_tinst_s"],
+                "unit": "T thread-instructions/s", "frac": issue["frac"], "peak_source": issue["peak_source"]}
+    return {"bound": "hbm", **hbm}
+
+
 def ncu_traffic(kernel_key: str):
     """DRAM bytes per launch (ncu), scaled to the bench's launch."""
     d = _ncu_summary()
@@ -332,14 +343,7 @@ def run_gpu(args):
         else "fallback 6.8 TB/s",
     }
     iss = issue_of(name, c, avg)
-    # the roof that binds: instruction issue when the kernel is closer to it
-    # than to HBM bandwidth (the normal-deviate kernels), else HBM
-    roofline = {"kernel": name}
-    if iss is not None and iss["frac"] > hbm["frac"]:
-        roofline.update({"bound": "alu", "achieved": iss["achieved_tinst_s"], "peak": iss["peak_tinst_s"],
-                         "unit": "T thread-instructions/s", "frac": iss["frac"], "peak_source": iss["peak_source"]})
-    else:
-        roofline.update({"bound": "hbm", **hbm})
+    roofline = {"kernel": name, **binding_roof(hbm, iss)}
     roofline.update({
         "share_of_step": round(tot / step_ms_total, 3),
         "algorithmic_bytes_per_launch": bulk.algorithmic_bytes(c),
