@@ -643,7 +643,8 @@ def batch_section(R, torch, args):
             "one_launch_per_lattice": {"sweeps": nb, "ms": round(ms_alone, 2), "flips_per_ns": round(fl_alone, 3)},
             "speedup": round(fl / fl_alone, 2), "launch": tuned, "plan": plan,
             "workload": "L log-uniform over {16..512}, beta U[0.30,0.60], xorwow/xs1024w alternating, G=2, "
-                        "one persistent launch per kind group, replayed from a CUDA graph"}
+                        "per generator kind, waves of lattices whose streams fit the registers (one persistent launch each per " \
+                        "4096 sweeps), all replayed from one CUDA graph"}
 
 
 def O_seed_word(seed, k):

@@ -285,8 +285,11 @@ int ising_get_launch(ising_t h, uint32_t *threads, int *ctas_per_sm, uint32_t *m
  * optional outputs). */
 int ising_autotune(ising_t h, uint32_t probe_sweeps, uint32_t *threads, int *ctas_per_sm);
 
-/* The current persistent launch plan: kind groups (one launch each), thread
- * blocks, row strips and threads per block.  Plans on first use. */
+/* The current persistent launch plan: launches per chunk of sweeps (one per
+ * wave of each kind group: lattices of one generator kind whose streams fit
+ * the registers of the device together, at most 2048 per SM), thread blocks
+ * and row strips summed over them, and the largest threads per block.
+ * Plans on first use. */
 int ising_plan_info(ising_t h, uint32_t *groups, uint32_t *blocks, uint32_t *strips, uint32_t *threads);
 
 /* Failure-detection hook for tests: row strip `strip` (-1: none) of the
@@ -317,12 +320,14 @@ int ising_info(ising_t h, uint32_t idx, uint32_t *n_lattices, uint32_t *L, int *
  * generator kinds rng_kind[b] (RNG_XORWOW or RNG_XS1024W or any per-thread
  * kind), lattice b seeded with w_b of the master seed; int8 layout.
  * Batching is not in the paper: it packs many application-test lattices
- * into one persistent launch over a work list of (lattice, tile) items. */
+ * into persistent launches over work lists of (lattice, row strip) items. */
 int ising_batch_create(ising_t *out, uint32_t n, const uint32_t *L, const double *beta,
                        const int *rng_kind, uint64_t seed, uint32_t G, void *cuda_stream);
 
-/* All lattices advance n_sweeps sweeps in one persistent launch (captured in
- * a CUDA graph and replayed when the same n_sweeps is requested again).
+/* All lattices advance n_sweeps sweeps, as one CUDA graph (captured once and
+ * replayed when the same n_sweeps is requested again).  Lattices of one
+ * generator kind run in waves whose streams fit the device's registers
+ * together; per chunk of 4096 sweeps each wave is one persistent launch.
  * Each lattice's result equals ising_sweep on that lattice alone. */
 int ising_batch_sweep(ising_t h, uint64_t n_sweeps, uint32_t measure_every, void *cuda_stream);
 

@@ -22,6 +22,7 @@ namespace {
 constexpr uint64_t kChunkSweeps = 4096;  // sweeps per persistent launch
 constexpr uint32_t kMaxHits = 65536;      // multi-hit sweeps per strip phase
 constexpr size_t kSmemCap = 200 * 1024;  // dynamic shared memory per block we plan for
+constexpr uint64_t kWaveStreamsPerSm = 2048;  // streams per SM that one persistent launch keeps in registers
 
 int dispatch_half(int kind, const LatDev &lat, int c, cudaStream_t s)
 {
@@ -388,6 +389,7 @@ struct SegPlan {
 
 int materialize_plan(ising_t h, int kind, int layout, const std::vector<std::vector<SegPlan>> &blocks, Plan &P,
                      bool multihit);
+int plan_blocks(ising_t h, const std::vector<uint32_t> &ids, double target, std::vector<std::vector<SegPlan>> &blocks);
 
 // Plans one kind group: splits big lattices into aligned row strips, packs
 // small whole lattices into shared blocks, and picks the block shape.
@@ -403,9 +405,25 @@ int build_plan(ising_t h, int kind, int layout, const std::vector<uint32_t> &ids
     // about one block per SM (or per_sm), but no fewer than 1024 sites per
     // block: smaller strips spend their time waiting on their neighbours
     const double min_sites = h->cfg_min_sites ? static_cast<double>(h->cfg_min_sites) : 1024.0;
-    const double target = std::max(min_sites, static_cast<double>(total_sites) / target_blocks);
-
+    double target = std::max(min_sites, static_cast<double>(total_sites) / target_blocks);
     std::vector<std::vector<SegPlan>> blocks;
+    // each lattice's strip count is rounded on its own, so the blocks can
+    // outnumber target_blocks; a larger target per block then brings them
+    // back within what the device holds at once
+    for (int attempt = 0; attempt < 16; attempt++) {
+        int st = plan_blocks(h, ids, target, blocks);
+        if (st != RNG_OK) return st;
+        if (blocks.size() <= target_blocks) break;
+        target *= 1.02 * static_cast<double>(blocks.size()) / static_cast<double>(target_blocks);
+    }
+    return materialize_plan(h, kind, layout, blocks, P, false);
+}
+
+// Strips and packed whole lattices of about `target` sites each, one list
+// per thread block.
+int plan_blocks(ising_t h, const std::vector<uint32_t> &ids, double target, std::vector<std::vector<SegPlan>> &blocks)
+{
+    blocks.clear();
     std::vector<std::pair<uint64_t, uint32_t>> whole;  // (sites, lattice) packed later
     for (uint32_t id : ids) {
         const IsingLat &t = h->lats[id];
@@ -453,7 +471,7 @@ int build_plan(ising_t h, int kind, int layout, const std::vector<uint32_t> &ids
         }
     }
     for (auto &b : wb) blocks.push_back(b);
-    return materialize_plan(h, kind, layout, blocks, P, false);
+    return RNG_OK;
 }
 
 // Segments, ring links, block shape and device buffers of a list of blocks
@@ -612,10 +630,43 @@ int build_multihit_plan(ising_t h, uint32_t n_strips, Plan &P)
     return materialize_plan(h, t.kind, t.layout, blocks, P, true);
 }
 
+// Splits the lattices of one kind group into waves whose streams fit the
+// device's registers (kWaveStreamsPerSm per SM: two blocks of 512 threads
+// with two resident streams each), first fit in decreasing size; a lattice
+// larger than that is a wave of its own.  Each wave is one persistent launch
+// per chunk of sweeps, its generator states in registers for the whole
+// launch; lattices are independent, so running them in waves changes no
+// result, while one launch over all of them would stream every state
+// through L2 in every half-sweep.
+std::vector<std::vector<uint32_t>> split_waves(const ising_t h, std::vector<uint32_t> ids, uint64_t cap_streams)
+{
+    std::stable_sort(ids.begin(), ids.end(),
+                     [&](uint32_t a, uint32_t b) { return h->lats[a].nstreams > h->lats[b].nstreams; });
+    std::vector<std::vector<uint32_t>> waves;
+    std::vector<uint64_t> used;
+    for (uint32_t id : ids) {
+        const uint64_t n = h->lats[id].nstreams;
+        size_t w = 0;
+        while (w < waves.size() && used[w] + n > cap_streams) w++;
+        if (w == waves.size()) {
+            waves.emplace_back();
+            used.push_back(0);
+        }
+        waves[w].push_back(id);
+        used[w] += n;
+    }
+    for (auto &w : waves) std::sort(w.begin(), w.end());
+    return waves;
+}
+
 int ensure_plan(ising_t h)
 {
     if (h->planned) return RNG_OK;
-    // one group per (kind, layout)
+    int dev = 0, sms = 0;
+    RNGX_CHECK_CUDA(cudaGetDevice(&dev));
+    RNGX_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const uint64_t cap_streams = static_cast<uint64_t>(sms) * kWaveStreamsPerSm;
+    // one group per (kind, layout), each in waves of register-resident size
     std::vector<std::pair<int, int>> keys;
     for (auto &t : h->lats)
         if (std::find(keys.begin(), keys.end(), std::make_pair(t.kind, t.layout)) == keys.end())
@@ -624,12 +675,14 @@ int ensure_plan(ising_t h)
         std::vector<uint32_t> ids;
         for (uint32_t i = 0; i < h->lats.size(); i++)
             if (h->lats[i].kind == k.first && h->lats[i].layout == k.second) ids.push_back(i);
-        Plan P;
-        int st = build_plan(h, k.first, k.second, ids, P);
-        h->plans.push_back(P);
-        if (st != RNG_OK) {
-            free_plans(h);
-            return st;
+        for (auto &wave : split_waves(h, ids, cap_streams)) {
+            Plan P;
+            int st = build_plan(h, k.first, k.second, wave, P);
+            h->plans.push_back(P);
+            if (st != RNG_OK) {
+                free_plans(h);
+                return st;
+            }
         }
     }
     h->planned = true;

@@ -266,6 +266,30 @@ def test_batch_matches_lattices_alone(R):
         R.ising_destroy(h)
 
 
+def test_batch_in_several_waves_matches_lattices_alone(R):
+    # more streams of one kind than the device keeps in registers at once
+    # (2048 per SM): that kind group runs as two waves of launches
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cap = sms * 2048
+    n512 = cap // (512 * 512 // 4) + 1
+    Ls = [512] * n512 + [256, 64, 16] + [512, 512, 128, 32]
+    kinds = [O.XORWOW] * (n512 + 3) + [O.XS1024W] * 4
+    betas = [0.30 + 0.02 * b for b in range(len(Ls))]
+    h = R.ising_batch_create(Ls, betas, kinds, SEED + 9, 2)
+    try:
+        info = R.ising_plan_info(h)
+        assert info["groups"] == 3, info
+        R.ising_batch_sweep(h, 12, 4)
+        for b, L in enumerate(Ls):
+            ref, acc, nm = O.ising_run(L, betas[b], kinds[b], O.seed_word(SEED + 9, b), 12, measure_every=4)
+            assert np.array_equal(R.ising_batch_get_spins(h, b), ref), b
+            obs = R.ising_batch_observables(h, b)
+            assert obs["n_meas"] == nm and obs["acc"] == acc.tolist(), b
+    finally:
+        R.ising_destroy(h)
+
+
 def test_strip_that_stops_publishing_times_out_without_hanging(R):
     import time
     h = R.ising_create(1024, 0.4, 0, O.XORWOW, 0, SEED, 2)
