@@ -388,7 +388,7 @@ struct SegPlan {
 };
 
 int materialize_plan(ising_t h, int kind, int layout, const std::vector<std::vector<SegPlan>> &blocks, Plan &P,
-                     bool multihit);
+                     bool multihit, unsigned cfg_threads);
 int plan_blocks(ising_t h, const std::vector<uint32_t> &ids, double target, std::vector<std::vector<SegPlan>> &blocks);
 
 // Plans one kind group: splits big lattices into aligned row strips, packs
@@ -398,13 +398,29 @@ int build_plan(ising_t h, int kind, int layout, const std::vector<uint32_t> &ids
     int dev = 0, sms = 0;
     RNGX_CHECK_CUDA(cudaGetDevice(&dev));
     RNGX_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int per_sm = h->cfg_ctas_per_sm > 0 ? h->cfg_ctas_per_sm : 1;
-    const uint64_t target_blocks = static_cast<uint64_t>(sms) * per_sm;
+    int per_sm = h->cfg_ctas_per_sm > 0 ? h->cfg_ctas_per_sm : 1;
+    unsigned cfg_threads = h->cfg_threads;
     uint64_t total_sites = 0;
     for (uint32_t id : ids) total_sites += static_cast<uint64_t>(h->lats[id].L) * h->lats[id].L;
     // about one block per SM (or per_sm), but no fewer than 1024 sites per
     // block: smaller strips spend their time waiting on their neighbours
-    const double min_sites = h->cfg_min_sites ? static_cast<double>(h->cfg_min_sites) : 1024.0;
+    double min_sites = h->cfg_min_sites ? static_cast<double>(h->cfg_min_sites) : 1024.0;
+    if (!h->batch && ids.size() == 1 && !h->cfg_threads && !h->cfg_ctas_per_sm && !h->cfg_min_sites) {
+        // a single lattice without a tuned shape takes the shapes the
+        // autotuner finds: one block with one stream per thread when its
+        // streams fit (no exchange at all), and two blocks of 512 threads
+        // with two resident streams each per SM when one block per SM would
+        // need more than 1024 streams (both always fit the device)
+        const uint64_t n = h->lats[ids[0]].nstreams;
+        if (n <= 1024) {
+            min_sites = static_cast<double>(total_sites);
+            cfg_threads = static_cast<unsigned>(std::max<uint64_t>(32, (n + 31) / 32 * 32));
+        } else if (n > static_cast<uint64_t>(sms) * 1024 && n <= static_cast<uint64_t>(sms) * 2048) {
+            per_sm = 2;
+            cfg_threads = 512;
+        }
+    }
+    const uint64_t target_blocks = static_cast<uint64_t>(sms) * per_sm;
     double target = std::max(min_sites, static_cast<double>(total_sites) / target_blocks);
     std::vector<std::vector<SegPlan>> blocks;
     // each lattice's strip count is rounded on its own, so the blocks can
@@ -416,7 +432,7 @@ int build_plan(ising_t h, int kind, int layout, const std::vector<uint32_t> &ids
         if (blocks.size() <= target_blocks) break;
         target *= 1.02 * static_cast<double>(blocks.size()) / static_cast<double>(target_blocks);
     }
-    return materialize_plan(h, kind, layout, blocks, P, false);
+    return materialize_plan(h, kind, layout, blocks, P, false, cfg_threads);
 }
 
 // Strips and packed whole lattices of about `target` sites each, one list
@@ -478,7 +494,7 @@ int plan_blocks(ising_t h, const std::vector<uint32_t> &ids, double target, std:
 // (each a list of strips).  Strips of one lattice are linked into a ring in
 // list order; a strip's coarse colour is its position in that ring mod 2.
 int materialize_plan(ising_t h, int kind, int layout, const std::vector<std::vector<SegPlan>> &blocks, Plan &P,
-                     bool multihit)
+                     bool multihit, unsigned cfg_threads)
 {
     std::vector<SegDev> segs;
     std::vector<uint32_t> cta(1, 0);
@@ -522,8 +538,8 @@ int materialize_plan(ising_t h, int kind, int layout, const std::vector<std::vec
     }
     // block shape: up to 4 streams per thread keep their state in registers;
     // beyond that the kernel streams the states through L2 each half-sweep
-    unsigned threads = h->cfg_threads ? h->cfg_threads : 256;
-    while (!h->cfg_threads && threads < 1024 && (max_streams + threads - 1) / threads > 4) threads *= 2;
+    unsigned threads = cfg_threads ? cfg_threads : 256;
+    while (!cfg_threads && threads < 1024 && (max_streams + threads - 1) / threads > 4) threads *= 2;
     uint64_t spt = std::min<uint64_t>(4, std::max<uint64_t>(1, (max_streams + threads - 1) / threads));
     if (spt >= 2 && threads > 512) {  // multi-slot kernels are built for at most 512 threads
         threads = 512;
@@ -535,7 +551,7 @@ int materialize_plan(ising_t h, int kind, int layout, const std::vector<std::vec
     // lattices of 16 .. 512)
     if (!multihit && max_streams > 4ull * threads) spt = 1;
     bool fixed = false;  // fixed slot roles (the kernel's modes 2 and 3)
-    if (multihit && !h->cfg_threads && max_streams <= 2048) {
+    if (multihit && !cfg_threads && max_streams <= 2048) {
         // one stream of each coarse colour per thread: every thread works
         // in both phases (the multi-hit kernel runs two slots at up to 1024)
         threads = static_cast<unsigned>(std::max<uint64_t>(32, max_streams / 2));
@@ -627,7 +643,7 @@ int build_multihit_plan(ising_t h, uint32_t n_strips, Plan &P)
     std::vector<std::vector<SegPlan>> blocks;
     for (uint32_t m = 0; m < n_strips / 2; m++)
         blocks.push_back({{0, 2 * m * R, (2 * m + 1) * R}, {0, (2 * m + 1) * R, (2 * m + 2) * R}});
-    return materialize_plan(h, t.kind, t.layout, blocks, P, true);
+    return materialize_plan(h, t.kind, t.layout, blocks, P, true, h->cfg_threads);
 }
 
 // Splits the lattices of one kind group into waves whose streams fit the

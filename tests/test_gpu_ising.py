@@ -180,9 +180,10 @@ def test_launch_shape_does_not_change_results(R):
 def test_whole_lattice_in_one_block(R, L, layout, kind):
     # one block holds the whole lattice, one stream per thread: a half-sweep
     # is one pass and one barrier, the edge rows also writing their halo
-    # copies; the default shape splits the lattice into strips instead
+    # copies (as does the default shape wherever the streams fit one block);
+    # 256 threads with 1024 sites per block split it into strips instead
     ref, acc, nm = O.ising_run(L, 0.43, kind, SEED, 40, measure_every=4)
-    for shape in ((1024, 1, 1 << 16), (0, 0, 0)):
+    for shape in ((1024, 1, 1 << 16), (0, 0, 0), (256, 1, 1024)):
         h = R.ising_create(L, 0.43, layout, kind, 0, SEED, 2)
         try:
             R.ising_set_launch(h, *shape)
@@ -200,9 +201,10 @@ def test_whole_lattice_in_one_block(R, L, layout, kind):
 def test_fixed_slot_exact_checkerboard(R, L, layout, kind, flags):
     # two blocks of 512 per SM: one strip of 2 to 4 rows per block, whose
     # first and last rows fill every thread's slot 0 and the rows between its
-    # slot 1 (the fixed-slot kernel); the default shape runs the general loop
+    # slot 1 (the fixed-slot kernel; the default shape at L = 1024); one block
+    # of 512 per SM runs the general loop with up to four slots per thread
     ref, acc, nm = O.ising_run(L, BETA_C, kind, SEED, 30, flags=flags, measure_every=3)
-    for shape in ((512, 2, 0), (0, 0, 0)):
+    for shape in ((512, 2, 0), (0, 0, 0), (512, 1, 0)):
         h = R.ising_create(L, BETA_C, layout, kind, flags, SEED, 2)
         try:
             R.ising_set_launch(h, *shape)
