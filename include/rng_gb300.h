@@ -269,8 +269,12 @@ int ising_observables(ising_t h, int64_t *E, int64_t *M, int64_t acc[4], uint64_
 /* Launch shape of the persistent kernel: threads per block (multiple of 32,
  * <= 1024; 0 = heuristic), blocks per SM the row-strip plan aims for (0 =
  * heuristic), and the fewest sites a block takes before lattices are split
- * into more strips (0 = 1024).  Results do not depend on it: the draw
- * order is fixed by the site numbering alone. */
+ * into more strips (0 = 1024).  With all three 0, a single lattice whose
+ * streams fit one block (at most 1024) runs whole in one block with one
+ * stream per thread, and one needing 1024 to 2048 streams per SM runs two
+ * blocks of 512 threads per SM; everything else aims for one block per SM.
+ * Results do not depend on the shape: the draw order is fixed by the site
+ * numbering alone. */
 int ising_set_launch(ising_t h, uint32_t threads, int ctas_per_sm, uint32_t min_sites_per_block);
 
 /* The launch shape last set by ising_set_launch or chosen by
