@@ -74,6 +74,9 @@ def lib():
                 "orc_mt19937_raw": (None, [u32, u64, p]),
                 "orc_lfib_raw": (i32, [u32, u32, i32, p, u64, p]),
                 "orc_ising_run_multihit": (i32, [u32, dbl, i32, u32, u64, u32, u32, u32, u64, u32, i32, p, p, p]),
+                "orc_ising_half_sweep_given": (i32, [u32, dbl, u32, i32, u32, u32, u64, p, p]),
+                "orc_ising_sweep_given": (i32, [u32, dbl, u32, u64, p, p]),
+                "orc_ising_multihit_round_given": (i32, [u32, dbl, u32, u32, u32, u64, p, p]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -228,6 +231,52 @@ def ising_run_multihit(L: int, beta: float, kind: int, seed: int, n_rounds: int,
                                         measure_every, philox_rounds, _ptr(s), _ptr(acc), ctypes.byref(nm)),
            "ising_run_multihit")
     return s, acc, nm.value
+
+
+def _lattices(spins: np.ndarray, L: int) -> np.ndarray:
+    s = np.ascontiguousarray(spins, dtype=np.int8).copy()
+    assert s.shape[-2:] == (L, L)
+    return s.reshape(-1, L, L)
+
+
+def ising_half_sweep_given(spins: np.ndarray, beta: float, colour: int, draws: np.ndarray, *, G: int = 2,
+                           rows: tuple[int, int] | None = None) -> np.ndarray:
+    """One half-sweep of the oracle's update on each lattice of spins (shape
+    (..., L, L)) with the caller's numbers: draws[b, sidx, g] is the g-th
+    number of stream sidx of lattice b (L^2 / (2G) streams; only the streams
+    of rows [row0, row1) are read).  Returns the new spins."""
+    L = spins.shape[-1]
+    s = _lattices(spins, L)
+    d = np.ascontiguousarray(draws, dtype=np.uint32).reshape(s.shape[0], -1)
+    assert d.shape[1] == L * L // 2
+    r0, r1 = rows if rows is not None else (0, L)
+    _check(lib().orc_ising_half_sweep_given(L, beta, G, colour, r0, r1, s.shape[0], _ptr(d), _ptr(s)),
+           "ising_half_sweep_given")
+    return s.reshape(spins.shape)
+
+
+def ising_sweep_given(spins: np.ndarray, beta: float, draws: np.ndarray, *, G: int = 2) -> np.ndarray:
+    """One sweep (colour 0 then colour 1) with the caller's numbers:
+    draws[b, sidx, d] is the d-th of the 2G numbers of stream sidx."""
+    L = spins.shape[-1]
+    s = _lattices(spins, L)
+    d = np.ascontiguousarray(draws, dtype=np.uint32).reshape(s.shape[0], -1)
+    assert d.shape[1] == L * L
+    _check(lib().orc_ising_sweep_given(L, beta, G, s.shape[0], _ptr(d), _ptr(s)), "ising_sweep_given")
+    return s.reshape(spins.shape)
+
+
+def ising_multihit_round_given(spins: np.ndarray, beta: float, draws: np.ndarray, *, k: int, n_strips: int,
+                               G: int = 2) -> np.ndarray:
+    """One multi-hit round with the caller's numbers: draws[b, sidx, d] is
+    the d-th of the 2kG numbers of stream sidx."""
+    L = spins.shape[-1]
+    s = _lattices(spins, L)
+    d = np.ascontiguousarray(draws, dtype=np.uint32).reshape(s.shape[0], -1)
+    assert d.shape[1] == L * L * k
+    _check(lib().orc_ising_multihit_round_given(L, beta, G, n_strips, k, s.shape[0], _ptr(d), _ptr(s)),
+           "ising_multihit_round_given")
+    return s.reshape(spins.shape)
 
 
 def lfib_raw(r: int, s: int, bits: int, seeds, K: int) -> np.ndarray:

@@ -995,6 +995,127 @@ static void ising_site(uint32_t L, int8_t *s, uint64_t q, int colour, uint32_t r
 }
 
 /*
+ * One half-sweep of colour c over the sites owned by streams [s0, s1):
+ * stream sidx's site number g (q = sidx G + g) takes draws[(sidx - s0) G +
+ * g], the g-th number that stream drew for this half-sweep.  Sites of one
+ * colour have no bond between them, so the order of the visits does not
+ * matter.
+ */
+static void ising_half_sweep(uint32_t L, int8_t *s, int c, uint32_t G, uint64_t s0, uint64_t s1,
+                             const uint32_t *draws, const uint64_t T[9])
+{
+    for (uint64_t sidx = s0; sidx < s1; sidx++)
+        for (uint32_t g = 0; g < G; g++) ising_site(L, s, sidx * G + g, c, draws[(sidx - s0) * G + g], T);
+}
+
+/*
+ * Where a half-sweep's numbers come from: fill(ctx, G, s0, s1, draws) puts
+ * the next G numbers of every stream sidx in [s0, s1) at draws[(sidx - s0) G
+ * + g], g = 0 .. G-1, in the order the stream produces them.
+ */
+typedef void (*ising_fill_fn)(void *ctx, uint32_t G, uint64_t s0, uint64_t s1, uint32_t *draws);
+
+/* The streams of an Ising run: per-thread instances, or one 1024-bit state
+ * per warp of 32 streams (lanes beyond the last stream draw but are unused). */
+typedef struct {
+    int kind;
+    int philox_rounds;
+    uint64_t nstreams;
+    inst_t *inst;
+    uint32_t *xs;
+    uint64_t *xs_steps;   /* the Weyl step count of each warp state */
+} ising_streams_t;
+
+static void ising_fill_streams(void *ctx, uint32_t G, uint64_t s0, uint64_t s1, uint32_t *draws)
+{
+    ising_streams_t *st = (ising_streams_t *)ctx;
+    if (st->kind == K_XS1024W) {
+        /* every lane of warp j draws once per step of the warp's state */
+        for (uint32_t g = 0; g < G; g++)
+            for (uint64_t j = s0 / 32; j < (s1 + 31) / 32; j++) {
+                uint32_t o[XS_WORDS];
+                st->xs_steps[j]++;
+                xs_step(st->xs + j * XS_WORDS, st->xs_steps[j], o);
+                for (int l = 0; l < XS_WORDS; l++) {
+                    uint64_t sidx = 32 * j + l;
+                    if (sidx >= s0 && sidx < s1) draws[(sidx - s0) * G + g] = o[l];
+                }
+            }
+        return;
+    }
+    for (uint64_t sidx = s0; sidx < s1; sidx++)
+        for (uint32_t g = 0; g < G; g++) draws[(sidx - s0) * G + g] = inst_next(&st->inst[sidx], st->philox_rounds);
+}
+
+static void ising_streams_free(ising_streams_t *st)
+{
+    if (st->inst)
+        for (uint64_t i = 0; i < st->nstreams; i++) inst_free(&st->inst[i]);
+    free(st->inst);
+    free(st->xs);
+    free(st->xs_steps);
+    st->inst = NULL;
+    st->xs = NULL;
+    st->xs_steps = NULL;
+}
+
+/* Seeds the streams of an L x L lattice at G sites per stream. */
+static int ising_streams_init(ising_streams_t *st, uint32_t L, int kind, uint32_t flags, uint64_t seed, uint32_t G,
+                              int philox_rounds)
+{
+    memset(st, 0, sizeof(*st));
+    st->kind = kind;
+    st->philox_rounds = philox_rounds;
+    st->nstreams = (uint64_t)L * L / 2 / G;
+    uint64_t n = kind == K_XS1024W ? (st->nstreams + 31) / 32 * 32 : st->nstreams;
+    int rc = check_kind_flags(kind, flags, n);
+    if (rc) return rc;
+    if (kind == K_XS1024W) {
+        uint64_t nwarps = n / 32;
+        st->xs = (uint32_t *)malloc(nwarps * XS_WORDS * sizeof(uint32_t));
+        st->xs_steps = (uint64_t *)calloc(nwarps, sizeof(uint64_t));
+        if (!st->xs || !st->xs_steps) { ising_streams_free(st); return ORC_ENOMEM; }
+        for (uint64_t j = 0; j < nwarps; j++)
+            if ((rc = xs_warp_init(flags, seed, j, st->xs + j * XS_WORDS))) { ising_streams_free(st); return rc; }
+        return ORC_OK;
+    }
+    st->inst = (inst_t *)calloc(n, sizeof(inst_t));
+    if (!st->inst) return ORC_ENOMEM;
+    for (uint64_t i = 0; i < n; i++)
+        if ((rc = inst_init(&st->inst[i], kind, flags, seed, n, i))) { ising_streams_free(st); return rc; }
+    return ORC_OK;
+}
+
+/* One sweep: colour 0, then colour 1; every stream draws G numbers per
+ * half-sweep.  draws: scratch of nstreams G words. */
+static void ising_sweep(uint32_t L, int8_t *s, uint32_t G, uint64_t nstreams, ising_fill_fn fill, void *ctx,
+                        uint32_t *draws, const uint64_t T[9])
+{
+    for (int c = 0; c < 2; c++) {
+        fill(ctx, G, 0, nstreams, draws);
+        ising_half_sweep(L, s, c, G, 0, nstreams, draws, T);
+    }
+}
+
+static void ising_measure(uint32_t L, const int8_t *s, int64_t acc[4], uint64_t *n_meas)
+{
+    int64_t E, M;
+    orc_ising_energy(L, s, &E, &M);
+    acc[0] += E;
+    acc[1] += E * E;
+    acc[2] += M * M;
+    acc[3] += M < 0 ? -M : M;
+    (*n_meas)++;
+}
+
+static void ising_thresholds(double beta, uint64_t T[9])
+{
+    memset(T, 0, 9 * sizeof(uint64_t));
+    T[4] = orc_ising_threshold(beta, 4);
+    T[8] = orc_ising_threshold(beta, 8);
+}
+
+/*
  * n_sweeps sweeps from the spins in s (updated in place) with freshly seeded
  * streams (n = L^2 / (2G) instances, rounded up to a multiple of 32 for the
  * 1024-bit generator, whose lanes beyond the last stream draw but are
@@ -1008,61 +1129,19 @@ int orc_ising_run(uint32_t L, double beta, int kind, uint32_t flags, uint64_t se
     if (L < 2 || L % 2 || G == 0 || ((uint64_t)L * L / 2) % G || kind == K_MT || kind == K_LFIB521 ||
         kind == K_LFIB1279)
         return ORC_EINVAL;
-    uint64_t nstreams = (uint64_t)L * L / 2 / G;
-    uint64_t n = kind == K_XS1024W ? (nstreams + 31) / 32 * 32 : nstreams;
-    int st = check_kind_flags(kind, flags, n);
-    if (st) return st;
-    uint64_t T[9] = {0};
-    T[4] = orc_ising_threshold(beta, 4);
-    T[8] = orc_ising_threshold(beta, 8);
-
-    inst_t *inst = NULL;
-    uint32_t *xs = NULL;
-    uint64_t nwarps = n / 32;
-    if (kind == K_XS1024W) {
-        xs = (uint32_t *)malloc(nwarps * XS_WORDS * sizeof(uint32_t));
-        if (!xs) return ORC_ENOMEM;
-        for (uint64_t j = 0; j < nwarps; j++)
-            if ((st = xs_warp_init(flags, seed, j, xs + j * XS_WORDS))) { free(xs); return st; }
-    } else {
-        inst = (inst_t *)calloc(n, sizeof(inst_t));
-        if (!inst) return ORC_ENOMEM;
-        for (uint64_t i = 0; i < n; i++)
-            if ((st = inst_init(&inst[i], kind, flags, seed, n, i))) { free(inst); return st; }
-    }
-    uint64_t xs_steps = 0;
+    ising_streams_t st;
+    int rc = ising_streams_init(&st, L, kind, flags, seed, G, philox_rounds);
+    if (rc) return rc;
+    uint32_t *draws = (uint32_t *)malloc(st.nstreams * G * sizeof(uint32_t));
+    if (!draws) { ising_streams_free(&st); return ORC_ENOMEM; }
+    uint64_t T[9];
+    ising_thresholds(beta, T);
     for (uint64_t t = 1; t <= n_sweeps; t++) {
-        for (int c = 0; c < 2; c++) {
-            if (kind == K_XS1024W) {
-                for (uint32_t g = 0; g < G; g++) {
-                    xs_steps++;
-                    for (uint64_t j = 0; j < nwarps; j++) {
-                        uint32_t o[XS_WORDS];
-                        xs_step(xs + j * XS_WORDS, xs_steps, o);
-                        for (int l = 0; l < XS_WORDS; l++) {
-                            uint64_t sidx = 32 * j + l;
-                            if (sidx < nstreams) ising_site(L, s, sidx * G + g, c, o[l], T);
-                        }
-                    }
-                }
-            } else {
-                for (uint64_t sidx = 0; sidx < nstreams; sidx++)
-                    for (uint32_t g = 0; g < G; g++)
-                        ising_site(L, s, sidx * G + g, c, inst_next(&inst[sidx], philox_rounds), T);
-            }
-        }
-        if (measure_every && t % measure_every == 0) {
-            int64_t E, M;
-            orc_ising_energy(L, s, &E, &M);
-            acc[0] += E;
-            acc[1] += E * E;
-            acc[2] += M * M;
-            acc[3] += M < 0 ? -M : M;
-            (*n_meas)++;
-        }
+        ising_sweep(L, s, G, st.nstreams, ising_fill_streams, &st, draws, T);
+        if (measure_every && t % measure_every == 0) ising_measure(L, s, acc, n_meas);
     }
-    free(xs);
-    free(inst);
+    free(draws);
+    ising_streams_free(&st);
     return ORC_OK;
 }
 
@@ -1079,81 +1158,130 @@ int orc_ising_run(uint32_t L, double beta, int kind, uint32_t flags, uint64_t se
  * Metropolis update, so the Boltzmann distribution is left invariant.
  * Measurements (if measure_every > 0) follow every measure_every-th round.
  */
+static void ising_multihit_round(uint32_t L, int8_t *s, uint32_t G, uint32_t n_strips, uint32_t k_hits,
+                                 uint64_t per_strip, ising_fill_fn fill, void *ctx, uint32_t *draws,
+                                 const uint64_t T[9])
+{
+    for (uint32_t C = 0; C < 2; C++)
+        for (uint32_t hit = 0; hit < k_hits; hit++)
+            for (int c = 0; c < 2; c++)
+                for (uint32_t b = C; b < n_strips; b += 2) {
+                    uint64_t s0 = b * per_strip, s1 = s0 + per_strip;
+                    fill(ctx, G, s0, s1, draws);
+                    ising_half_sweep(L, s, c, G, s0, s1, draws, T);
+                }
+}
+
+static int multihit_args_ok(uint32_t L, uint32_t G, uint32_t n_strips, uint32_t k_hits)
+{
+    return L >= 2 && L % 2 == 0 && G != 0 && (L / 2) % G == 0 && n_strips >= 2 && n_strips % 2 == 0 &&
+           L % n_strips == 0 && k_hits != 0;
+}
+
 int orc_ising_run_multihit(uint32_t L, double beta, int kind, uint32_t flags, uint64_t seed, uint32_t G,
                            uint32_t n_strips, uint32_t k_hits, uint64_t n_rounds, uint32_t measure_every,
                            int philox_rounds, int8_t *s, int64_t acc[4], uint64_t *n_meas)
 {
-    if (L < 2 || L % 2 || G == 0 || (L / 2) % G || kind == K_MT || kind == K_LFIB521 || kind == K_LFIB1279 ||
-        n_strips < 2 || n_strips % 2 ||
-        L % n_strips || k_hits == 0)
+    if (!multihit_args_ok(L, G, n_strips, k_hits) || kind == K_MT || kind == K_LFIB521 || kind == K_LFIB1279)
         return ORC_EINVAL;
-    uint64_t nstreams = (uint64_t)L * L / 2 / G;
-    uint64_t n = kind == K_XS1024W ? (nstreams + 31) / 32 * 32 : nstreams;
-    int st = check_kind_flags(kind, flags, n);
-    if (st) return st;
-    uint64_t T[9] = {0};
-    T[4] = orc_ising_threshold(beta, 4);
-    T[8] = orc_ising_threshold(beta, 8);
-    uint64_t spr = (uint64_t)(L / 2) / G;       /* streams per row */
-    uint64_t rows = L / n_strips;               /* rows per strip */
-    uint64_t per_strip = rows * spr;            /* streams per strip */
-    if (kind == K_XS1024W && per_strip % 32) return ORC_EINVAL;  /* a warp state within one strip */
-
-    inst_t *inst = NULL;
-    uint32_t *xs = NULL;
-    uint64_t *xs_steps = NULL;   /* the Weyl step count of each warp state */
-    uint64_t nwarps = n / 32;
-    if (kind == K_XS1024W) {
-        xs = (uint32_t *)malloc(nwarps * XS_WORDS * sizeof(uint32_t));
-        xs_steps = (uint64_t *)calloc(nwarps, sizeof(uint64_t));
-        if (!xs || !xs_steps) { free(xs); free(xs_steps); return ORC_ENOMEM; }
-        for (uint64_t j = 0; j < nwarps; j++)
-            if ((st = xs_warp_init(flags, seed, j, xs + j * XS_WORDS))) { free(xs); free(xs_steps); return st; }
-    } else {
-        inst = (inst_t *)calloc(n, sizeof(inst_t));
-        if (!inst) return ORC_ENOMEM;
-        for (uint64_t i = 0; i < n; i++)
-            if ((st = inst_init(&inst[i], kind, flags, seed, n, i))) { free(inst); return st; }
-    }
+    uint64_t per_strip = (uint64_t)(L / n_strips) * ((L / 2) / G);  /* streams per strip */
+    if (kind == K_XS1024W && per_strip % 32) return ORC_EINVAL;      /* a warp state within one strip */
+    ising_streams_t st;
+    int rc = ising_streams_init(&st, L, kind, flags, seed, G, philox_rounds);
+    if (rc) return rc;
+    uint32_t *draws = (uint32_t *)malloc(per_strip * G * sizeof(uint32_t));
+    if (!draws) { ising_streams_free(&st); return ORC_ENOMEM; }
+    uint64_t T[9];
+    ising_thresholds(beta, T);
     for (uint64_t t = 1; t <= n_rounds; t++) {
-        for (uint32_t C = 0; C < 2; C++) {
-            for (uint32_t hit = 0; hit < k_hits; hit++) {
-                for (int c = 0; c < 2; c++) {
-                    for (uint32_t b = C; b < n_strips; b += 2) {
-                        uint64_t s0 = b * per_strip, s1 = s0 + per_strip;
-                        if (kind == K_XS1024W) {
-                            for (uint32_t g = 0; g < G; g++)
-                                for (uint64_t j = s0 / 32; j < s1 / 32; j++) {
-                                    uint32_t o[XS_WORDS];
-                                    xs_steps[j]++;
-                                    xs_step(xs + j * XS_WORDS, xs_steps[j], o);
-                                    for (int l = 0; l < XS_WORDS; l++) {
-                                        uint64_t sidx = 32 * j + l;
-                                        if (sidx < nstreams) ising_site(L, s, sidx * G + g, c, o[l], T);
-                                    }
-                                }
-                        } else {
-                            for (uint64_t sidx = s0; sidx < s1; sidx++)
-                                for (uint32_t g = 0; g < G; g++)
-                                    ising_site(L, s, sidx * G + g, c, inst_next(&inst[sidx], philox_rounds), T);
-                        }
-                    }
-                }
-            }
-        }
-        if (measure_every && t % measure_every == 0) {
-            int64_t E, M;
-            orc_ising_energy(L, s, &E, &M);
-            acc[0] += E;
-            acc[1] += E * E;
-            acc[2] += M * M;
-            acc[3] += M < 0 ? -M : M;
-            (*n_meas)++;
-        }
+        ising_multihit_round(L, s, G, n_strips, k_hits, per_strip, ising_fill_streams, &st, draws, T);
+        if (measure_every && t % measure_every == 0) ising_measure(L, s, acc, n_meas);
     }
-    free(xs);
-    free(xs_steps);
-    free(inst);
+    free(draws);
+    ising_streams_free(&st);
+    return ORC_OK;
+}
+
+/*
+ * The same updates driven by numbers the caller gives, for tests that
+ * enumerate the draws (the exact transition matrix of the update): stream
+ * sidx's d-th draw of the call is given[sidx * per_stream + d].  Each of
+ * n_lattices lattices (spins: n_lattices L x L arrays, updated in place)
+ * takes its own block of nstreams * per_stream words.
+ */
+typedef struct {
+    const uint32_t *given;
+    uint64_t per_stream;
+    uint64_t *used;       /* draws taken so far by each stream */
+} ising_given_t;
+
+static void ising_fill_given(void *ctx, uint32_t G, uint64_t s0, uint64_t s1, uint32_t *draws)
+{
+    ising_given_t *gv = (ising_given_t *)ctx;
+    for (uint64_t sidx = s0; sidx < s1; sidx++)
+        for (uint32_t g = 0; g < G; g++) {
+            uint64_t d = gv->used[sidx]++;
+            draws[(sidx - s0) * G + g] = d < gv->per_stream ? gv->given[sidx * gv->per_stream + d] : 0;
+        }
+}
+
+/* One half-sweep of colour c over the rows [row0, row1) (the streams that
+ * own them: G numbers each). */
+int orc_ising_half_sweep_given(uint32_t L, double beta, uint32_t G, int colour, uint32_t row0, uint32_t row1,
+                               uint64_t n_lattices, const uint32_t *given, int8_t *spins)
+{
+    if (L < 2 || L % 2 || G == 0 || (L / 2) % G || colour < 0 || colour > 1 || row0 >= row1 || row1 > L)
+        return ORC_EINVAL;
+    uint64_t spr = (L / 2) / G, nstreams = (uint64_t)L * L / 2 / G;
+    uint64_t s0 = row0 * spr, s1 = row1 * spr;
+    uint64_t T[9];
+    ising_thresholds(beta, T);
+    for (uint64_t b = 0; b < n_lattices; b++)
+        ising_half_sweep(L, spins + b * L * L, colour, G, s0, s1, given + b * nstreams * G + s0 * G, T);
+    return ORC_OK;
+}
+
+/* One sweep (both colours, 2G numbers per stream), as in orc_ising_run. */
+int orc_ising_sweep_given(uint32_t L, double beta, uint32_t G, uint64_t n_lattices, const uint32_t *given,
+                          int8_t *spins)
+{
+    if (L < 2 || L % 2 || G == 0 || ((uint64_t)L * L / 2) % G) return ORC_EINVAL;
+    uint64_t nstreams = (uint64_t)L * L / 2 / G;
+    uint32_t *draws = (uint32_t *)malloc(nstreams * G * sizeof(uint32_t));
+    uint64_t *used = (uint64_t *)calloc(nstreams, sizeof(uint64_t));
+    if (!draws || !used) { free(draws); free(used); return ORC_ENOMEM; }
+    uint64_t T[9];
+    ising_thresholds(beta, T);
+    for (uint64_t b = 0; b < n_lattices; b++) {
+        ising_given_t gv = {given + b * nstreams * 2 * G, 2 * (uint64_t)G, used};
+        memset(used, 0, nstreams * sizeof(uint64_t));
+        ising_sweep(L, spins + b * L * L, G, nstreams, ising_fill_given, &gv, draws, T);
+    }
+    free(draws);
+    free(used);
+    return ORC_OK;
+}
+
+/* One multi-hit round (2 k G numbers per stream), as in orc_ising_run_multihit. */
+int orc_ising_multihit_round_given(uint32_t L, double beta, uint32_t G, uint32_t n_strips, uint32_t k_hits,
+                                   uint64_t n_lattices, const uint32_t *given, int8_t *spins)
+{
+    if (!multihit_args_ok(L, G, n_strips, k_hits)) return ORC_EINVAL;
+    uint64_t nstreams = (uint64_t)L * L / 2 / G;
+    uint64_t per_strip = (uint64_t)(L / n_strips) * ((L / 2) / G);
+    uint64_t per_stream = 2 * (uint64_t)k_hits * G;
+    uint32_t *draws = (uint32_t *)malloc(per_strip * G * sizeof(uint32_t));
+    uint64_t *used = (uint64_t *)calloc(nstreams, sizeof(uint64_t));
+    if (!draws || !used) { free(draws); free(used); return ORC_ENOMEM; }
+    uint64_t T[9];
+    ising_thresholds(beta, T);
+    for (uint64_t b = 0; b < n_lattices; b++) {
+        ising_given_t gv = {given + b * nstreams * per_stream, per_stream, used};
+        memset(used, 0, nstreams * sizeof(uint64_t));
+        ising_multihit_round(L, spins + b * L * L, G, n_strips, k_hits, per_strip, ising_fill_given, &gv, draws, T);
+    }
+    free(draws);
+    free(used);
     return ORC_OK;
 }
 

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from ising_stats import jackknife_e_cv
 from oracle import ising_exact as X
 
 mp = pytest.importorskip("mpmath")
@@ -80,23 +81,20 @@ def test_initial_spins_are_balanced():
 @pytest.mark.parametrize("beta", [0.3, 0.4])
 def test_checkerboard_chain_reproduces_exact_energy(kind, flags, beta):
     # Application test of Sec. 2 on a lattice whose exact values are cheap:
-    # e and C_V of an 8x8 torus, estimated from 50 independent chunks.
+    # e and C_V of an 8x8 torus from 50 independent chains, pooled, with
+    # jackknife errors over the chains
     L, chunks, per = 8, 50, 2000
-    e_chunks, cv_chunks = [], []
-    N = L * L
+    sE, sE2, nb = [], [], []
     for c in range(chunks):
         s0, _, _ = O.ising_run(L, beta, kind, 5000 + c, 200, flags=flags)  # equilibration
         s, acc, nm = O.ising_run(L, beta, kind, 9000 + c, per, measure_every=1, spins=s0, flags=flags)
-        mE = acc[0] / nm
-        mE2 = acc[1] / nm
-        e_chunks.append(-mE / N)
-        cv_chunks.append(beta * beta * (mE2 - mE * mE) / N)
+        sE.append(acc[0])
+        sE2.append(acc[1])
+        nb.append(nm)
+    (e_est, e_err), (cv_est, cv_err) = jackknife_e_cv(sE, sE2, nb, L * L, beta)
     e_ex, cv_ex = X.exact_e_cv(L, beta)
-    e_est, e_err = np.mean(e_chunks), np.std(e_chunks, ddof=1) / np.sqrt(chunks)
-    cv_est, cv_err = np.mean(cv_chunks), np.std(cv_chunks, ddof=1) / np.sqrt(chunks)
     assert abs(e_est - e_ex) < 4.5 * e_err, (e_est, e_ex, e_err)
-    # per-chunk variance estimates are biased by O(tau/per); allow that too
-    assert abs(cv_est - cv_ex) < 4.5 * cv_err + 0.02 * cv_ex, (cv_est, cv_ex, cv_err)
+    assert abs(cv_est - cv_ex) < 4.5 * cv_err, (cv_est, cv_ex, cv_err)
 
 
 def test_zero_temperature_energy_never_increases():
@@ -166,19 +164,18 @@ def test_multihit_zero_temperature_energy_never_increases():
 @pytest.mark.parametrize("beta", [0.3, 0.4])
 def test_multihit_chain_reproduces_exact_energy(k, strips, beta):
     # single-site Metropolis steps in any order keep the Boltzmann weights:
-    # e and C_V of an 8x8 torus from 50 independent chunks
+    # e and C_V of an 8x8 torus from 50 independent chains, pooled, with
+    # jackknife errors over the chains
     L, chunks, rounds = 8, 50, 2000 // k
-    e_c, cv_c = [], []
-    N = L * L
+    sE, sE2, nb = [], [], []
     for c in range(chunks):
         s0, _, _ = O.ising_run_multihit(L, beta, O.XORWOW, 300 + c, 100, k=k, n_strips=strips)
         _, acc, nm = O.ising_run_multihit(L, beta, O.XORWOW, 700 + c, rounds, k=k, n_strips=strips,
                                           measure_every=1, spins=s0)
-        mE, mE2 = acc[0] / nm, acc[1] / nm
-        e_c.append(-mE / N)
-        cv_c.append(beta * beta * (mE2 - mE * mE) / N)
+        sE.append(acc[0])
+        sE2.append(acc[1])
+        nb.append(nm)
+    (e_est, e_err), (cv_est, cv_err) = jackknife_e_cv(sE, sE2, nb, L * L, beta)
     e_ex, cv_ex = X.exact_e_cv(L, beta)
-    e_est, e_err = np.mean(e_c), np.std(e_c, ddof=1) / np.sqrt(chunks)
-    cv_est, cv_err = np.mean(cv_c), np.std(cv_c, ddof=1) / np.sqrt(chunks)
     assert abs(e_est - e_ex) < 4.5 * e_err, (e_est, e_ex, e_err)
-    assert abs(cv_est - cv_ex) < 4.5 * cv_err + 0.03 * cv_ex, (cv_est, cv_ex, cv_err)
+    assert abs(cv_est - cv_ex) < 4.5 * cv_err, (cv_est, cv_ex, cv_err)
