@@ -145,8 +145,7 @@ int rng_skipahead(rng_t h, uint64_t n);
  * array the caller owns, with no device allocation of any kind: for callers
  * that cannot allocate device memory (code inside a framework that owns
  * every device allocation, or that must not let an allocation synchronise
- * the device mid-sequence).  The paper has no counterpart; it is an
- * interface variant of the skip-ahead of Sec. 6.
+ * the device mid-sequence).  The paper has no counterpart.
  *  d_state: device array in the library's state layout, advanced in place:
  *    RNG_XORWOW   6 consecutive arrays of n_instances words (x, y, z, w, v, d);
  *    RNG_XS1024W  n_instances words, 32 consecutive words per warp state
@@ -156,8 +155,10 @@ int rng_skipahead(rng_t h, uint64_t n);
  *  matrices), held by every GPU that loads the library until the process
  *  exits.  States wider than 1024 bits (RNG_MT19937_SHARED, RNG_LFIB*) are rejected
  *  with RNG_EINVAL; kinds that skip without matrices (LCGs, MWC, Philox)
- *  with RNG_EUNSUPPORTED.  The first call on a device looks up the array's
- *  device address with that device current (make it before any stream
+ *  with RNG_EUNSUPPORTED; more than (2^31 - 1) * 256 instances (one launch
+ *  of 256-thread blocks) with RNG_EINVAL.  Every call looks up the array's
+ *  device address with the calling device current; the first call on a
+ *  device also loads the library's module there (make it before any stream
  *  capture).  Every call on a device shares the one array: calls whose work
  *  overlaps on the GPU (different streams, no ordering) race and give wrong
  *  results; order them on one stream or synchronise between them.

@@ -11,7 +11,6 @@
 // largest generator, 1024 state bits: 3 x 1024 x 1024 bits = 384 KiB.  Every
 // GPU that loads the library holds that array until the process exits.
 #include <cstring>
-#include <mutex>
 
 #include "gen_device.cuh"
 
@@ -23,28 +22,22 @@ constexpr size_t kMatrixWords = static_cast<size_t>(kMaxStateBits) * (kMaxStateB
 static __device__ __align__(256) uint32_t g_skip_scratch[3 * kMatrixWords];
 
 // Host code sees g_skip_scratch only as a stand-in symbol: its device
-// address is looked up once per device, with that device current.
-std::mutex g_mu;
-uint32_t *g_addr[64] = {};
-
+// address is looked up on every call, with the calling device current, so
+// that no pointer outlives a cudaDeviceReset (which reloads the module and
+// can move the array).  The lookup costs little; the first one on a device
+// also loads the module there.
 int scratch_address(uint32_t **out)
 {
-    int dev = 0;
-    RNGX_CHECK_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) {
-        rngx::set_error("rng_skipahead_noalloc: device index %d out of range", dev);
-        return RNG_EINVAL;
-    }
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_skip_scratch);
-        if (e != cudaSuccess) return rngx::cuda_fail(e, "cudaGetSymbolAddress(g_skip_scratch)");
-        g_addr[dev] = static_cast<uint32_t *>(p);
-    }
-    *out = g_addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_skip_scratch);
+    if (e != cudaSuccess) return rngx::cuda_fail(e, "cudaGetSymbolAddress(g_skip_scratch)");
+    *out = static_cast<uint32_t *>(p);
     return RNG_OK;
 }
+
+// One thread per instance in blocks of 256: the grid's x extent (at most
+// 2^31 - 1 blocks) bounds the instance count.
+constexpr uint64_t kMaxInstances = ((1ull << 31) - 1) * 256ull;
 
 }  // namespace
 
@@ -76,6 +69,11 @@ extern "C" int rng_skipahead_noalloc(int kind, void *d_state, uint64_t n_instanc
     }
     if (!d_state || n_instances == 0) {
         set_error("rng_skipahead_noalloc: null state or no instances");
+        return RNG_EINVAL;
+    }
+    if (n_instances > kMaxInstances) {
+        set_error("rng_skipahead_noalloc: %llu instances exceed the %llu that one launch covers",
+                  static_cast<unsigned long long>(n_instances), static_cast<unsigned long long>(kMaxInstances));
         return RNG_EINVAL;
     }
     if (kind == RNG_XS1024W && n_instances % 32) {

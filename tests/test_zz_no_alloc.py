@@ -2,14 +2,17 @@
 device memory (a framework that owns every device allocation, or a sequence
 that must not synchronise on an allocation).  It advances a state array the
 caller owns, keeping its matrix scratch in a static device array, and must
-give exactly what rng_skipahead gives on a library handle.  Collected last on
-purpose: a failure here comes after every other test has run."""
+give exactly what rng_skipahead gives on a library handle -- on two calls in
+a row, with every way the library could allocate made to fail, and with the
+device's free memory unchanged.  Collected last on purpose: a failure here
+comes after every other test has run."""
 import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
 
 SEED = 0x0123456789ABCDEF
+STEPS = (12345, 2**40 + 77)  # two calls in a row
 
 
 @pytest.fixture(scope="module")
@@ -26,21 +29,47 @@ def state_words(R, h, n_words):
 
 
 @pytest.mark.parametrize("kind,n,arrays", [(3, 1000, 6), (5, 4096, 1)])
-def test_noalloc_matches_rng_skipahead_twice(env, kind, n, arrays):
+def test_noalloc_matches_rng_skipahead_twice(env, kind, n, arrays, monkeypatch):
     R, torch = env
+    # the expected states, from a library handle and its allocating skip-ahead
     h = R.rng_create(kind, n)
     try:
         R.rng_seed(h, SEED)
-        mine = torch.from_numpy(state_words(R, h, arrays * n).view(np.int32)).cuda()
-        for t in (12345, 2**40 + 77):  # two calls in a row
-            R.rng_skipahead_noalloc(kind, mine.data_ptr(), n, t)
+        start = state_words(R, h, arrays * n)
+        expected = []
+        for t in STEPS:
             R.rng_skipahead(h, t)
-            torch.cuda.synchronize()
-            ref = state_words(R, h, arrays * n)
-            got = mine.cpu().numpy().view(np.uint32)
-            assert np.array_equal(got, ref), t
+            expected.append(state_words(R, h, arrays * n))
     finally:
         R.rng_destroy(h)
+    mine = torch.from_numpy(start.view(np.int32)).cuda()
+    # a first call loads the module (and its static array) on this device
+    warm = mine.clone()
+    R.rng_skipahead_noalloc(kind, warm.data_ptr(), n, 1)
+    torch.cuda.synchronize()
+
+    # every allocation route of the library fails from here on: the
+    # injected out-of-memory fault and an allocator that counts and refuses
+    calls = []
+
+    def refuse(nbytes, stream):
+        calls.append(nbytes)
+        return 0
+
+    monkeypatch.setenv("RNG_FAULT", "oom")
+    R.rng_set_allocator(refuse, lambda ptr, stream: None)
+    try:
+        free_before, _ = torch.cuda.mem_get_info()
+        for t, want in zip(STEPS, expected):
+            R.rng_skipahead_noalloc(kind, mine.data_ptr(), n, t)
+            torch.cuda.synchronize()
+            got = mine.cpu().numpy().view(np.uint32)
+            assert np.array_equal(got, want), t
+        free_after, _ = torch.cuda.mem_get_info()
+    finally:
+        R.rng_set_allocator()
+    assert calls == [], "the no-allocation entry point asked the allocator for memory"
+    assert free_after == free_before, "device memory was allocated during the calls"
 
 
 def test_noalloc_rejects_what_it_cannot_do(env):
@@ -57,3 +86,7 @@ def test_noalloc_rejects_what_it_cannot_do(env):
     assert e.value.status == R.RNG_EINVAL
     with pytest.raises(R.RngError):
         R.rng_skipahead_noalloc(R.RNG_XORWOW, 0, 64, 5)
+    # more instances than one launch covers: rejected before anything runs
+    with pytest.raises(R.RngError) as e:
+        R.rng_skipahead_noalloc(R.RNG_XORWOW, buf.data_ptr(), 1 << 40, 5)
+    assert e.value.status == R.RNG_EINVAL and "instances" in str(e.value)
