@@ -416,30 +416,74 @@ def test_argument_errors(R, torch_cuda):
 # ------------------------------------------------ full size (config 2)
 @pytest.mark.parametrize("kind", ALL_KINDS)
 def test_full_size_sampled(R, torch_cuda, kind):
-    """2^30 outputs per call in the bench's launch configuration, checked on
-    sampled instances (every draw of each sampled instance)."""
+    """2^30 outputs per call in the bench's launch configuration and order
+    (u32, f32, normal, then u32 consumed in registers as an XOR, one handle),
+    checked on sampled instances, every draw of each: bit-exact for u32, f32
+    and the XOR, within 2e-6 for the normals."""
     torch = torch_cuda
     if kind in SHARED_KINDS:
         n, K, layout = 1 << 15, 1 << 15, 1  # one generator per warp, 2^20 threads
     else:
         n, K, layout = 1 << 20, 1024, 0
-    flags = O.SEED_SUBSTREAM if kind == O.XS1024W else 0
+    h = R.rng_create(kind, n, 0)
+    try:
+        R.rng_seed(h, SEED)
+        buf = torch.empty(n * K, dtype=torch.int32, device="cuda")
+        red = torch.empty(n, dtype=torch.int32, device="cuda")
+        rng = np.random.default_rng(kind)
+        if kind == O.XS1024W:
+            samp = sorted({0, 31, 32, n - 1, *rng.integers(0, n, 6).tolist()})
+        elif kind in SHARED_KINDS:
+            samp = sorted({0, 1, n - 1, *rng.integers(0, n, 5).tolist()})
+        else:
+            samp = sorted({0, 1, n - 1, *rng.integers(0, n, 24).tolist()})
+        want = {i: O.generate(kind, SEED, n, 4 * K, i_lo=i, i_hi=i + 1)[0] for i in samp}
+
+        def column(i):
+            v = buf.view(K, n)[:, i] if layout == 0 else buf.view(n, K)[i]
+            return v.cpu().numpy()
+
+        R.rng_generate_u32(h, buf.data_ptr(), K, layout)
+        torch.cuda.synchronize()
+        for i in samp:
+            assert np.array_equal(column(i).view(np.uint32), want[i][:K]), ("u32", i)
+        R.rng_generate_f32(h, buf.data_ptr(), K, layout)
+        torch.cuda.synchronize()
+        for i in samp:
+            assert np.array_equal(column(i).view(np.float32), as_f32_oracle(want[i][K:2 * K])), ("f32", i)
+        R.rng_generate_normal(h, buf.data_ptr(), K, layout)
+        torch.cuda.synchronize()
+        for i in samp:
+            z = O.box_muller(want[i][2 * K:3 * K])
+            dev = np.abs(column(i).view(np.float32).astype(np.float64) - z).max()
+            assert dev <= NORMAL_TOL, ("normal", i, dev)
+        R.rng_generate_u32(h, red.data_ptr(), K, R.RNG_XOR_REDUCE)
+        torch.cuda.synchronize()
+        got = red.cpu().numpy().view(np.uint32)
+        for i in samp:
+            assert got[i] == np.bitwise_xor.reduce(want[i][3 * K:]), ("xor", i)
+        del buf
+    finally:
+        R.rng_destroy(h)
+
+
+@pytest.mark.parametrize("kind", [O.XS1024W, O.MWC])
+def test_full_size_sampled_u32_substream_and_same_a(R, torch_cuda, kind):
+    """u32 at the bench's size with the other seeding modes: sub-streams for
+    the 1024-bit generator, one shared multiplier for MWC."""
+    torch = torch_cuda
+    n, K = 1 << 20, 1024
+    flags = O.SEED_SUBSTREAM if kind == O.XS1024W else O.MWC_SAME_A
     h = R.rng_create(kind, n, flags)
     try:
         R.rng_seed(h, SEED)
         buf = torch.empty(n * K, dtype=torch.int32, device="cuda")
-        R.rng_generate_u32(h, buf.data_ptr(), K, layout)
+        R.rng_generate_u32(h, buf.data_ptr(), K, 0)
         torch.cuda.synchronize()
-        rng = np.random.default_rng(kind)
-        if kind == O.XS1024W:
-            samp = sorted({0, 31, 32, n - 1, *rng.integers(0, n, 6).tolist()})
-        else:
-            samp = sorted({0, 1, n - 1, *rng.integers(0, n, 24).tolist()})
-        view = buf.view(K, n) if layout == 0 else buf.view(n, K)
-        for i in samp:
-            g = (view[:, i] if layout == 0 else view[i]).cpu().numpy().view(np.uint32)
-            o = O.generate(kind, SEED, n, K, flags=flags, i_lo=i, i_hi=i + 1)[0]
-            assert np.array_equal(g, o), i
+        rng = np.random.default_rng(7 + kind)
+        for i in sorted({0, 31, 32, n - 1, *rng.integers(0, n, 6).tolist()}):
+            g = buf.view(K, n)[:, i].cpu().numpy().view(np.uint32)
+            assert np.array_equal(g, O.generate(kind, SEED, n, K, flags=flags, i_lo=i, i_hi=i + 1)[0]), i
         del buf
     finally:
         R.rng_destroy(h)
