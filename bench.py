@@ -10,6 +10,9 @@ reduce).  One step = those 40 calls (ten kinds x four forms).  `value` = outputs
 device time (Gnum/s).  Extra keys report the Ising sweep (flips/ns) and
 the other workloads.
 
+`--case gen|ising|all` runs one kernel configuration on a small case for a
+profiler instead (see run_case).
+
 Under torchrun (N>1) each rank holds its own shard of an N x 2^20-instance
 generator (global instance indices, no collective on the data path):
 weak scaling.
@@ -44,6 +47,18 @@ FORMS = ["u32", "f32", "normal", "u32_xor"]
 STATE_TRAFFIC = {0: 8, 1: 16, 2: 20, 3: 48, 4: 8, 5: 8, 6: 2 * 624 * 4, 7: 8, 8: 2 * 521 * 4, 9: 2 * 1279 * 4}
 # LCG32, LCG64, MWC, XORWOW, Philox4x32-10, XS1024W, MT19937, Philox4x32-7,
 # lagged Fibonacci (521, 353) and (1279, 861)
+# Algorithmic integer operations per number of each generator's recurrence
+# (the roof of the consume-in-register form, which writes 4 B per instance):
+# LCG32 one multiply-add; LCG64 a 64-bit multiply-add (3 32-bit operations);
+# MWC a 32 x 32 -> 64-bit multiply-add and a move; XORWOW four shifts, four
+# XORs (two three-input), the Weyl add and the output add (8); Philox4x32-10
+# per 4 numbers 10 rounds of two wide multiplies, three XORs and two key adds
+# (18 per number; 7 rounds: 12.6); the 1024-bit generator per word three
+# funnel shifts, three XORs, the three pairs of neighbour words (6 shuffles)
+# and the Weyl output (16); MT19937 per word the twist (mask merge, shift,
+# conditional XOR, XOR: 4) and the tempering (4 shifts, 4 masked XORs: 8);
+# lagged Fibonacci one add.
+ALG_OPS = {0: 1.0, 1: 3.0, 2: 2.0, 3: 8.0, 4: 18.0, 5: 16.0, 6: 12.0, 7: 12.6, 8: 1.0, 9: 1.0}
 N_KINDS = 10
 SHARED = (6, 8, 9)  # block-shared kinds: one state per warp, 2^15 generators x 2^15 draws
 
@@ -134,7 +149,7 @@ def file_hash(paths):
 
 
 GEN_SOURCES = ["paper_1204_6193_gb300/csrc/gen.cu", "paper_1204_6193_gb300/csrc/gen_device.cuh",
-               "paper_1204_6193_gb300/csrc/lfib.cu", "paper_1204_6193_gb300/csrc/normal_poly.h"]
+               "paper_1204_6193_gb300/csrc/lfib.cu", "paper_1204_6193_gb300/csrc/normal_tables.h"]
 
 
 def _ncu_summary():
@@ -148,14 +163,14 @@ def _ncu_summary():
     return d if d.get("source_hash") == file_hash(GEN_SOURCES) else None
 
 
-def binding_roof(hbm: dict, issue: dict | None) -> dict:
-    """The roof that binds a kernel: instruction issue (bound "alu") when its
-    fraction of the issue roof is higher than its fraction of HBM bandwidth,
-    as for the normal-deviate kernels; else HBM.  Without instruction counts
-    (sources changed since the ncu capture) only HBM can be stated."""
-    if issue is not None and issue["frac"] > hbm["frac"]:
-        return {"bound": "alu", "achieved": issue["achieved_tinst_s"], "peak": issue["peak_tinst_s"],
-                "unit": "T thread-instructions/s", "frac": issue["frac"], "peak_source": issue["peak_source"]}
+def roof_of(form: str, hbm: dict, alg: dict) -> dict:
+    """The roof of a generation call by the algorithmic work it must do: a
+    call that writes its numbers is bound by HBM (output bytes plus the
+    state's load and store); the consume-in-register call writes 4 bytes per
+    instance and is bound by the integer operations of the recurrence
+    (ALG_OPS) against the instruction-issue roof."""
+    if form == "u32_xor":
+        return {"bound": "alu", **alg}
     return {"bound": "hbm", **hbm}
 
 
@@ -308,14 +323,31 @@ def run_gpu(args):
         issue_peak, issue_src = None, None
 
     def issue_of(name, c, avg_ms):
+        """Executed thread instructions (ncu count per output) against the
+        issue roof: why a kernel sits where it does, not its roofline."""
         ipo = ncu_inst_per_output(name)
         if ipo is None or issue_peak is None:
             return None
         ach = ipo * c[4] * c[5] / (avg_ms * 1e-3) / 1e12
         return {"inst_per_output": round(ipo, 2), "achieved_tinst_s": round(ach, 2),
                 "peak_tinst_s": round(issue_peak, 2), "frac": round(ach / issue_peak, 3), "peak_source": issue_src,
-                "source": "thread instructions per output from profiles/gen_bulk_traffic.json (ncu) x outputs / "
-                          "CUDA-event time"}
+                "source": "executed thread instructions per output (profiles/gen_bulk_traffic.json, ncu) x "
+                          "outputs / CUDA-event time"}
+
+    def hbm_of(c, avg_ms):
+        ach = bulk.algorithmic_bytes(c) / (avg_ms * 1e-3) / 1e9
+        return {"achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(ach / peaks["hbm_gbs"], 4),
+                "peak_source": f"{peaks['source']} (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)"
+                if peaks["source"] == "measured" else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": bulk.algorithmic_bytes(c)}
+
+    def alg_of(c, avg_ms):
+        ops = ALG_OPS[c[1]]
+        ach = ops * c[4] * c[5] / (avg_ms * 1e-3) / 1e12
+        return {"achieved": round(ach, 2), "peak": round(issue_peak, 2) if issue_peak else None,
+                "unit": "T integer ops/s", "frac": round(ach / issue_peak, 4) if issue_peak else None,
+                "peak_source": issue_src, "ops_per_number": ops}
 
     detail = {}
     best = None
@@ -323,33 +355,30 @@ def run_gpu(args):
         c = d["call"]
         avg = sum(d["ms"]) / len(d["ms"])
         tot = sum(d["ms"])
-        gb = bulk.algorithmic_bytes(c) / (avg * 1e-3) / 1e9
-        detail[name] = {"ms": round(avg, 4), "gnum_s": round(c[4] * c[5] / (avg * 1e-3) / 1e9, 1),
-                        "gb_s": round(gb, 1), "frac_hbm": round(gb / peaks["hbm_gbs"], 3)}
+        rec = {"ms": round(avg, 4), "gnum_s": round(c[4] * c[5] / (avg * 1e-3) / 1e9, 1)}
+        if c[2] == "u32_xor":
+            a = alg_of(c, avg)
+            rec.update({"bound": "alu", "frac_alg_ops": a["frac"], "ops_per_number": a["ops_per_number"]})
+        else:
+            h_ = hbm_of(c, avg)
+            rec.update({"bound": "hbm", "gb_s": h_["achieved"], "frac_hbm": h_["frac"]})
         iss = issue_of(name, c, avg)
         if iss:
-            detail[name]["issue_frac"] = iss["frac"]
+            rec["issue_frac"] = iss["frac"]
+            rec["inst_per_output"] = iss["inst_per_output"]
+        detail[name] = rec
         if best is None or tot > best[1]:
             best = (name, tot, avg, c)
     name, tot, avg, c = best
-    ach = bulk.algorithmic_bytes(c) / (avg * 1e-3) / 1e9
     step_ms_total = sum(sum(d["ms"]) for d in per.values())
-    hbm = {
-        "achieved": round(ach, 1),
-        "peak": peaks["hbm_gbs"],
-        "unit": "GB/s",
-        "frac": round(ach / peaks["hbm_gbs"], 4),
-        "peak_source": f"{peaks['source']} (MEASURED_PEAKS.json hbm_gbs)" if peaks["source"] == "measured"
-        else "fallback 6.8 TB/s",
-    }
-    iss = issue_of(name, c, avg)
-    roofline = {"kernel": name, **binding_roof(hbm, iss)}
+    roofline = {"kernel": name, **roof_of(c[2], hbm_of(c, avg), alg_of(c, avg))}
     roofline.update({
         "share_of_step": round(tot / step_ms_total, 3),
-        "algorithmic_bytes_per_launch": bulk.algorithmic_bytes(c),
+        "launch_ms": round(avg, 4),
+        "timing": "mean CUDA-event time of the kernel's launches inside the timed region, on its stream",
         "traffic": ncu_traffic(name),
-        "hbm": hbm,
-        "issue": iss,
+        "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum per launch (profiles/gen_bulk_traffic.json)",
+        "issue": issue_of(name, c, avg),
     })
 
     # end to end through the C ABI with host buffers: each step reseeds from a
@@ -407,7 +436,7 @@ def run_gpu(args):
                     i += 1
             stream.wait_stream(copy_stream)
 
-        variants = {}
+        variants, step_ms = {}, {}
         for name, fn in (("direct", run_direct), ("copy_overlapped", run_copy)):
             barrier()
             s0 = torch.cuda.Event(enable_timing=True)
@@ -418,9 +447,28 @@ def run_gpu(args):
             barrier()
             e_ms = max_over_ranks(s0.elapsed_time(s1), dist if world > 1 else None, "cuda")
             variants[name] = round(outputs_per_step_rank * world * e_steps / (e_ms * 1e-3) / 1e9, 2)
+            step_ms[name] = e_ms / e_steps
         best = max(variants, key=variants.get)
+        # the host link's own roof: a plain pinned device-to-host copy of the
+        # 4 GiB output buffer, best of three, CUDA events on this stream
+        link = []
+        for _ in range(3):
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            host.copy_(bulk.out, non_blocking=True)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            link.append(host.numel() * 4 / (c0.elapsed_time(c1) * 1e-3) / 1e9)
+        link_gbs = max(link)
+        d2h = sum(out_bytes)
+        achieved_gbs = d2h / (step_ms[best] * 1e-3) / 1e9
         e2e = {"value": variants[best], "unit": "Gnum/s", "h2d_bytes_per_step": 0,
-               "d2h_bytes_per_step": sum(out_bytes), "steps": e_steps, "variant": best, "variants": variants,
+               "d2h_bytes_per_step": d2h, "steps": e_steps, "variant": best, "variants": variants,
+               "roofline": {"bound": "host link", "achieved": round(achieved_gbs, 1), "peak": round(link_gbs, 1),
+                            "unit": "GB/s", "frac": round(achieved_gbs / link_gbs, 3),
+                            "peak_source": "pinned device-to-host copy of 4 GiB (torch copy_, best of 3, CUDA "
+                                           "events), measured in this run"},
                "note": "seed passed by value (no input arrays); every output lands in pinned host memory"}
         del dev2
 
@@ -869,6 +917,63 @@ def run_reference(args):
             "e2e": {"value": round(v, 4), "unit": "Gnum/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ------------------------------------------------------- single-kernel cases
+def run_case(args):
+    """One kernel configuration on a small case, for a profiler: `gen` runs
+    --reps calls of one generator kind and form; `ising` one persistent
+    Ising launch (or multi-hit rounds with --hits); `all` one call of every
+    kind and form of the bulk workload with its instance counts and
+    --outputs / instances draws.  Prints "ok"."""
+    import torch
+
+    import paper_1204_6193_gb300 as R
+
+    torch.cuda.set_device(0)
+    kind = {v: k for k, v in R.KIND_NAMES.items()}[args.kind]
+    if args.case == "all":
+        out = torch.empty(args.outputs, dtype=torch.int32, device="cuda")
+        for kd in sorted(R.KIND_NAMES):
+            n = MT_GENS if kd in SHARED else N_INST
+            K = args.outputs // n
+            lay = R.RNG_INSTANCE_MAJOR if kd in SHARED else R.RNG_STEP_MAJOR
+            h = R.rng_create(kd, n)
+            R.rng_seed(h, SEED)
+            R.rng_generate_u32(h, out.data_ptr(), K, lay)
+            R.rng_generate_f32(h, out.data_ptr(), K, lay)
+            R.rng_generate_normal(h, out.data_ptr(), K, lay)
+            R.rng_generate_u32(h, out.data_ptr(), K, R.RNG_XOR_REDUCE)
+            torch.cuda.synchronize()
+            R.rng_destroy(h)
+    elif args.case == "ising":
+        layout = R.ISING_INT8 if args.spins == "int8" else R.ISING_MULTISPIN32
+        h = R.ising_create(args.L, BETA_C, layout, kind, 0, SEED, 2)
+        if args.launch:
+            R.ising_set_launch(h, *(int(v) for v in args.launch.split(",")))
+        if args.hits:
+            R.ising_sweep_multihit(h, args.sweeps, args.hits, args.strips)
+        else:
+            R.ising_sweep(h, args.sweeps)
+        R.ising_observables(h)
+        R.ising_destroy(h)
+    else:
+        layout = {"step": R.RNG_STEP_MAJOR, "instance": R.RNG_INSTANCE_MAJOR}[args.layout]
+        h = R.rng_create(kind, args.n)
+        R.rng_seed(h, SEED)
+        out = torch.empty(args.n * (1 if args.form == "u32_xor" else args.K), dtype=torch.int32, device="cuda")
+        for _ in range(args.reps):
+            if args.form == "u32":
+                R.rng_generate_u32(h, out.data_ptr(), args.K, layout)
+            elif args.form == "f32":
+                R.rng_generate_f32(h, out.data_ptr(), args.K, layout)
+            elif args.form == "normal":
+                R.rng_generate_normal(h, out.data_ptr(), args.K, layout)
+            else:
+                R.rng_generate_u32(h, out.data_ptr(), args.K, R.RNG_XOR_REDUCE)
+        torch.cuda.synchronize()
+        R.rng_destroy(h)
+    print("ok")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -885,7 +990,25 @@ def main():
     ap.add_argument("--batch-sweeps", type=int, default=10000)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=10000)
+    # single-kernel cases for profiling (see run_case)
+    ap.add_argument("--case", choices=["gen", "ising", "all"], default=None)
+    ap.add_argument("--kind", default="lcg32")
+    ap.add_argument("--form", default="u32", choices=["u32", "f32", "normal", "u32_xor"])
+    ap.add_argument("--layout", default="step", choices=["step", "instance"])
+    ap.add_argument("--n", type=int, default=1 << 20, help="instances (or warp-shared generators)")
+    ap.add_argument("--K", type=int, default=64, help="draws per instance and call")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--L", type=int, default=1024, help="Ising lattice size")
+    ap.add_argument("--spins", default="int8", choices=["int8", "multispin"])
+    ap.add_argument("--sweeps", type=int, default=200, help="Ising sweeps (or multi-hit rounds)")
+    ap.add_argument("--hits", type=int, default=0, help="k > 0: multi-hit rounds of k sweeps per strip phase")
+    ap.add_argument("--strips", type=int, default=256)
+    ap.add_argument("--launch", default="", help="threads,ctas_per_sm,min_sites_per_block of the Ising launch")
+    ap.add_argument("--outputs", type=int, default=1 << 26, help="outputs per call with --case all")
     args = ap.parse_args()
+    if args.case:
+        run_case(args)
+        return
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     line = run_reference(args) if args.impl == "reference" else run_gpu(args)
