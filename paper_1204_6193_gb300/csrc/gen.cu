@@ -23,6 +23,8 @@ template <int KIND, int OUT, int LAYOUT>
 __global__ void __launch_bounds__(kBlock) k_generate(DevParams p, void *out_, uint64_t K)
 {
     __shared__ uint32_t tile[LAYOUT == RNG_INSTANCE_MAJOR ? kWarps : 1][32][33];
+    BmTables bt{};
+    if constexpr (OUT == OUT_NORMAL) bt = bm_stage();  // every thread, before any leaves
     const uint64_t n = p.n;
     const uint64_t i = static_cast<uint64_t>(blockIdx.x) * kBlock + threadIdx.x;
     const bool active = i < n;
@@ -49,8 +51,8 @@ __global__ void __launch_bounds__(kBlock) k_generate(DevParams p, void *out_, ui
                                 o[1], o[2], o[3]);
                 if (OUT == OUT_NORMAL) {
                     float z[4];
-                    box_muller(o[0], o[1], z[0], z[1]);
-                    box_muller(o[2], o[3], z[2], z[3]);
+                    box_muller(o[0], o[1], z[0], z[1], bt);
+                    box_muller(o[2], o[3], z[2], z[3], bt);
                     if (LAYOUT == RNG_XOR_REDUCE) {
 #pragma unroll
                         for (int j = 0; j < 4; j++) facc += z[j];
@@ -82,7 +84,7 @@ __global__ void __launch_bounds__(kBlock) k_generate(DevParams p, void *out_, ui
             for (uint64_t k = 0; k < K; k += 2) {
                 const uint32_t r0 = g.next(), r1 = g.next();
                 float z0, z1;
-                box_muller(r0, r1, z0, z1);
+                box_muller(r0, r1, z0, z1, bt);
                 if (active) {
                     st_stream(out + k * n + i, z0);
                     st_stream(out + (k + 1) * n + i, z1);
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(kBlock) k_generate(DevParams p, void *out_, ui
                 for (int j = 0; j < cnt; j += 2) {
                     const uint32_t r0 = g.next(), r1 = g.next();
                     float z0, z1;
-                    box_muller(r0, r1, z0, z1);
+                    box_muller(r0, r1, z0, z1, bt);
                     tile[w][lane][j] = __float_as_uint(z0);
                     tile[w][lane][j + 1] = __float_as_uint(z1);
                 }
@@ -131,7 +133,7 @@ __global__ void __launch_bounds__(kBlock) k_generate(DevParams p, void *out_, ui
             for (uint64_t k = 0; k < K; k += 2) {
                 const uint32_t r0 = g.next(), r1 = g.next();
                 float z0, z1;
-                box_muller(r0, r1, z0, z1);
+                box_muller(r0, r1, z0, z1, bt);
                 acc += z0;
                 acc += z1;
             }
@@ -219,6 +221,8 @@ template <int OUT, int LAYOUT>
 __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out_, uint64_t K)
 {
     __shared__ __align__(16) uint32_t tb_s[OUT == OUT_NORMAL ? kMtWarps : 1][MT_N + 2];  // normals: tempered words, pair-aligned
+    BmTables bt{};
+    if constexpr (OUT == OUT_NORMAL) bt = bm_stage();  // every thread, before any leaves
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t gidx = static_cast<uint64_t>(blockIdx.x) * kMtWarps + w;
     const uint64_t n = p.n;
@@ -272,7 +276,7 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
             for (int t = lane; t < avail / 2; t += 32) {
                 const uint2 pr = reinterpret_cast<const uint2 *>(tb)[t];
                 float z0, z1;
-                box_muller(pr.x, pr.y, z0, z1);
+                box_muller(pr.x, pr.y, z0, z1, bt);
                 if (LAYOUT == RNG_XOR_REDUCE) {
                     facc += z0;
                     facc += z1;
@@ -360,6 +364,8 @@ template <int OUT, int LAYOUT>
 __global__ void __launch_bounds__(kXsBlock) k_generate_xs_reg(DevParams p, void *out_, uint64_t K)
 {
     __shared__ uint32_t tile_s[kXsBlock / 32][32][33];
+    BmTables bt{};
+    if constexpr (OUT == OUT_NORMAL) bt = bm_stage();  // every thread, before any leaves
     const uint64_t n = p.n, nstates = n / 32;
     const uint64_t j = static_cast<uint64_t>(blockIdx.x) * kXsBlock + threadIdx.x;
     const int lane = threadIdx.x & 31;
@@ -414,7 +420,7 @@ __global__ void __launch_bounds__(kXsBlock) k_generate_xs_reg(DevParams p, void 
 #pragma unroll
                 for (int l = 0; l < 32; l++) {
                     float z0, z1;
-                    box_muller(a[l], x[l] + y1, z0, z1);
+                    box_muller(a[l], x[l] + y1, z0, z1, bt);
                     facc[l] += z0;
                     facc[l] += z1;
                 }
@@ -459,7 +465,7 @@ __global__ void __launch_bounds__(kXsBlock) k_generate_xs_reg(DevParams p, void 
 #pragma unroll
                 for (int l = 0; l < 32; l++) {
                     float z0, z1;
-                    box_muller(a[l], x[l] + y1, z0, z1);
+                    box_muller(a[l], x[l] + y1, z0, z1, bt);
                     a[l] = __float_as_uint(z0);
                     z1b[l] = __float_as_uint(z1);
                 }
@@ -503,6 +509,21 @@ inline bool xs_reg_normals(uint64_t n)
     return n / 32 >= 200ull * static_cast<uint64_t>(sms);
 }
 
+// Launches KERN with the Box-Muller tables' dynamic shared memory when it
+// makes normals.
+template <int OUT, auto KERN>
+int launch_gen(dim3 grid, int block, cudaStream_t s, const DevParams &p, void *out, uint64_t K)
+{
+    size_t smem = 0;
+    if constexpr (OUT == OUT_NORMAL) {
+        RNGX_CHECK_CUDA(bm_allow_smem<KERN>());
+        smem = kBmSmemBytes;
+    }
+    KERN<<<grid, block, smem, s>>>(p, out, K);
+    RNGX_CHECK_LAUNCH();
+    return RNG_OK;
+}
+
 template <int KIND, int OUT>
 int launch_kind_out(const GenState &g, void *out, uint64_t K, int layout, cudaStream_t s)
 {
@@ -510,25 +531,26 @@ int launch_kind_out(const GenState &g, void *out, uint64_t K, int layout, cudaSt
     if constexpr (KIND == RNG_MT19937_SHARED) {
         const dim3 grid(static_cast<unsigned>((g.n + kMtWarps - 1) / kMtWarps));
         switch (layout) {
-        case RNG_STEP_MAJOR: k_generate_mt<OUT, RNG_STEP_MAJOR><<<grid, kMtBlock, 0, s>>>(p, out, K); break;
-        case RNG_INSTANCE_MAJOR: k_generate_mt<OUT, RNG_INSTANCE_MAJOR><<<grid, kMtBlock, 0, s>>>(p, out, K); break;
-        default: k_generate_mt<OUT, RNG_XOR_REDUCE><<<grid, kMtBlock, 0, s>>>(p, out, K); break;
+        case RNG_STEP_MAJOR: return launch_gen<OUT, k_generate_mt<OUT, RNG_STEP_MAJOR>>(grid, kMtBlock, s, p, out, K);
+        case RNG_INSTANCE_MAJOR:
+            return launch_gen<OUT, k_generate_mt<OUT, RNG_INSTANCE_MAJOR>>(grid, kMtBlock, s, p, out, K);
+        default: return launch_gen<OUT, k_generate_mt<OUT, RNG_XOR_REDUCE>>(grid, kMtBlock, s, p, out, K);
         }
     } else if (KIND == RNG_XS1024W && layout != RNG_INSTANCE_MAJOR &&
                (reinterpret_cast<uintptr_t>(out) & 15) == 0 && (OUT != OUT_NORMAL || xs_reg_normals(g.n))) {
         const dim3 grid(static_cast<unsigned>((g.n / 32 + kXsBlock - 1) / kXsBlock));
-        if (layout == RNG_STEP_MAJOR) k_generate_xs_reg<OUT, RNG_STEP_MAJOR><<<grid, kXsBlock, 0, s>>>(p, out, K);
-        else k_generate_xs_reg<OUT, RNG_XOR_REDUCE><<<grid, kXsBlock, 0, s>>>(p, out, K);
+        if (layout == RNG_STEP_MAJOR)
+            return launch_gen<OUT, k_generate_xs_reg<OUT, RNG_STEP_MAJOR>>(grid, kXsBlock, s, p, out, K);
+        return launch_gen<OUT, k_generate_xs_reg<OUT, RNG_XOR_REDUCE>>(grid, kXsBlock, s, p, out, K);
     } else {
         const dim3 grid(static_cast<unsigned>((g.n + kBlock - 1) / kBlock));
         switch (layout) {
-        case RNG_STEP_MAJOR: k_generate<KIND, OUT, RNG_STEP_MAJOR><<<grid, kBlock, 0, s>>>(p, out, K); break;
-        case RNG_INSTANCE_MAJOR: k_generate<KIND, OUT, RNG_INSTANCE_MAJOR><<<grid, kBlock, 0, s>>>(p, out, K); break;
-        default: k_generate<KIND, OUT, RNG_XOR_REDUCE><<<grid, kBlock, 0, s>>>(p, out, K); break;
+        case RNG_STEP_MAJOR: return launch_gen<OUT, k_generate<KIND, OUT, RNG_STEP_MAJOR>>(grid, kBlock, s, p, out, K);
+        case RNG_INSTANCE_MAJOR:
+            return launch_gen<OUT, k_generate<KIND, OUT, RNG_INSTANCE_MAJOR>>(grid, kBlock, s, p, out, K);
+        default: return launch_gen<OUT, k_generate<KIND, OUT, RNG_XOR_REDUCE>>(grid, kBlock, s, p, out, K);
         }
     }
-    RNGX_CHECK_LAUNCH();
-    return RNG_OK;
 }
 
 template <int KIND>
@@ -547,17 +569,18 @@ namespace {
 // Word pairs -> normal pairs, 16-byte loads and stores for four words.
 __global__ void k_u32_to_normal(const uint32_t *in, float *out, uint64_t n_pairs)
 {
+    const BmTables bt = bm_stage();
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
     for (uint64_t q = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; 2 * q < n_pairs; q += stride) {
         if (2 * q + 1 < n_pairs) {
             const uint4 w = reinterpret_cast<const uint4 *>(in)[q];
             float4 z;
-            box_muller(w.x, w.y, z.x, z.y);
-            box_muller(w.z, w.w, z.z, z.w);
+            box_muller(w.x, w.y, z.x, z.y, bt);
+            box_muller(w.z, w.w, z.z, z.w, bt);
             reinterpret_cast<float4 *>(out)[q] = z;
         } else {
             float z0, z1;
-            box_muller(in[4 * q], in[4 * q + 1], z0, z1);
+            box_muller(in[4 * q], in[4 * q + 1], z0, z1, bt);
             out[4 * q] = z0;
             out[4 * q + 1] = z1;
         }
@@ -573,7 +596,8 @@ int launch_u32_to_normal(const uint32_t *in, float *out, uint64_t n_pairs, cudaS
     RNGX_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const uint64_t quads = (n_pairs + 1) / 2;
     const unsigned blocks = static_cast<unsigned>(std::min<uint64_t>((quads + 255) / 256, static_cast<uint64_t>(sms) * 8));
-    k_u32_to_normal<<<blocks, 256, 0, s>>>(in, out, n_pairs);
+    RNGX_CHECK_CUDA(bm_allow_smem<k_u32_to_normal>());
+    k_u32_to_normal<<<blocks, 256, kBmSmemBytes, s>>>(in, out, n_pairs);
     RNGX_CHECK_LAUNCH();
     return RNG_OK;
 }

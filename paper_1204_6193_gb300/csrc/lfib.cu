@@ -55,6 +55,8 @@ __global__ void __launch_bounds__(Lfib<R, S>::kBlock) k_generate_lfib(DevParams 
     // a normal pair never straddles two steps: even steps from the call start
     constexpr int STEP = OUT == OUT_NORMAL ? (S & ~1) : S;
     __shared__ uint32_t ring_s[W][RS];
+    BmTables bt{};
+    if constexpr (OUT == OUT_NORMAL) bt = bm_stage();  // every thread, before any leaves
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t g = static_cast<uint64_t>(blockIdx.x) * W + w;
     const uint64_t n = p.n;
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(Lfib<R, S>::kBlock) k_generate_lfib(DevParams 
                 c0 = c0 >= RS ? c0 - RS : c0;
                 c1 = c1 >= RS ? c1 - RS : c1;
                 float z0, z1;
-                box_muller(ring[c0], ring[c1], z0, z1);
+                box_muller(ring[c0], ring[c1], z0, z1, bt);
                 if (LAYOUT == RNG_XOR_REDUCE) {
                     facc += z0;
                     facc += z1;
@@ -178,6 +180,8 @@ __global__ void __launch_bounds__(LfibChunked<R, S>::kBlock) k_generate_lfib_chu
     constexpr int RS = F::kRS, G = F::kG, U = F::kU, W = F::kWarps;
     constexpr uint32_t MASK = RS - 1;
     __shared__ __align__(16) uint32_t ring_s[W][F::kBuf];
+    BmTables bt{};
+    if constexpr (OUT == OUT_NORMAL) bt = bm_stage();  // every thread, before any leaves
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t g = static_cast<uint64_t>(blockIdx.x) * W + w;
     const uint64_t n = p.n;
@@ -213,7 +217,7 @@ __global__ void __launch_bounds__(LfibChunked<R, S>::kBlock) k_generate_lfib_chu
     auto put_pair = [&](uint32_t pc, uint64_t k, int t) {
         const uint2 pr = *reinterpret_cast<const uint2 *>(ring + pc + 2 * t);
         float z0, z1;
-        box_muller(pr.x, pr.y, z0, z1);
+        box_muller(pr.x, pr.y, z0, z1, bt);
         if (LAYOUT == RNG_XOR_REDUCE) {
             facc += z0;
             facc += z1;
@@ -287,6 +291,19 @@ __global__ void __launch_bounds__(LfibChunked<R, S>::kBlock) k_generate_lfib_chu
     }
 }
 
+template <int OUT, auto KERN>
+int launch_lfib_kernel(dim3 grid, int block, cudaStream_t s, const DevParams &p, void *out, uint64_t K)
+{
+    size_t smem = 0;
+    if constexpr (OUT == OUT_NORMAL) {  // the Box-Muller tables
+        RNGX_CHECK_CUDA(bm_allow_smem<KERN>());
+        smem = kBmSmemBytes;
+    }
+    KERN<<<grid, block, smem, s>>>(p, out, K);
+    RNGX_CHECK_LAUNCH();
+    return RNG_OK;
+}
+
 template <int R, int S, int OUT>
 int launch_out(const GenState &g, void *out, uint64_t K, int layout, cudaStream_t s)
 {
@@ -296,27 +313,24 @@ int launch_out(const GenState &g, void *out, uint64_t K, int layout, cudaStream_
         const dim3 grid(static_cast<unsigned>((g.n + F::kWarps - 1) / F::kWarps));
         switch (layout) {
         case RNG_STEP_MAJOR:
-            k_generate_lfib_chunked<R, S, OUT, RNG_STEP_MAJOR><<<grid, F::kBlock, 0, s>>>(p, out, K);
-            break;
+            return launch_lfib_kernel<OUT, k_generate_lfib_chunked<R, S, OUT, RNG_STEP_MAJOR>>(grid, F::kBlock, s, p,
+                                                                                              out, K);
         case RNG_INSTANCE_MAJOR:
-            k_generate_lfib_chunked<R, S, OUT, RNG_INSTANCE_MAJOR><<<grid, F::kBlock, 0, s>>>(p, out, K);
-            break;
-        default: k_generate_lfib_chunked<R, S, OUT, RNG_XOR_REDUCE><<<grid, F::kBlock, 0, s>>>(p, out, K); break;
+            return launch_lfib_kernel<OUT, k_generate_lfib_chunked<R, S, OUT, RNG_INSTANCE_MAJOR>>(grid, F::kBlock, s,
+                                                                                                  p, out, K);
+        default:
+            return launch_lfib_kernel<OUT, k_generate_lfib_chunked<R, S, OUT, RNG_XOR_REDUCE>>(grid, F::kBlock, s, p,
+                                                                                              out, K);
         }
-        RNGX_CHECK_LAUNCH();
-        return RNG_OK;
     }
-    constexpr int W = Lfib<R, S>::kWarps;
+    constexpr int W = Lfib<R, S>::kWarps, B = Lfib<R, S>::kBlock;
     const dim3 grid(static_cast<unsigned>((g.n + W - 1) / W));
     switch (layout) {
-    case RNG_STEP_MAJOR: k_generate_lfib<R, S, OUT, RNG_STEP_MAJOR><<<grid, Lfib<R, S>::kBlock, 0, s>>>(p, out, K); break;
+    case RNG_STEP_MAJOR: return launch_lfib_kernel<OUT, k_generate_lfib<R, S, OUT, RNG_STEP_MAJOR>>(grid, B, s, p, out, K);
     case RNG_INSTANCE_MAJOR:
-        k_generate_lfib<R, S, OUT, RNG_INSTANCE_MAJOR><<<grid, Lfib<R, S>::kBlock, 0, s>>>(p, out, K);
-        break;
-    default: k_generate_lfib<R, S, OUT, RNG_XOR_REDUCE><<<grid, Lfib<R, S>::kBlock, 0, s>>>(p, out, K); break;
+        return launch_lfib_kernel<OUT, k_generate_lfib<R, S, OUT, RNG_INSTANCE_MAJOR>>(grid, B, s, p, out, K);
+    default: return launch_lfib_kernel<OUT, k_generate_lfib<R, S, OUT, RNG_XOR_REDUCE>>(grid, B, s, p, out, K);
     }
-    RNGX_CHECK_LAUNCH();
-    return RNG_OK;
 }
 
 template <int R, int S>
