@@ -1015,8 +1015,16 @@ static void ising_half_sweep(uint32_t L, int8_t *s, int c, uint32_t G, uint64_t 
  */
 typedef void (*ising_fill_fn)(void *ctx, uint32_t G, uint64_t s0, uint64_t s1, uint32_t *draws);
 
-/* The streams of an Ising run: per-thread instances, or one 1024-bit state
- * per warp of 32 streams (lanes beyond the last stream draw but are unused). */
+/* The streams of an Ising run: per-thread instances, or one state per warp
+ * of 32 streams -- the 1024-bit generator (Sec. 6), and the block-shared
+ * generators MT19937 (Sec. 5) and lagged Fibonacci (Sec. 4), of which
+ * generator j is seeded as generator j of a generation call with
+ * ceil(streams / 32) generators.  In a warp-shared draw round the 32
+ * streams 32j .. 32j+31 each take one word: stream 32j + l takes word l of
+ * the round, so its d-th number is word 32d + l of generator j's stream.
+ * Lanes beyond the last stream draw but are unused. */
+static int warp_shared(int kind) { return kind == K_XS1024W || kind == K_MT || kind == K_LFIB521 || kind == K_LFIB1279; }
+
 typedef struct {
     int kind;
     int philox_rounds;
@@ -1029,14 +1037,18 @@ typedef struct {
 static void ising_fill_streams(void *ctx, uint32_t G, uint64_t s0, uint64_t s1, uint32_t *draws)
 {
     ising_streams_t *st = (ising_streams_t *)ctx;
-    if (st->kind == K_XS1024W) {
-        /* every lane of warp j draws once per step of the warp's state */
+    if (warp_shared(st->kind)) {
+        /* every lane of warp j draws once per round of the warp's generator */
         for (uint32_t g = 0; g < G; g++)
             for (uint64_t j = s0 / 32; j < (s1 + 31) / 32; j++) {
-                uint32_t o[XS_WORDS];
-                st->xs_steps[j]++;
-                xs_step(st->xs + j * XS_WORDS, st->xs_steps[j], o);
-                for (int l = 0; l < XS_WORDS; l++) {
+                uint32_t o[32];
+                if (st->kind == K_XS1024W) {
+                    st->xs_steps[j]++;
+                    xs_step(st->xs + j * XS_WORDS, st->xs_steps[j], o);
+                } else {
+                    for (int l = 0; l < 32; l++) o[l] = inst_next(&st->inst[j], st->philox_rounds);
+                }
+                for (int l = 0; l < 32; l++) {
                     uint64_t sidx = 32 * j + l;
                     if (sidx >= s0 && sidx < s1) draws[(sidx - s0) * G + g] = o[l];
                 }
@@ -1049,8 +1061,9 @@ static void ising_fill_streams(void *ctx, uint32_t G, uint64_t s0, uint64_t s1, 
 
 static void ising_streams_free(ising_streams_t *st)
 {
+    uint64_t n_inst = warp_shared(st->kind) ? (st->nstreams + 31) / 32 : st->nstreams;
     if (st->inst)
-        for (uint64_t i = 0; i < st->nstreams; i++) inst_free(&st->inst[i]);
+        for (uint64_t i = 0; i < n_inst; i++) inst_free(&st->inst[i]);
     free(st->inst);
     free(st->xs);
     free(st->xs_steps);
@@ -1067,7 +1080,8 @@ static int ising_streams_init(ising_streams_t *st, uint32_t L, int kind, uint32_
     st->kind = kind;
     st->philox_rounds = philox_rounds;
     st->nstreams = (uint64_t)L * L / 2 / G;
-    uint64_t n = kind == K_XS1024W ? (st->nstreams + 31) / 32 * 32 : st->nstreams;
+    uint64_t n = kind == K_XS1024W ? (st->nstreams + 31) / 32 * 32
+               : warp_shared(kind) ? (st->nstreams + 31) / 32 : st->nstreams;  /* instances */
     int rc = check_kind_flags(kind, flags, n);
     if (rc) return rc;
     if (kind == K_XS1024W) {
@@ -1126,9 +1140,7 @@ int orc_ising_run(uint32_t L, double beta, int kind, uint32_t flags, uint64_t se
                   uint64_t n_sweeps, uint32_t measure_every, int philox_rounds, int8_t *s,
                   int64_t acc[4], uint64_t *n_meas)
 {
-    if (L < 2 || L % 2 || G == 0 || ((uint64_t)L * L / 2) % G || kind == K_MT || kind == K_LFIB521 ||
-        kind == K_LFIB1279)
-        return ORC_EINVAL;
+    if (L < 2 || L % 2 || G == 0 || ((uint64_t)L * L / 2) % G) return ORC_EINVAL;
     ising_streams_t st;
     int rc = ising_streams_init(&st, L, kind, flags, seed, G, philox_rounds);
     if (rc) return rc;
@@ -1182,10 +1194,9 @@ int orc_ising_run_multihit(uint32_t L, double beta, int kind, uint32_t flags, ui
                            uint32_t n_strips, uint32_t k_hits, uint64_t n_rounds, uint32_t measure_every,
                            int philox_rounds, int8_t *s, int64_t acc[4], uint64_t *n_meas)
 {
-    if (!multihit_args_ok(L, G, n_strips, k_hits) || kind == K_MT || kind == K_LFIB521 || kind == K_LFIB1279)
-        return ORC_EINVAL;
+    if (!multihit_args_ok(L, G, n_strips, k_hits)) return ORC_EINVAL;
     uint64_t per_strip = (uint64_t)(L / n_strips) * ((L / 2) / G);  /* streams per strip */
-    if (kind == K_XS1024W && per_strip % 32) return ORC_EINVAL;      /* a warp state within one strip */
+    if (warp_shared(kind) && per_strip % 32) return ORC_EINVAL;     /* a warp's generator within one strip */
     ising_streams_t st;
     int rc = ising_streams_init(&st, L, kind, flags, seed, G, philox_rounds);
     if (rc) return rc;

@@ -179,3 +179,66 @@ def test_multihit_chain_reproduces_exact_energy(k, strips, beta):
     e_ex, cv_ex = X.exact_e_cv(L, beta)
     assert abs(e_est - e_ex) < 4.5 * e_err, (e_est, e_ex, e_err)
     assert abs(cv_est - cv_ex) < 4.5 * cv_err, (cv_est, cv_ex, cv_err)
+
+
+# ------------------------------- block-shared generators in the application test
+SHARED = [O.MT19937_SHARED, O.LFIB521, O.LFIB1279]
+
+
+@pytest.mark.parametrize("kind", SHARED)
+def test_shared_generator_feeds_its_32_streams_in_lane_order(kind):
+    # generator j serves streams 32j .. 32j+31; the d-th number of stream
+    # 32j + l is word 32d + l of generator j's stream (seeded as generator j
+    # of a generation call with ceil(streams / 32) generators)
+    L, G, beta, seed = 16, 2, 0.44, 77
+    nst = L * L // 2 // G              # 64 streams: 2 generators
+    ngen = (nst + 31) // 32
+    words = O.generate(kind, seed, ngen, 32 * 2 * G)  # one sweep: 2G numbers per stream
+    draws = np.zeros((nst, 2 * G), dtype=np.uint32)
+    for s in range(nst):
+        j, l = divmod(s, 32)
+        draws[s] = words[j, l::32][: 2 * G]
+    s0 = O.ising_init_spins(L, seed)
+    want = O.ising_sweep_given(s0[None], beta, draws[None], G=G)[0]
+    got, _, _ = O.ising_run(L, beta, kind, seed, 1, G=G)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("kind", SHARED)
+def test_shared_generator_infinite_and_zero_temperature(kind):
+    init = O.ising_init_spins(32, 5)
+    out, _, _ = O.ising_run(32, 0.0, kind, 5, 1)
+    assert np.array_equal(out, -init)
+    s = init
+    E_prev = O.ising_energy(s)[0]
+    for t in range(8):
+        s, _, _ = O.ising_run(32, 50.0, kind, 5 + t, 1, spins=s)
+        E = O.ising_energy(s)[0]
+        assert E <= E_prev
+        E_prev = E
+
+
+@pytest.mark.parametrize("kind", SHARED)
+def test_shared_generator_chain_reproduces_exact_energy(kind):
+    # e and C_V of an 8x8 torus at beta = 0.4 from 50 independent chains
+    L, beta, chunks, per = 8, 0.4, 50, 2000
+    sE, sE2, nb = [], [], []
+    for c in range(chunks):
+        s0, _, _ = O.ising_run(L, beta, kind, 5000 + c, 200)
+        _, acc, nm = O.ising_run(L, beta, kind, 9000 + c, per, measure_every=1, spins=s0)
+        sE.append(acc[0])
+        sE2.append(acc[1])
+        nb.append(nm)
+    (e_est, e_err), (cv_est, cv_err) = jackknife_e_cv(sE, sE2, nb, L * L, beta)
+    e_ex, cv_ex = X.exact_e_cv(L, beta)
+    assert abs(e_est - e_ex) < 4.5 * e_err, (e_est, e_ex, e_err)
+    assert abs(cv_est - cv_ex) < 4.5 * cv_err, (cv_est, cv_ex, cv_err)
+
+
+def test_shared_generator_multihit_needs_whole_warps_per_strip():
+    # a warp's generator must lie within one strip: 8 x 8 with 4 strips has
+    # 8 streams per strip
+    with pytest.raises(O.OracleError):
+        O.ising_run_multihit(8, 0.4, O.MT19937_SHARED, 1, 1, k=1, n_strips=4)
+    out, _, _ = O.ising_run_multihit(32, 0.0, O.LFIB521, 3, 1, k=1, n_strips=2)
+    assert np.array_equal(out, -O.ising_init_spins(32, 3))
