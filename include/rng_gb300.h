@@ -212,9 +212,18 @@ int rng_mwc_multipliers(uint64_t first, uint64_t count, uint32_t *host_out);
  * application test).  Colour of site (x, y) = (x + y) & 1; the colour-c
  * sites are numbered q = y (L/2) + (x >> 1); stream s owns q in
  * [sG, (s+1)G) of both colours, giving L^2/(2G) streams of generator
- * `rng_kind` seeded by rng_seed(seed) semantics with `rng_flags`
- * (block-shared kinds -- RNG_MT19937_SHARED, RNG_LFIB521, RNG_LFIB1279 --
- * give no per-site streams: RNG_EUNSUPPORTED).  Initial spins: site j = y L + x is +1 iff bit j % 64 of
+ * `rng_kind` seeded by rng_seed(seed) semantics with `rng_flags`.  The
+ * block-shared kinds (RNG_MT19937_SHARED, Sec. 5; RNG_LFIB521 and
+ * RNG_LFIB1279, Sec. 4 and Table 1) share one generator among 32 streams:
+ * generator j of ceil(streams / 32), seeded as generator j of a generation
+ * handle, feeds streams 32j .. 32j+31 in lane order, so the d-th number of
+ * stream 32j + l is word 32d + l of generator j's stream (as the 1024-bit
+ * generator feeds its lanes).  Their states are too large to stay on chip
+ * for a whole lattice, so their sweeps run the per-half-sweep path: each
+ * half-sweep the generators write their 32 G words per generator to an
+ * L2-resident buffer (the generation kernels), and one kernel consumes
+ * them; ising_batch_create and ising_sweep_multihit do not take them
+ * (RNG_EUNSUPPORTED).  Initial spins: site j = y L + x is +1 iff bit j % 64 of
  * SplitMix64 word j / 64 of (seed XOR 0x5350494E) is set.  Requires L even,
  * 4 <= L <= 65536, G dividing L/2 (each stream's sites lie in one row), and
  * L % 64 == 0 for ISING_MULTISPIN32. */
@@ -248,7 +257,8 @@ int ising_sweep(ising_t h, uint64_t n_sweeps, uint32_t measure_every, void *cuda
  * stream by 2kG draws; k = 1 is a legal Markov chain with a different
  * update order than ising_sweep, and no round equals a plain sweep.
  * measure_every counts rounds (E, M measured after the round).  Requires
- * one lattice per handle (else RNG_EUNSUPPORTED), 1 <= k <= 65536, each
+ * one lattice per handle of a per-thread kind or the 1024-bit generator
+ * (else RNG_EUNSUPPORTED), 1 <= k <= 65536, each
  * strip's streams a multiple of 32 (whole warps), L % 8 == 0 for
  * ISING_INT8, two strips per block fitting in shared memory and n_strips/2
  * co-resident blocks (else RNG_EINVAL / RNG_EUNSUPPORTED).  Asynchronous
@@ -287,7 +297,8 @@ int ising_get_launch(ising_t h, uint32_t *threads, int *ctas_per_sm, uint32_t *m
 /* Times the persistent kernel on a clone of the handle (same lattices and
  * seeds; the handle itself does not advance) for a few launch shapes,
  * probe_sweeps sweeps each, and applies the fastest (reported through the
- * optional outputs). */
+ * optional outputs).  The block-shared kinds have no persistent shape to
+ * tune: RNG_OK with *threads = 256 and *ctas_per_sm = 0. */
 int ising_autotune(ising_t h, uint32_t probe_sweeps, uint32_t *threads, int *ctas_per_sm);
 
 /* The current persistent launch plan: launches per chunk of sweeps (one per
@@ -323,7 +334,8 @@ int ising_info(ising_t h, uint32_t idx, uint32_t *n_lattices, uint32_t *L, int *
 
 /* n independent lattices of sizes L[b], inverse temperatures beta[b] and
  * generator kinds rng_kind[b] (RNG_XORWOW or RNG_XS1024W or any per-thread
- * kind), lattice b seeded with w_b of the master seed; int8 layout.
+ * kind; the block-shared kinds: RNG_EUNSUPPORTED), lattice b seeded with
+ * w_b of the master seed; int8 layout.
  * Batching is not in the paper: it packs many application-test lattices
  * into persistent launches over work lists of (lattice, row strip) items. */
 int ising_batch_create(ising_t *out, uint32_t n, const uint32_t *L, const double *beta,

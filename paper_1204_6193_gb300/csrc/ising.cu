@@ -188,6 +188,69 @@ __global__ void k_meas_finalize(const int64_t *meas, uint32_t n, int64_t *acc)
 __global__ void k_add_u64(uint64_t *p, uint64_t v) { *p += v; }
 __global__ void k_set_u64(uint64_t *p, uint64_t v) { *p = v; }
 
+// One half-sweep with warp-shared generators (MT19937, lagged Fibonacci):
+// their numbers for this half-sweep were generated into `draws`, generator
+// j's 32 G words at draws[j 32 G ..], so that the g-th number of stream s =
+// 32 j + l is draws[j 32 G + 32 g + l].  One thread per stream.
+template <int LAYOUT>
+__global__ void __launch_bounds__(256) k_ising_half_given(LatDev lat, int c, const uint32_t *__restrict__ draws)
+{
+    const uint64_t s = static_cast<uint64_t>(blockIdx.x) * 256 + threadIdx.x;
+    if ((s & ~31ull) >= lat.nstreams) return;  // whole warps
+    const bool valid = s < lat.nstreams;
+    const uint32_t G = lat.G, half = lat.half, L = lat.L;
+    const uint32_t *dr = draws + (s >> 5) * 32ull * G + (s & 31u);
+    const uint64_t q0 = s * G;
+    const uint32_t y = valid ? static_cast<uint32_t>(q0 / half) : 0;
+    const uint32_t xh0 = valid ? static_cast<uint32_t>(q0 - static_cast<uint64_t>(y) * half) : 0;
+    const uint32_t p = (c + y) & 1u;
+    const uint32_t yu = y == 0 ? L - 1 : y - 1, yd = y + 1 == L ? 0 : y + 1;
+    if (LAYOUT == ISING_INT8) {
+        int8_t *sp = static_cast<int8_t *>(lat.spins);
+        for (uint32_t g = 0; g < G && valid; g++) {
+            const uint32_t rr = dr[32u * g];
+            const uint32_t x = 2 * (xh0 + g) + p;
+            const uint32_t xl = x == 0 ? L - 1 : x - 1, xr = x + 1 == L ? 0 : x + 1;
+            const size_t row = static_cast<size_t>(y) * L;
+            const int nn = sp[row + xl] + sp[row + xr] + sp[static_cast<size_t>(yu) * L + x] +
+                           sp[static_cast<size_t>(yd) * L + x];
+            const int si = sp[row + x];
+            if (accept_flip(2 * si * nn, rr, lat.T4, lat.T8)) sp[row + x] = static_cast<int8_t>(-si);
+        }
+    } else {
+        const uint32_t W = lat.W;
+        uint32_t *pc = static_cast<uint32_t *>(lat.spins) + static_cast<size_t>(c) * L * W;
+        const uint32_t *po = static_cast<const uint32_t *>(lat.spins) + static_cast<size_t>(1 - c) * L * W;
+        const uint32_t *o = po + static_cast<size_t>(y) * W;
+        const uint32_t *ou = po + static_cast<size_t>(yu) * W;
+        const uint32_t *od = po + static_cast<size_t>(yd) * W;
+        const uint32_t *own = pc + static_cast<size_t>(y) * W;
+        const int lane = threadIdx.x & 31;
+        const uint32_t lq0 = lane * G;
+        uint32_t c_lo = 0, c_hi = 0;
+        for (uint32_t g = 0; g < G && valid; g++) {
+            const uint32_t rr = dr[32u * g];
+            const uint32_t xh = xh0 + g;
+            const int nn = bit_spin(o, col_left(xh, p, half)) + bit_spin(o, col_right(xh, p, half)) + bit_spin(ou, xh) +
+                           bit_spin(od, xh);
+            const int si = bit_spin(own, xh);
+            if (accept_flip(2 * si * nn, rr, lat.T4, lat.T8)) {
+                const uint32_t lq = lq0 + g;
+                if ((lq >> 5) == (lq0 >> 5)) c_lo |= 1u << (lq & 31);
+                else c_hi |= 1u << (lq & 31);
+            }
+        }
+        // the warp's 32 G sites are G consecutive words of plane c
+        const uint64_t first_word = ((s & ~31ull) * G) >> 5;
+        const uint64_t words = static_cast<uint64_t>(L) * W;
+        for (uint32_t m = 0; m < G; m++) {
+            const uint32_t mine = ((lq0 >> 5) == m ? c_lo : 0u) | ((lq0 >> 5) + 1 == m ? c_hi : 0u);
+            const uint32_t word = __reduce_or_sync(0xffffffffu, mine);
+            if (lane == 0 && word && first_word + m < words) pc[first_word + m] ^= word;
+        }
+    }
+}
+
 }  // namespace
 }  // namespace rngx
 
@@ -207,6 +270,7 @@ struct IsingLat {
     uint64_t *pos_dev = nullptr; // device [1]
     int64_t *meas = nullptr;     // device [2 * meas_cap]
     uint64_t meas_cap = 0;
+    uint32_t *draws = nullptr;   // warp-shared generators: one half-sweep's numbers, 32 G per generator
 };
 
 // Persistent launch plan of one group of lattices of one generator kind.
@@ -271,7 +335,7 @@ int lat_create(IsingLat &t, uint32_t L, double beta, int layout, int kind, uint3
         set_error("Ising: G (sites per stream per colour) must divide L/2");
         return RNG_EINVAL;
     }
-    if (kind < RNG_LCG32 || kind >= kNumKinds || is_block_shared(kind)) {
+    if (kind < RNG_LCG32 || kind >= kNumKinds) {
         set_error("Ising: generator kind %d is not supported by the application test", kind);
         return RNG_EUNSUPPORTED;
     }
@@ -287,9 +351,14 @@ int lat_create(IsingLat &t, uint32_t L, double beta, int layout, int kind, uint3
     t.T4 = static_cast<uint64_t>(std::floor(4294967296.0 * std::exp(-beta * 4.0)));
     t.T8 = static_cast<uint64_t>(std::floor(4294967296.0 * std::exp(-beta * 8.0)));
     t.nstreams = static_cast<uint64_t>(L) * L / 2 / G;
-    const uint64_t n_inst = kind == RNG_XS1024W ? (t.nstreams + 31) / 32 * 32 : t.nstreams;
+    // the 1024-bit generator: a lane per stream, whole warps; the block-shared
+    // generators: one per 32 streams, feeding them in lane order
+    const uint64_t n_inst = kind == RNG_XS1024W ? (t.nstreams + 31) / 32 * 32
+                            : is_block_shared(kind) ? (t.nstreams + 31) / 32 : t.nstreams;
     RNGX_CHECK(rng_create(&t.rng, kind, n_inst, flags, s));
     RNGX_CHECK(rng_seed(t.rng, seed));
+    if (is_block_shared(kind))
+        RNGX_CHECK(dalloc(reinterpret_cast<void **>(&t.draws), n_inst * 32 * G * sizeof(uint32_t), s));
     t.spin_bytes = layout == ISING_INT8 ? static_cast<size_t>(L) * L : 2ull * L * t.W * 4;
     RNGX_CHECK(dalloc(&t.spins, t.spin_bytes, s));
     RNGX_CHECK(dalloc(reinterpret_cast<void **>(&t.acc), 8 * sizeof(int64_t), s));
@@ -316,6 +385,7 @@ void lat_free(IsingLat &t, cudaStream_t s)
     dfree(t.acc, s);
     dfree(t.pos_dev, s);
     dfree(t.meas, s);
+    dfree(t.draws, s);
     t = IsingLat();
 }
 
@@ -887,6 +957,13 @@ int ising_batch_create(ising_t *out, uint32_t n, const uint32_t *L, const double
     h->batch = true;
     h->master_seed = seed;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
+    for (uint32_t b = 0; b < n; b++)
+        if (is_block_shared(rng_kind[b])) {
+            delete h;
+            set_error("ising_batch_create: the block-shared generators (kind %d) sweep one lattice per handle",
+                      rng_kind[b]);
+            return RNG_EUNSUPPORTED;
+        }
     h->lats.resize(n);
     int st = RNG_OK;
     for (uint32_t b = 0; b < n && st == RNG_OK; b++) {
@@ -925,7 +1002,9 @@ int ising_sweep(ising_t h, uint64_t n_sweeps, uint32_t measure_every, void *cuda
     RNGX_CHECK(valid(h));
     if (n_sweeps == 0) return RNG_OK;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    if (h->plan_unfit) return ising_sweep_plain(h, n_sweeps, measure_every, cuda_stream);
+    // warp-shared generators stream their states each half-sweep: they run
+    // the per-half-sweep path
+    if (h->plan_unfit || is_block_shared(h->lats[0].kind)) return ising_sweep_plain(h, n_sweeps, measure_every, cuda_stream);
     if (!h->batch && !h->planned) {
         const int st = ensure_plan(h);
         if (st == RNG_EUNSUPPORTED) {
@@ -956,6 +1035,10 @@ int ising_sweep_multihit(ising_t h, uint64_t n_rounds, uint32_t k, uint32_t n_st
         return RNG_EUNSUPPORTED;
     }
     const IsingLat &t = h->lats[0];
+    if (is_block_shared(t.kind)) {
+        set_error("Ising multi-hit: not built for the block-shared generators (kind %d)", t.kind);
+        return RNG_EUNSUPPORTED;
+    }
     if (k == 0 || k > kMaxHits || n_strips < 2 || n_strips % 2 || t.L % n_strips) {
         set_error("Ising multi-hit: need 1 <= k <= %u and an even strip count >= 2 that divides L=%u (got k=%u, "
                   "n_strips=%u)",
@@ -995,8 +1078,19 @@ int ising_sweep_plain(ising_t h, uint64_t n_sweeps, uint32_t measure_every, void
     for (auto &t : h->lats) {
         LatDev d = lat_dev(t);
         const uint64_t n = t.layout == ISING_INT8 ? static_cast<uint64_t>(t.L) * t.L : static_cast<uint64_t>(t.L) * t.W;
+        const bool shared = is_block_shared(t.kind);
         for (uint64_t sw = 0; sw < n_sweeps; sw++) {
             for (int c = 0; c < 2; c++) {
+                if (shared) {
+                    // this half-sweep's 32 G words of every generator (the
+                    // generator advances its own position), then the sites
+                    RNGX_CHECK(rng_generate_u32(t.rng, t.draws, 32ull * t.G, RNG_INSTANCE_MAJOR, s));
+                    const unsigned nb = static_cast<unsigned>((t.nstreams + 255) / 256);
+                    if (t.layout == ISING_INT8) k_ising_half_given<ISING_INT8><<<nb, 256, 0, s>>>(d, c, t.draws);
+                    else k_ising_half_given<ISING_MULTISPIN32><<<nb, 256, 0, s>>>(d, c, t.draws);
+                    RNGX_CHECK_LAUNCH();
+                    continue;
+                }
                 d.rng.pos = t.rng->g.pos;
                 RNGX_CHECK(dispatch_half(t.kind, d, c, s));
                 t.rng->g.pos += t.G;
@@ -1140,6 +1234,13 @@ int ising_batch_sweep(ising_t h, uint64_t n_sweeps, uint32_t measure_every, void
 extern "C" int ising_autotune(ising_t h, uint32_t probe_sweeps, uint32_t *threads_out, int *ctas_per_sm_out)
 {
     RNGX_CHECK(valid(h));
+    if (!h->batch && is_block_shared(h->lats[0].kind)) {
+        // the per-half-sweep path of the block-shared generators has no
+        // persistent launch shape to tune
+        if (threads_out) *threads_out = 256;
+        if (ctas_per_sm_out) *ctas_per_sm_out = 0;
+        return RNG_OK;
+    }
     if (probe_sweeps == 0) probe_sweeps = 64;
     static const uint32_t kThreads[] = {256, 512, 1024};
     static const int kPerSm[] = {1, 2, 4};

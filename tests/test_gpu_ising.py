@@ -317,8 +317,8 @@ def test_argument_errors(R):
     for args in [(63, 0.4, 0), (66, 0.4, 1), (64, -1.0, 0), (2, 0.4, 0)]:
         with pytest.raises(R.RngError):
             R.ising_create(args[0], args[1], args[2], O.XORWOW, 0, 1, 2)
-    with pytest.raises(R.RngError) as e:
-        R.ising_create(64, 0.4, 0, O.MT19937_SHARED, 0, 1, 2)
+    with pytest.raises(R.RngError) as e:  # block-shared kinds: one lattice per handle
+        R.ising_batch_create([64, 32], [0.4, 0.4], [O.XORWOW, O.MT19937_SHARED], 1, 2)
     assert e.value.status == R.RNG_EUNSUPPORTED
     with pytest.raises(R.RngError):
         R.ising_create(64, 0.4, 0, O.XORWOW, 0, 1, 3)  # G does not divide L/2
