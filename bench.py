@@ -566,6 +566,25 @@ def ising_section(R, torch, args):
                     }
                 finally:
                     R.ising_destroy(h)
+    # the block-shared generators (MT19937, lagged Fibonacci; Table 1's
+    # Fibonacci rows): one generator per 32 streams, states streamed through
+    # L2 every half-sweep (the per-half-sweep path)
+    n_sh = max(20, n // 50)
+    for L in (1024, 64):
+        for layout, lname in ((R.ISING_INT8, "int8"), (R.ISING_MULTISPIN32, "multispin32")):
+            for kind in (R.RNG_MT19937_SHARED, R.RNG_LFIB521, R.RNG_LFIB1279):
+                if L == 64 and layout != R.ISING_INT8:
+                    continue
+                h = R.ising_create(L, BETA_C, layout, kind, 0, SEED, 2)
+                try:
+                    R.ising_sweep(h, 5)
+                    ms = _time_sweeps(R, torch, h, n_sh)
+                    out[f"L{L}/{lname}/{R.KIND_NAMES[kind]}"] = {
+                        "flips_per_ns": round(L * L * n_sh / (ms * 1e6), 3), "us_per_sweep": round(1e3 * ms / n_sh, 2),
+                        "sweeps_timed": n_sh, "path": "per half-sweep: generators write 32 G words each to an "
+                                                      "L2-resident buffer, one kernel consumes them"}
+                finally:
+                    R.ising_destroy(h)
     out["multihit"] = multihit_section(R, torch, n)
     if not args.no_cpu:
         out["cpu_oracle"] = ising_oracle_rate()
