@@ -316,6 +316,17 @@ int ising_plan_info(ising_t h, uint32_t *groups, uint32_t *blocks, uint32_t *str
  * undefined.  The device context stays usable. */
 int ising_debug_mute_strip(ising_t h, int32_t strip, uint64_t wait_budget_ns);
 
+/* Bounds-check build.  The library compiled with -DRNG_BOUNDS_CHECK (a
+ * separate shared object, see build.py) checks the shared- and
+ * global-memory indices of the generation kernels, the lagged Fibonacci
+ * kernels and the persistent Ising kernel: an index out of range is
+ * recorded and the access skipped, so that it becomes an error status
+ * instead of a memory fault.  This call synchronises the device and reports
+ * the first recorded access (*site = file code * 10000 + source line; 0:
+ * none), clearing the records when reset != 0.  A library built without
+ * the checks returns RNG_EUNSUPPORTED. */
+int rng_debug_bounds_status(int *site, int reset);
+
 /* Spins as int8 +-1, row-major y L + x (host_LxL holds L*L bytes). */
 int ising_get_spins(ising_t h, int8_t *host_LxL);
 int ising_set_spins(ising_t h, const int8_t *host_LxL);

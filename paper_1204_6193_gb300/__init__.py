@@ -13,7 +13,9 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "librng_gb300.so")
+# RNG_GB300_LIBRARY selects another build of the same library (the
+# bounds-check build of build.py, for tests)
+LIB_PATH = os.environ.get("RNG_GB300_LIBRARY") or os.path.join(_HERE, "_build", "librng_gb300.so")
 
 RNG_OK, RNG_EINVAL, RNG_ENOMEM, RNG_EUNSUPPORTED, RNG_ECUDA, RNG_ETIMEOUT, RNG_EBUSY = range(7)
 (RNG_LCG32, RNG_LCG64, RNG_MWC, RNG_XORWOW, RNG_PHILOX4X32_10, RNG_XS1024W,
@@ -76,6 +78,7 @@ _SIGS = {
     "ising_batch_observables": [_p, _u32, _p, _p, _p, _p],
     "ising_batch_get_spins": [_p, _u32, _p],
     "ising_debug_mute_strip": [_p, ctypes.c_int32, _u64],
+    "rng_debug_bounds_status": [ctypes.POINTER(_i32), _i32],
     "ising_plan_info": [_p, _p, _p, _p, _p],
     "rng_server_create": [_pp, _u32, _u32, _u32, _u64],
     "rng_server_submit": [_p, _p, ctypes.POINTER(_u64)],
@@ -409,6 +412,15 @@ def ising_batch_get_spins(h: int, idx: int):
 
 def ising_debug_mute_strip(h: int, strip: int, wait_budget_ns: int = 0) -> None:
     _call("ising_debug_mute_strip", h, strip, wait_budget_ns)
+
+
+def rng_debug_bounds_status(reset: bool = False) -> int:
+    """The first out-of-range access recorded by the bounds-check build
+    (file code * 10000 + line; 0: none).  Raises RngError with
+    RNG_EUNSUPPORTED on a library built without the checks."""
+    site = _i32()
+    _call("rng_debug_bounds_status", ctypes.byref(site), int(reset))
+    return site.value
 
 
 def ising_plan_info(h: int) -> dict:

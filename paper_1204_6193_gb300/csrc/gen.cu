@@ -58,14 +58,17 @@ __global__ void __launch_bounds__(kBlock) k_generate(DevParams p, void *out_, ui
                         for (int j = 0; j < 4; j++) facc += z[j];
                     } else if (active) {
 #pragma unroll
-                        for (int j = 0; j < 4; j++) st_stream(static_cast<float *>(out_) + (k + j) * n + i, z[j]);
+                        for (int j = 0; j < 4; j++)
+                            if (RNGX_IDX_OK((k + j) * n + i, n * K, kSiteGen + __LINE__))
+                                st_stream(static_cast<float *>(out_) + (k + j) * n + i, z[j]);
                     }
                 } else {
 #pragma unroll
                     for (int j = 0; j < 4; j++) {
                         const uint32_t bits = OUT == OUT_U32 ? o[j] : __float_as_uint(u32_to_unit(o[j]));
                         if (LAYOUT == RNG_XOR_REDUCE) xacc ^= bits;
-                        else if (active) __stcs(static_cast<uint32_t *>(out_) + (k + j) * n + i, bits);
+                        else if (active && RNGX_IDX_OK((k + j) * n + i, n * K, kSiteGen + __LINE__))
+                            __stcs(static_cast<uint32_t *>(out_) + (k + j) * n + i, bits);
                     }
                 }
             }
@@ -85,7 +88,7 @@ __global__ void __launch_bounds__(kBlock) k_generate(DevParams p, void *out_, ui
                 const uint32_t r0 = g.next(), r1 = g.next();
                 float z0, z1;
                 box_muller(r0, r1, z0, z1, bt);
-                if (active) {
+                if (active && RNGX_IDX_OK((k + 1) * n + i, n * K, kSiteGen + __LINE__)) {
                     st_stream(out + k * n + i, z0);
                     st_stream(out + (k + 1) * n + i, z1);
                 }
@@ -93,7 +96,7 @@ __global__ void __launch_bounds__(kBlock) k_generate(DevParams p, void *out_, ui
         } else {
             for (uint64_t k = 0; k < K; k++) {
                 const uint32_t r = g.next();
-                if (!active) continue;
+                if (!active || !RNGX_IDX_OK(k * n + i, n * K, kSiteGen + __LINE__)) continue;
                 if (OUT == OUT_U32) st_stream(static_cast<uint32_t *>(out_) + k * n + i, r);
                 else st_stream(static_cast<float *>(out_) + k * n + i, u32_to_unit(r));
             }
@@ -123,7 +126,8 @@ __global__ void __launch_bounds__(kBlock) k_generate(DevParams p, void *out_, ui
             if (lane < cnt) {
                 uint32_t *out = static_cast<uint32_t *>(out_);
                 for (int r = 0; r < 32; r++)
-                    if (i0 + r < n) __stcs(out + (i0 + r) * K + k0 + lane, tile[w][r][lane]);
+                    if (i0 + r < n && RNGX_IDX_OK((i0 + r) * K + k0 + lane, n * K, kSiteGen + __LINE__))
+                        __stcs(out + (i0 + r) * K + k0 + lane, tile[w][r][lane]);
             }
             __syncwarp();
         }
@@ -228,6 +232,7 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
     const uint64_t n = p.n;
     if (gidx >= n) return;  // whole warps only: no block-wide barriers below
     uint32_t *st = static_cast<uint32_t *>(p.s[0]) + gidx * MT_N;
+    const uint64_t n_out = LAYOUT == RNG_XOR_REDUCE ? n : n * K;  // words of the output
     uint32_t x[kMtRegs];
 #pragma unroll
     for (int j = 0; j < kMtRegs - 1; j++) x[j] = st[32 * j + lane];
@@ -257,7 +262,8 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
                     const uint32_t r = mt_temper_mul(x[j]);
                     const uint32_t bits = OUT == OUT_U32 ? r : __float_as_uint(u32_to_unit(r));
                     if (LAYOUT == RNG_XOR_REDUCE) xacc ^= bits;
-                    else __stcs(static_cast<uint32_t *>(out_) + out_index(kb + (wd - lo)), bits);
+                    else if (RNGX_IDX_OK(out_index(kb + (wd - lo)), n_out, kSiteGen + __LINE__))
+                        __stcs(static_cast<uint32_t *>(out_) + out_index(kb + (wd - lo)), bits);
                 }
             }
         } else {
@@ -268,7 +274,7 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
             for (int j = 0; j < kMtRegs; j++) {
                 const int wd = 32 * j + lane;
                 const bool in = FULLB ? (j < kMtRegs - 1 || wd < MT_N) : (wd >= lo && wd < hi);
-                if (in) tb[off + wd - lo] = mt_temper_mul(x[j]);
+                if (in && RNGX_IDX_OK(off + wd - lo, MT_N + 2, kSiteGen + __LINE__)) tb[off + wd - lo] = mt_temper_mul(x[j]);
             }
             __syncwarp();
             const int avail = off + hi - lo;
@@ -280,6 +286,8 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
                 if (LAYOUT == RNG_XOR_REDUCE) {
                     facc += z0;
                     facc += z1;
+                } else if (!RNGX_IDX_OK(out_index(d0 + 2 * t + 1), n_out, kSiteGen + __LINE__) ||
+                           !RNGX_IDX_OK(out_index(d0 + 2 * t), n_out, kSiteGen + __LINE__)) {
                 } else if (LAYOUT == RNG_INSTANCE_MAJOR && out_even) {
                     // gidx K + d0 + 2t is even (K and d0 even): one 8-byte store
                     __stcs(reinterpret_cast<float2 *>(static_cast<float *>(out_) + out_index(d0 + 2 * t)),
@@ -344,7 +352,8 @@ constexpr int kXsBlock = 64;
 // shared memory so that each 16-byte store instruction covers 512
 // consecutive bytes.
 __device__ __forceinline__ void xs_store_step(uint32_t (*tile)[33], const uint32_t (&v)[32], uint32_t *row,
-                                              uint64_t j0, uint64_t nstates, int lane)
+                                              uint64_t j0, uint64_t nstates, int lane, const uint32_t *row_base,
+                                              uint64_t row_len)
 {
 #pragma unroll
     for (int l = 0; l < 32; l++) tile[lane][l] = v[l];
@@ -353,7 +362,7 @@ __device__ __forceinline__ void xs_store_step(uint32_t (*tile)[33], const uint32
     for (int m = 0; m < 8; m++) {
         const int c = m * 32 + lane;  // 16-byte chunk of the warp's 4 KiB
         const int o = c >> 3, wo = (c & 7) * 4;
-        if (j0 + o < nstates)
+        if (j0 + o < nstates && RNGX_IDX_OK(static_cast<uint64_t>(row + 32 * j0 + 4 * c + 3 - row_base), row_len, kSiteGen + __LINE__))
             __stcs(reinterpret_cast<uint4 *>(row + 32 * j0) + c,
                    make_uint4(tile[o][wo], tile[o][wo + 1], tile[o][wo + 2], tile[o][wo + 3]));
     }
@@ -436,7 +445,7 @@ __global__ void __launch_bounds__(kXsBlock) k_generate_xs_reg(DevParams p, void 
                 }
             }
         }
-        if (active) {
+        if (active && RNGX_IDX_OK(32 * j + 31, n, kSiteGen + __LINE__)) {
             uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(out_) + 32 * j);
 #pragma unroll
             for (int m = 0; m < 8; m++) {
@@ -469,8 +478,8 @@ __global__ void __launch_bounds__(kXsBlock) k_generate_xs_reg(DevParams p, void 
                     a[l] = __float_as_uint(z0);
                     z1b[l] = __float_as_uint(z1);
                 }
-                xs_store_step(tile, a, out + k * n, j0, nstates, lane);
-                xs_store_step(tile, z1b, out + (k + 1) * n, j0, nstates, lane);
+                xs_store_step(tile, a, out + k * n, j0, nstates, lane, out, n * K);
+                xs_store_step(tile, z1b, out + (k + 1) * n, j0, nstates, lane, out, n * K);
             }
         } else {
             for (uint64_t k = 0; k < K; k++) {
@@ -482,7 +491,7 @@ __global__ void __launch_bounds__(kXsBlock) k_generate_xs_reg(DevParams p, void 
                     const uint32_t r = x[l] + yy;
                     v[l] = OUT == OUT_U32 ? r : __float_as_uint(u32_to_unit(r));
                 }
-                xs_store_step(tile, v, out + k * n, j0, nstates, lane);
+                xs_store_step(tile, v, out + k * n, j0, nstates, lane, out, n * K);
             }
         }
     }
@@ -580,6 +589,7 @@ __global__ void k_u32_to_normal(const uint32_t *in, float *out, uint64_t n_pairs
             reinterpret_cast<float4 *>(out)[q] = z;
         } else {
             float z0, z1;
+            if (!RNGX_IDX_OK(4 * q + 1, 2 * n_pairs, kSiteGen + __LINE__)) continue;
             box_muller(in[4 * q], in[4 * q + 1], z0, z1, bt);
             out[4 * q] = z0;
             out[4 * q + 1] = z1;
@@ -587,6 +597,8 @@ __global__ void k_u32_to_normal(const uint32_t *in, float *out, uint64_t n_pairs
     }
 }
 }  // namespace
+
+RNGX_BOUNDS_MODULE(gen)
 
 int launch_u32_to_normal(const uint32_t *in, float *out, uint64_t n_pairs, cudaStream_t s)
 {

@@ -114,4 +114,17 @@ int xs_substream_matrices(int levels, const uint32_t **d_P, cudaStream_t s);  //
 struct DevParams;
 int launch_matrix_apply(int kind, const DevParams &p, const uint32_t *M, uint64_t t, cudaStream_t s);
 
+// Bounds-check build (bounds.cuh): each module's first recorded site.
+#define RNGX_BOUNDS_READER(name) int bounds_site_##name(int *site, bool reset);
+RNGX_BOUNDS_READER(gen)
+RNGX_BOUNDS_READER(lfib)
+RNGX_BOUNDS_READER(persist_RNG_LCG32)
+RNGX_BOUNDS_READER(persist_RNG_LCG64)
+RNGX_BOUNDS_READER(persist_RNG_MWC)
+RNGX_BOUNDS_READER(persist_RNG_XORWOW)
+RNGX_BOUNDS_READER(persist_RNG_PHILOX4X32_10)
+RNGX_BOUNDS_READER(persist_RNG_PHILOX4X32_7)
+RNGX_BOUNDS_READER(persist_RNG_XS1024W)
+#undef RNGX_BOUNDS_READER
+
 }  // namespace rngx

@@ -815,6 +815,7 @@ int enqueue_persistent(ising_t h, std::vector<Plan> &plans, uint64_t n_units, ui
             a.cta_seg = P.d_cta;
             a.halo = P.d_halo;
             a.halo_row_bytes = P.halo_row_bytes;
+            a.halo_bytes = P.halo_bytes();
             a.err = h->d_err;
             a.n_sweeps = chunk;
             a.measure_every = measure_every;

@@ -133,6 +133,7 @@ int launch_persist(int layout, int smax, const PersistArgs &a, unsigned nblocks,
 #define RNGX_ISING_INSTANTIATE(KIND)                                                                          \
     template int launch_half<KIND>(const LatDev &, int, cudaStream_t);                                        \
     template int launch_persist<KIND>(int, int, const PersistArgs &, unsigned, unsigned, size_t, cudaStream_t, \
-                                      int *);
+                                      int *);                                                                 \
+    RNGX_BOUNDS_MODULE(persist_##KIND)
 
 }  // namespace rngx

@@ -28,6 +28,7 @@ struct PersistArgs {
     const uint32_t *cta_seg;   // segments of block b: [cta_seg[b], cta_seg[b+1])
     uint8_t *halo;             // per segment: 2 slots x 2 rows (first, last) x 2 colours x halo_row_bytes
     uint32_t halo_row_bytes;
+    uint64_t halo_bytes;       // size of the halo buffer (bounds-check build)
     int *err;
     uint64_t n_sweeps;
     uint64_t sweep0;           // sweeps of the same call before this launch
@@ -76,7 +77,10 @@ __device__ void load_segment(uint8_t *smem, const SegLocal &S, const void *spins
             const uint32_t x = idx % S.L;
             const uint32_t y = (S.y0 + S.L + r) % S.L;
             const int c = (x + y) & 1;
-            reinterpret_cast<int8_t *>(plane_row<LAYOUT>(smem, S, c, r))[x >> 1] = g[static_cast<size_t>(y) * S.L + x];
+            int8_t *dst = reinterpret_cast<int8_t *>(plane_row<LAYOUT>(smem, S, c, r)) + (x >> 1);
+            if (RNGX_IDX_OK(static_cast<size_t>(y) * S.L + x, static_cast<uint64_t>(S.L) * S.L, kSitePersist + __LINE__) &&
+                RNGX_SMEM_OK(dst, smem, 1, kSitePersist + __LINE__))
+                *dst = g[static_cast<size_t>(y) * S.L + x];
         }
     } else {
         const uint32_t *g = static_cast<const uint32_t *>(spins);
@@ -87,8 +91,10 @@ __device__ void load_segment(uint8_t *smem, const SegLocal &S, const void *spins
             const int r = static_cast<int>(rem / S.W) - 1;
             const uint32_t w = rem % S.W;
             const uint32_t y = (S.y0 + S.L + r) % S.L;
-            reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, S, c, r))[w] =
-                g[static_cast<size_t>(c) * S.L * S.W + static_cast<size_t>(y) * S.W + w];
+            uint32_t *dst = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, S, c, r)) + w;
+            const size_t gi = static_cast<size_t>(c) * S.L * S.W + static_cast<size_t>(y) * S.W + w;
+            if (RNGX_IDX_OK(gi, 2ull * S.L * S.W, kSitePersist + __LINE__) && RNGX_SMEM_OK(dst, smem, 4, kSitePersist + __LINE__))
+                *dst = g[gi];
         }
     }
 }
@@ -104,7 +110,10 @@ __device__ void store_segment(uint8_t *smem, const SegLocal &S, void *spins)
             const uint32_t x = idx % S.L;
             const uint32_t y = S.y0 + r;
             const int c = (x + y) & 1;
-            g[static_cast<size_t>(y) * S.L + x] = reinterpret_cast<int8_t *>(plane_row<LAYOUT>(smem, S, c, r))[x >> 1];
+            const int8_t *src = reinterpret_cast<int8_t *>(plane_row<LAYOUT>(smem, S, c, r)) + (x >> 1);
+            if (RNGX_IDX_OK(static_cast<size_t>(y) * S.L + x, static_cast<uint64_t>(S.L) * S.L, kSitePersist + __LINE__) &&
+                RNGX_SMEM_OK(src, smem, 1, kSitePersist + __LINE__))
+                g[static_cast<size_t>(y) * S.L + x] = *src;
         }
     } else {
         uint32_t *g = static_cast<uint32_t *>(spins);
@@ -114,8 +123,10 @@ __device__ void store_segment(uint8_t *smem, const SegLocal &S, void *spins)
             const uint32_t rem = idx % (S.R * S.W);
             const int r = static_cast<int>(rem / S.W);
             const uint32_t w = rem % S.W;
-            g[static_cast<size_t>(c) * S.L * S.W + static_cast<size_t>(S.y0 + r) * S.W + w] =
-                reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, S, c, r))[w];
+            const uint32_t *src = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, S, c, r)) + w;
+            const size_t gi = static_cast<size_t>(c) * S.L * S.W + static_cast<size_t>(S.y0 + r) * S.W + w;
+            if (RNGX_IDX_OK(gi, 2ull * S.L * S.W, kSitePersist + __LINE__) && RNGX_SMEM_OK(src, smem, 4, kSitePersist + __LINE__))
+                g[gi] = *src;
         }
     }
 }
@@ -267,6 +278,16 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
             const int hf = static_cast<int>(half);
             const int dl = p ? 0 : ((sl.flags & SL_ROW_FIRST) ? hf - 1 : -1);
             const int dr = p ? ((sl.flags & SL_ROW_LAST) ? 2 - hf : 2) : 1;
+            if (!RNGX_SMEM_OK(ow, smem, 2, kSitePersist + __LINE__) || !RNGX_SMEM_OK(ox + dl, smem, 1, kSitePersist + __LINE__) ||
+                !RNGX_SMEM_OK(ox + dr, smem, 1, kSitePersist + __LINE__) ||
+                !RNGX_SMEM_OK(ox - hf, smem, 2, kSitePersist + __LINE__) || !RNGX_SMEM_OK(ox + hf, smem, 2, kSitePersist + __LINE__))
+                return;
+            if constexpr (DUP) {
+                if ((sl.flags & (SL_DUP_DOWN | SL_DUP_UP)) &&
+                    !RNGX_SMEM_OK(ow + static_cast<int>(sg.R * half) * ((sl.flags & SL_DUP_DOWN) ? 1 : -1), smem, 2,
+                                  kSitePersist + __LINE__))
+                    return;
+            }
             const int mid = ox[p];
             const int s0 = ow[0], s1 = ow[1];
             const int a0 = s0 * (ox[dl] + mid + ox[-hf] + ox[hf]);
@@ -290,6 +311,9 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
             const uint32_t rr = gen.next();
             if (!sl.val()) continue;
             const uint32_t xh = sl.xh0 + g;
+            if (!RNGX_IDX_OK(xh, half, kSitePersist + __LINE__) || !RNGX_SMEM_OK(ou + xh, smem, 1, kSitePersist + __LINE__) ||
+                !RNGX_SMEM_OK(od + xh, smem, 1, kSitePersist + __LINE__) || !RNGX_SMEM_OK(own + xh, smem, 1, kSitePersist + __LINE__))
+                continue;
             const int nn = o[col_left(xh, p, half)] + o[col_right(xh, p, half)] + ou[xh] + od[xh];
             const int sp = own[xh];
             if (accept_a(sp * nn, rr, T4, T8)) {
@@ -314,7 +338,10 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
             // word, its row neighbours (shifted by one site) and the words
             // above and below
             const uint32_t r0 = gen.next(), r1 = gen.next();
-            if (sl.val()) {
+            if (sl.val() && RNGX_IDX_OK(sl.xh0 >> 5, W, kSitePersist + __LINE__) &&
+                RNGX_SMEM_OK(ou + (sl.xh0 >> 5), smem, 4, kSitePersist + __LINE__) &&
+                RNGX_SMEM_OK(od + (sl.xh0 >> 5), smem, 4, kSitePersist + __LINE__) &&
+                RNGX_SMEM_OK(own + (sl.xh0 >> 5), smem, 4, kSitePersist + __LINE__)) {
                 const uint32_t wi = sl.xh0 >> 5, b0 = sl.xh0 & 31u;
                 const uint32_t ow = own[wi], mw = o[wi];
                 const uint32_t n2 = p ? (mw >> 1) | (o[wi + 1 == W ? 0 : wi + 1] << 31)
@@ -355,7 +382,8 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
         for (uint32_t m = 0; m < G; m++) {
             const uint32_t mine = ((lq0 >> 5) == m ? c_lo : 0u) | ((lq0 >> 5) + 1 == m ? c_hi : 0u);
             const uint32_t word = __reduce_or_sync(0xffffffffu, mine);
-            if (lane == 0 && word && wbase + m < own_words) {
+            if (lane == 0 && word && wbase + m < own_words &&
+                RNGX_SMEM_OK(plane_c + wbase + m, smem, 4, kSitePersist + __LINE__)) {
                 plane_c[wbase + m] ^= word;
                 if constexpr (DUP) {  // the halo copies of the whole lattice's edge rows
                     if (wbase + m < W) plane_c[wbase + m + own_words] ^= word;
@@ -464,7 +492,12 @@ __device__ __forceinline__ void publish_rows(uint8_t *smem, const SegLocal &sg, 
     const uint32_t *rowl = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, c, sg.R - 1));
     uint64_t *d0 = halo_row(a, sg.gid, slot, 0, c), *d1 = halo_row(a, sg.gid, slot, 1, c);
     const uint64_t t = static_cast<uint64_t>(tag) << 32;
+    const uint64_t *hb = reinterpret_cast<const uint64_t *>(a.halo);
     for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) {
+        if (!RNGX_IDX_OK(d0 + i - hb, a.halo_bytes / 8, kSitePersist + __LINE__) ||
+            !RNGX_IDX_OK(d1 + i - hb, a.halo_bytes / 8, kSitePersist + __LINE__) ||
+            !RNGX_SMEM_OK(row0 + i, smem, 4, kSitePersist + __LINE__) || !RNGX_SMEM_OK(rowl + i, smem, 4, kSitePersist + __LINE__))
+            continue;
         st_relaxed_u64(d0 + i, t | row0[i]);
         st_relaxed_u64(d1 + i, t | rowl[i]);
     }
@@ -482,8 +515,14 @@ __device__ __forceinline__ bool poll_rows(uint8_t *smem, const SegLocal &sg, con
     const uint64_t *up_last = halo_row(a, sg.up, slot, 1, c), *dn_first = halo_row(a, sg.down, slot, 0, c);
     uint32_t *top = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, -1));
     uint32_t *bot = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, sg.R));
+    const uint64_t *hb = reinterpret_cast<const uint64_t *>(a.halo);
     for (uint32_t i = threadIdx.x; i < 2 * words; i += blockDim.x) {
         const uint64_t *src = i < words ? up_last + i : dn_first + (i - words);
+        // an index outside the halo buffer or the halo rows is recorded
+        // and skipped, never waited on
+        if (!RNGX_IDX_OK(src - hb, a.halo_bytes / 8, kSitePersist + __LINE__) ||
+            !RNGX_SMEM_OK(i < words ? top + i : bot + (i - words), smem, 4, kSitePersist + __LINE__))
+            continue;
         uint64_t v;
         uint32_t spins = 0;
         while (((v = ld_relaxed_u64(src)) >> 32) != tag) {

@@ -93,12 +93,16 @@ __global__ void __launch_bounds__(Lfib<R, S>::kBlock) k_generate_lfib(DevParams 
             a = a >= RS ? a - RS : a;
             b = b >= RS ? b - RS : b;
             c = c >= RS ? c - RS : c;
+            if (!RNGX_IDX_OK(a, RS, kSiteLfib + __LINE__) || !RNGX_IDX_OK(b, RS, kSiteLfib + __LINE__) ||
+                !RNGX_IDX_OK(c, RS, kSiteLfib + __LINE__))
+                continue;
             const uint32_t v = ring[a] + ring[b];
             ring[c] = v;
             if (OUT != OUT_NORMAL) {
                 const uint32_t bits = OUT == OUT_U32 ? v : __float_as_uint(u32_to_unit(v));
                 if (LAYOUT == RNG_XOR_REDUCE) xacc ^= bits;
-                else __stcs(static_cast<uint32_t *>(out_) + out_index(k + j), bits);
+                else if (RNGX_IDX_OK(out_index(k + j), n * K, kSiteLfib + __LINE__))
+                    __stcs(static_cast<uint32_t *>(out_) + out_index(k + j), bits);
             }
         }
         if (OUT == OUT_NORMAL) {
@@ -211,10 +215,14 @@ __global__ void __launch_bounds__(LfibChunked<R, S>::kBlock) k_generate_lfib_chu
     auto put = [&](uint64_t d, uint32_t v) {
         const uint32_t bits = OUT == OUT_U32 ? v : __float_as_uint(u32_to_unit(v));
         if (LAYOUT == RNG_XOR_REDUCE) xacc ^= bits;
-        else __stcs(static_cast<uint32_t *>(out_) + out_index(d), bits);
+        else if (RNGX_IDX_OK(out_index(d), n * K, kSiteLfib + __LINE__))
+            __stcs(static_cast<uint32_t *>(out_) + out_index(d), bits);
     };
     // normal pair t of the words just written at slots pc.. (call index k..)
     auto put_pair = [&](uint32_t pc, uint64_t k, int t) {
+        if (!RNGX_IDX_OK(pc + 2 * t + 1, F::kBuf, kSiteLfib + __LINE__) ||
+            (LAYOUT != RNG_XOR_REDUCE && !RNGX_IDX_OK(out_index(k + 2 * t + 1), n * K, kSiteLfib + __LINE__)))
+            return;
         const uint2 pr = *reinterpret_cast<const uint2 *>(ring + pc + 2 * t);
         float z0, z1;
         box_muller(pr.x, pr.y, z0, z1, bt);
@@ -236,6 +244,12 @@ __global__ void __launch_bounds__(LfibChunked<R, S>::kBlock) k_generate_lfib_chu
         if ((pc & (G - 1)) == 0 && K - k >= static_cast<uint64_t>(G)) {
             const uint32_t *ra = ring + ((pc + RS - R) & MASK) + lane;
             const uint32_t *rb = ring + ((pc + RS - S) & MASK) + lane;
+            // warp-uniform checks (the last lane's words): the whole warp leaves
+            // the loop together, before its next warp sync
+            if (!RNGX_IDX_OK(((pc + RS - R) & MASK) + 31 + 32 * (U - 1), F::kBuf, kSiteLfib + __LINE__) ||
+                !RNGX_IDX_OK(((pc + RS - S) & MASK) + 31 + 32 * (U - 1), F::kBuf, kSiteLfib + __LINE__) ||
+                !RNGX_IDX_OK(pc + 31 + 32 * (U - 1) + (pc == 0 ? RS : 0), F::kBuf, kSiteLfib + __LINE__))
+                break;
             uint32_t v[U];
 #pragma unroll
             for (int u = 0; u < U; u++) v[u] = ra[32 * u] + rb[32 * u];
@@ -259,6 +273,7 @@ __global__ void __launch_bounds__(LfibChunked<R, S>::kBlock) k_generate_lfib_chu
             k += G;
         } else {  // one chunk: aligning the slot to a group, or the tail
             const int cnt = K - k < 32 ? static_cast<int>(K - k) : 32;
+            if (!RNGX_IDX_OK(pc + 31 + (pc < G ? RS : 0), F::kBuf, kSiteLfib + __LINE__)) break;
             const uint32_t v = ring[((pc + RS - R) & MASK) + lane] + ring[((pc + RS - S) & MASK) + lane];
             if (lane < cnt) {
                 ring[pc + lane] = v;
@@ -344,6 +359,8 @@ int launch_lags(const GenState &g, void *out, uint64_t K, int out_kind, int layo
 }
 
 }  // namespace
+
+RNGX_BOUNDS_MODULE(lfib)
 
 int launch_generate_lfib(const GenState &g, void *d_out, uint64_t K, int out_kind, int layout, cudaStream_t s)
 {

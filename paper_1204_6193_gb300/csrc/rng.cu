@@ -492,3 +492,36 @@ const char *rng_strerror(int status)
 const char *rng_last_error(void) { return t_err; }
 
 }  // extern "C"
+
+// See include/rng_gb300.h.
+extern "C" int rng_debug_bounds_status(int *site, int reset)
+{
+    using namespace rngx;
+    if (!site) {
+        set_error("rng_debug_bounds_status: null output");
+        return RNG_EINVAL;
+    }
+    *site = 0;
+#ifdef RNG_BOUNDS_CHECK
+    int (*readers[])(int *, bool) = {bounds_site_gen,
+                                     bounds_site_lfib,
+                                     bounds_site_persist_RNG_LCG32,
+                                     bounds_site_persist_RNG_LCG64,
+                                     bounds_site_persist_RNG_MWC,
+                                     bounds_site_persist_RNG_XORWOW,
+                                     bounds_site_persist_RNG_PHILOX4X32_10,
+                                     bounds_site_persist_RNG_PHILOX4X32_7,
+                                     bounds_site_persist_RNG_XS1024W};
+    RNGX_CHECK_CUDA(cudaDeviceSynchronize());
+    for (auto rd : readers) {
+        int v = 0;
+        RNGX_CHECK(rd(&v, reset != 0));
+        if (v && !*site) *site = v;
+    }
+    return RNG_OK;
+#else
+    (void)reset;
+    set_error("rng_debug_bounds_status: this library was built without RNG_BOUNDS_CHECK");
+    return RNG_EUNSUPPORTED;
+#endif
+}

@@ -53,3 +53,14 @@ def test_status_strings_without_gpu():
     import paper_1204_6193_gb300 as R
     assert R.rng_strerror(R.RNG_OK) == "ok"
     assert "invalid" in R.rng_strerror(R.RNG_EINVAL)
+
+
+def test_normal_build_reports_no_bounds_checks_without_gpu():
+    # the status query of the bounds-check build; the normal build has no
+    # checks and says so before touching a device
+    import paper_1204_6193_gb300 as R
+    if os.environ.get("RNG_GB300_LIBRARY"):
+        pytest.skip("another build of the library is loaded")
+    with pytest.raises(R.RngError) as e:
+        R.rng_debug_bounds_status()
+    assert e.value.status == R.RNG_EUNSUPPORTED
