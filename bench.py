@@ -759,6 +759,7 @@ def _serve_run(R, srv, reqs, rate):
     gaps = rng.exponential(1.0 / rate, len(reqs)) if rate else np.zeros(len(reqs))
     tickets = [None] * len(reqs)
     lat = [None] * len(reqs)
+    wait = [None] * len(reqs)
     ready = threading.Semaphore(0)
 
     def collector():
@@ -766,6 +767,7 @@ def _serve_run(R, srv, reqs, rate):
             ready.acquire()
             res = R.rng_server_wait(srv, tickets[i], 600.0)
             lat[i] = (res.t_done_ns - res.t_submit_ns) / 1e6
+            wait[i] = (res.t_start_ns - res.t_submit_ns) / 1e6
             R.rng_server_fetch(srv, tickets[i], None, 0)
 
     th = threading.Thread(target=collector)
@@ -782,6 +784,7 @@ def _serve_run(R, srv, reqs, rate):
         tickets[i] = R.rng_server_submit(srv, r)
         ready.release()
     th.join()
+    _serve_run.last_wait = wait
     return lat, time.perf_counter() - t0
 
 
@@ -824,24 +827,32 @@ def serve_section(R, torch, args):
         lat_cap, wall_cap = _serve_run(R, srv, reqs, None)  # closed loop: capacity
         cap = len(reqs) / wall_cap
         rates = {}
+        is_sweep = np.array([r.type == R.RNG_REQ_SWEEP for r in reqs])
         for f in (0.5, 0.8, 1.0):
             lat, wall = _serve_run(R, srv, reqs, f * cap)
+            lat_a, wait_a = np.array(lat), np.array(_serve_run.last_wait)
             rates[str(f)] = {"rate_req_s": round(f * cap, 1), "p50_ms": round(float(np.percentile(lat, 50)), 3),
                              "p99_ms": round(float(np.percentile(lat, 99)), 3),
-                             "gnum_s": round(numbers / wall / 1e9, 2)}
+                             "gnum_s": round(numbers / wall / 1e9, 2),
+                             "p99_draw_ms": round(float(np.percentile(lat_a[~is_sweep], 99)), 3),
+                             "p99_sweep_ms": round(float(np.percentile(lat_a[is_sweep], 99)), 3),
+                             "p99_queue_wait_ms": round(float(np.percentile(wait_a, 99)), 3)}
         stats = R.rng_server_stats(srv)
     finally:
         R.rng_server_destroy(srv)
     lat_p, wall_p = _plain_run(R, torch, reqs, n_set)
+    lat_pa = np.array(lat_p)
     return {"requests": len(reqs), "draw_numbers": numbers, "capacity_req_s": round(cap, 1),
             "capacity_gnum_s": round(numbers / wall_cap / 1e9, 2), "rates": rates,
             "plain_sequential": {"p50_ms": round(float(np.percentile(lat_p, 50)), 3),
                                  "p99_ms": round(float(np.percentile(lat_p, 99)), 3),
+                                 "p99_draw_ms": round(float(np.percentile(lat_pa[~is_sweep], 99)), 3),
+                                 "p99_sweep_ms": round(float(np.percentile(lat_pa[is_sweep], 99)), 3),
                                  "gnum_s": round(numbers / wall_p / 1e9, 2), "wall_s": round(wall_p, 2)},
             "speedup_vs_plain": round(wall_p / wall_cap, 2), "max_concurrent": stats["max_concurrent"],
             "workload": "80% draws (2^U(10,26) numbers, u32/f32/normal, 6 kinds, 64 seeds, offsets k 2^20), "
                         "20% sweeps (L in 64..1024, 10..1000 sweeps); 512 resident stream sets of 4096 "
-                        "instances; 8 draw slots + 1 sweep slot; latency = submit to GPU completion"}
+                        "instances; 8 draw slots + 4 sweep slots; latency = submit to GPU completion"}
 
 
 # ------------------------------------------------------------ CPU oracle arm

@@ -369,10 +369,14 @@ int ising_batch_get_spins(ising_t h, uint32_t idx, int8_t *host_LxL);
 /* A request loop with continuous batching (not in the paper): generator
  * states stay resident on the device as "stream sets", and requests that
  * arrive while others run are admitted as soon as a slot (one of n_slots
- * CUDA streams for draws, plus one for sweeps) and device memory (a byte
- * budget for outputs and lattices) are free, in arrival order; their GPU
- * work overlaps.  A host worker thread owns all of the server's CUDA calls;
- * submit, wait and fetch may be called from any host thread. */
+ * CUDA streams for draws, plus four for sweeps) and device memory (a byte
+ * budget for outputs and lattices) are free, in arrival order within each
+ * request type (a request waiting for a slot of its type holds back only
+ * later requests of that type); their GPU work overlaps.  The lattices of fetched sweep requests are kept (a few
+ * per slot, size and kind) and reset for the next request of that shape
+ * instead of being created again.  A host worker thread owns all of the
+ * server's CUDA calls; submit, wait and fetch may be called from any host
+ * thread. */
 typedef struct rng_server_s *rng_server_t;
 
 enum { RNG_REQ_DRAW = 0, RNG_REQ_SWEEP = 1 };

@@ -7,6 +7,7 @@
 #include <type_traits>
 
 #include "gen_device.cuh"
+#include "modarith.cuh"
 
 namespace rngx {
 namespace {
@@ -152,6 +153,94 @@ __global__ void __launch_bounds__(kBlock) k_generate(DevParams p, void *out_, ui
         }
     }
     if (active) g.store(p, i);
+}
+
+// ------------------------------------------------- long streams, few instances
+// Step-major output of a handle with too few instances to fill the GPU:
+// each instance's K draws are cut into ranges of Kc (a multiple of 4), one
+// thread per (instance, range).  Thread (i, c) jumps its copy of instance
+// i's state over c Kc draws -- Eq. (2) for the LCGs, v a^t mod (a 2^32 - 1)
+// for MWC, the counter for Philox -- and makes draws [c Kc, min(K, (c+1)
+// Kc)); the last range stores the state.  The draws are those of the
+// one-thread-per-instance kernel.
+template <int KIND>
+__device__ __forceinline__ void jump_draws(Gen<KIND> &g, const DevParams &p, uint64_t t)
+{
+    if constexpr (KIND == RNG_LCG32 || KIND == RNG_LCG64) {
+        uint64_t at, ct;
+        affine_pow(p.A, p.C, t, at, ct);
+        if constexpr (KIND == RNG_LCG32) g.x = static_cast<uint32_t>(at) * g.x + static_cast<uint32_t>(ct);
+        else g.x = at * g.x + ct;
+    } else if constexpr (KIND == RNG_MWC) {
+        const uint64_t mod = (static_cast<uint64_t>(g.a) << 32) - 1;
+        const Mont m = mont_setup(mod);
+        g.v = from_mont(mont_mul(to_mont(g.v, m), mont_pow(to_mont(g.a, m), t, m), m), m);
+    } else {
+        g.pos += t;  // Philox: the counter
+    }
+}
+
+template <int KIND, int OUT>
+__global__ void __launch_bounds__(kBlock) k_generate_split(DevParams p, void *out_, uint64_t K, uint64_t Kc)
+{
+    BmTables bt{};
+    if constexpr (OUT == OUT_NORMAL) bt = bm_stage();  // every thread, before any leaves
+    const uint64_t n = p.n;
+    const uint64_t i = static_cast<uint64_t>(blockIdx.x) * kBlock + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t k0 = blockIdx.y * Kc, k1 = k0 + Kc < K ? k0 + Kc : K;
+    Gen<KIND> g;
+    g.load(p, i);
+    jump_draws<KIND>(g, p, k0);
+    if constexpr (is_philox(KIND)) {
+        if ((g.pos & 3) == 0) {  // whole counter blocks: the round keys once
+            constexpr int RR = Gen<KIND>::kRounds;
+            const PhiloxKeys<RR> keys(g.k0, g.k1);
+            for (uint64_t k = k0; k < k1; k += 4) {
+                const uint64_t blk = (g.pos + (k - k0)) >> 2;
+                uint32_t o[4];
+                philox_keys<RR>(static_cast<uint32_t>(blk), static_cast<uint32_t>(blk >> 32), 0u, 0u, keys, o[0],
+                                o[1], o[2], o[3]);
+                if (OUT == OUT_NORMAL) {
+                    float z[4];
+                    box_muller(o[0], o[1], z[0], z[1], bt);
+                    box_muller(o[2], o[3], z[2], z[3], bt);
+#pragma unroll
+                    for (int j = 0; j < 4; j++)
+                        if (k + j < k1 && RNGX_IDX_OK((k + j) * n + i, n * K, kSiteGen + __LINE__))
+                            st_stream(static_cast<float *>(out_) + (k + j) * n + i, z[j]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        const uint32_t bits = OUT == OUT_U32 ? o[j] : __float_as_uint(u32_to_unit(o[j]));
+                        if (k + j < k1 && RNGX_IDX_OK((k + j) * n + i, n * K, kSiteGen + __LINE__))
+                            __stcs(static_cast<uint32_t *>(out_) + (k + j) * n + i, bits);
+                    }
+                }
+            }
+            return;  // Philox keeps no state beyond the handle's position
+        }
+    }
+    if (OUT == OUT_NORMAL) {
+        float *out = static_cast<float *>(out_);
+        for (uint64_t k = k0; k < k1; k += 2) {  // k0 and K are even
+            const uint32_t r0 = g.next(), r1 = g.next();
+            float z0, z1;
+            box_muller(r0, r1, z0, z1, bt);
+            if (RNGX_IDX_OK((k + 1) * n + i, n * K, kSiteGen + __LINE__)) {
+                st_stream(out + k * n + i, z0);
+                st_stream(out + (k + 1) * n + i, z1);
+            }
+        }
+    } else {
+        for (uint64_t k = k0; k < k1; k++) {
+            const uint32_t r = g.next();
+            if (!RNGX_IDX_OK(k * n + i, n * K, kSiteGen + __LINE__)) continue;
+            if (OUT == OUT_U32) st_stream(static_cast<uint32_t *>(out_) + k * n + i, r);
+            else st_stream(static_cast<float *>(out_) + k * n + i, u32_to_unit(r));
+        }
+    }
+    if (k1 == K) g.store(p, i);
 }
 
 // ------------------------------------------------------------- MT19937
@@ -518,6 +607,38 @@ inline bool xs_reg_normals(uint64_t n)
     return n / 32 >= 200ull * static_cast<uint64_t>(sms);
 }
 
+// SMs of the current device (0 if unknown).
+inline int device_sms()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return sms;
+}
+
+// Whether a step-major call of n instances x K draws takes the split form,
+// and its range length Kc: when the instances fill less than a quarter of
+// the device's thread slots (2048 per SM) and each range keeps at least 256
+// draws, the ranges bring the threads up to about the device's slots.
+inline bool split_draws(uint64_t n, uint64_t K, uint64_t *Kc)
+{
+    const uint64_t slots = static_cast<uint64_t>(device_sms()) * 2048;
+    if (slots == 0 || 4 * n >= slots || K < 512) return false;
+    uint64_t ranges = (slots + n - 1) / n;
+    ranges = ranges < K / 256 ? ranges : K / 256;
+    if (ranges < 2) return false;
+    uint64_t kc = (K + ranges - 1) / ranges;
+    kc = (kc + 3) & ~3ull;  // whole Philox blocks and normal pairs
+    if (kc >= K) return false;
+    *Kc = kc;
+    return true;
+}
+
+// The one-thread-per-state form of the 1024-bit generator needs states
+// enough to occupy the device (one thread each): at least 16 per SM.
+inline bool xs_reg_uniform(uint64_t n) { return n / 32 >= 16ull * static_cast<uint64_t>(device_sms()); }
+
 // Launches KERN with the Box-Muller tables' dynamic shared memory when it
 // makes normals.
 template <int OUT, auto KERN>
@@ -546,12 +667,28 @@ int launch_kind_out(const GenState &g, void *out, uint64_t K, int layout, cudaSt
         default: return launch_gen<OUT, k_generate_mt<OUT, RNG_XOR_REDUCE>>(grid, kMtBlock, s, p, out, K);
         }
     } else if (KIND == RNG_XS1024W && layout != RNG_INSTANCE_MAJOR &&
-               (reinterpret_cast<uintptr_t>(out) & 15) == 0 && (OUT != OUT_NORMAL || xs_reg_normals(g.n))) {
+               (reinterpret_cast<uintptr_t>(out) & 15) == 0 &&
+               (OUT != OUT_NORMAL ? xs_reg_uniform(g.n) : xs_reg_normals(g.n))) {
         const dim3 grid(static_cast<unsigned>((g.n / 32 + kXsBlock - 1) / kXsBlock));
         if (layout == RNG_STEP_MAJOR)
             return launch_gen<OUT, k_generate_xs_reg<OUT, RNG_STEP_MAJOR>>(grid, kXsBlock, s, p, out, K);
         return launch_gen<OUT, k_generate_xs_reg<OUT, RNG_XOR_REDUCE>>(grid, kXsBlock, s, p, out, K);
     } else {
+        if constexpr (KIND == RNG_LCG32 || KIND == RNG_LCG64 || KIND == RNG_MWC || is_philox(KIND)) {
+            uint64_t Kc = 0;
+            if (layout == RNG_STEP_MAJOR && split_draws(g.n, K, &Kc)) {
+                const dim3 grid(static_cast<unsigned>((g.n + kBlock - 1) / kBlock),
+                                static_cast<unsigned>((K + Kc - 1) / Kc));
+                size_t smem = 0;
+                if constexpr (OUT == OUT_NORMAL) {
+                    RNGX_CHECK_CUDA((bm_allow_smem<k_generate_split<KIND, OUT>>()));
+                    smem = kBmSmemBytes;
+                }
+                k_generate_split<KIND, OUT><<<grid, kBlock, smem, s>>>(p, out, K, Kc);
+                RNGX_CHECK_LAUNCH();
+                return RNG_OK;
+            }
+        }
         const dim3 grid(static_cast<unsigned>((g.n + kBlock - 1) / kBlock));
         switch (layout) {
         case RNG_STEP_MAJOR: return launch_gen<OUT, k_generate<KIND, OUT, RNG_STEP_MAJOR>>(grid, kBlock, s, p, out, K);

@@ -14,24 +14,6 @@ constexpr int kBlock = 256;
 
 inline unsigned blocks_for(uint64_t n) { return static_cast<unsigned>((n + kBlock - 1) / kBlock); }
 
-// Coefficients of t applications of x -> a x + c (mod 2^64): x_{n+t} =
-// a_t x_n + c_t (Sec. 2, Eq. (2)), by binary powering of the affine map.
-__device__ __forceinline__ void affine_pow(uint64_t a, uint64_t c, uint64_t t, uint64_t &at, uint64_t &ct)
-{
-    uint64_t ra = 1, rc = 0;
-    while (t) {
-        if (t & 1) {
-            rc = a * rc + c;
-            ra = a * ra;
-        }
-        c = a * c + c;
-        a = a * a;
-        t >>= 1;
-    }
-    at = ra;
-    ct = rc;
-}
-
 constexpr uint64_t kLcg32A = 1664525ull, kLcg32C = 1013904223ull;
 constexpr uint64_t kLcg64A = 2862933555777941757ull, kLcg64C = 1442695040888963407ull;
 

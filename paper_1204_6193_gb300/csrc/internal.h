@@ -114,6 +114,10 @@ int xs_substream_matrices(int levels, const uint32_t **d_P, cudaStream_t s);  //
 struct DevParams;
 int launch_matrix_apply(int kind, const DevParams &p, const uint32_t *M, uint64_t t, cudaStream_t s);
 
+// Single-lattice Ising handle back to its state after ising_create with
+// (beta, seed), keeping memory and plan (the server's lattice pool).
+int ising_reset_lattice(ising_t h, double beta, uint64_t seed);
+
 // Bounds-check build (bounds.cuh): each module's first recorded site.
 #define RNGX_BOUNDS_READER(name) int bounds_site_##name(int *site, bool reset);
 RNGX_BOUNDS_READER(gen)

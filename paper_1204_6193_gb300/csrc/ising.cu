@@ -308,6 +308,7 @@ struct ising_s {
     uint64_t wait_budget_ns = kWaitBudgetNs;
     uint64_t g_sweeps = 0;
     uint32_t g_meas = 0;
+    LatDev host_lat{};  // staging of an asynchronous parameter upload (ising_reset_lattice)
 };
 
 namespace {
@@ -918,6 +919,48 @@ int get_spins(ising_t h, uint32_t idx, int8_t *out)
 }
 
 }  // namespace
+
+namespace rngx {
+
+// Puts a single-lattice handle back in the state ising_create(L, beta,
+// layout, kind, flags, seed, G) leaves, keeping its memory and launch plan
+// (for the server's pool of lattices): new thresholds, reseeded streams,
+// initial spins, zeroed accumulators, all on the handle's stream.
+int ising_reset_lattice(ising_t h, double beta, uint64_t seed)
+{
+    RNGX_CHECK(valid(h));
+    if (h->lats.size() != 1 || !(beta >= 0.0) || !std::isfinite(beta)) {
+        set_error("ising_reset_lattice: one lattice per handle and a finite beta >= 0");
+        return RNG_EINVAL;
+    }
+    IsingLat &t = h->lats[0];
+    cudaStream_t s = h->stream;
+    t.beta = beta;
+    t.seed = seed;
+    t.T4 = static_cast<uint64_t>(std::floor(4294967296.0 * std::exp(-beta * 4.0)));
+    t.T8 = static_cast<uint64_t>(std::floor(4294967296.0 * std::exp(-beta * 8.0)));
+    RNGX_CHECK(rng_seed(t.rng, seed));
+    const uint64_t seed2 = seed ^ 0x5350494EULL;
+    if (t.layout == ISING_INT8) {
+        const uint64_t n = static_cast<uint64_t>(t.L) * t.L;
+        k_init_int8<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(static_cast<int8_t *>(t.spins), t.L, seed2);
+    } else {
+        const uint64_t n = 2ull * t.L * t.W;
+        k_init_ms<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(static_cast<uint32_t *>(t.spins), t.L, t.W,
+                                                                          seed2);
+    }
+    RNGX_CHECK_LAUNCH();
+    RNGX_CHECK_CUDA(cudaMemsetAsync(t.acc, 0, 8 * sizeof(int64_t), s));
+    RNGX_CHECK_CUDA(cudaMemsetAsync(t.pos_dev, 0, sizeof(uint64_t), s));
+    RNGX_CHECK_CUDA(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
+    // the device copy of the lattice's parameters (thresholds, generator
+    // position), staged from the handle so that the copy stays ordered
+    h->host_lat = lat_dev(t);
+    RNGX_CHECK_CUDA(cudaMemcpyAsync(h->d_lats, &h->host_lat, sizeof(LatDev), cudaMemcpyHostToDevice, s));
+    return RNG_OK;
+}
+
+}  // namespace rngx
 
 extern "C" {
 

@@ -22,6 +22,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -117,11 +118,18 @@ struct SetEntry {
     int in_use = 0;
 };
 
+// Sweep requests run on the last kSweepSlots slots.
+constexpr uint32_t kSweepSlots = 4;
+
 struct rng_server_s {
     uint32_t n_sets = 0, n_set_inst = 0, n_slots = 0;
     uint64_t budget = 0, in_use = 0;
     int device = 0;
-    std::vector<cudaStream_t> slots;          // draw slots; the last one runs sweeps
+    std::vector<cudaStream_t> slots;          // draw slots, then kSweepSlots sweep slots
+    // lattices of finished sweep requests, by (slot, L, kind), reset and
+    // reused instead of created again (a handle stays on the slot whose
+    // stream it was created on)
+    std::map<std::tuple<int, uint32_t, int>, std::vector<ising_t>> lattice_pool;
     std::vector<ServerReq *> slot_req;
     std::vector<std::vector<rng_t>> work;     // [slot][kind] working generator
     std::map<std::pair<int, uint64_t>, SetEntry *> sets;
@@ -236,7 +244,14 @@ int launch_sweep(rng_server_s *S, ServerReq *q)
 {
     cudaStream_t s = S->slots[q->slot];
     const rng_request_t &r = q->r;
-    RNGX_CHECK(ising_create(&q->ising, r.L, r.beta, ISING_INT8, r.kind, 0, r.seed, 2, s));
+    auto &pool = S->lattice_pool[std::make_tuple(q->slot, r.L, r.kind)];
+    if (!pool.empty()) {
+        q->ising = pool.back();
+        pool.pop_back();
+        RNGX_CHECK(ising_reset_lattice(q->ising, r.beta, r.seed));
+    } else {
+        RNGX_CHECK(ising_create(&q->ising, r.L, r.beta, ISING_INT8, r.kind, 0, r.seed, 2, s));
+    }
     return ising_sweep(q->ising, r.sweeps, 0, s);
 }
 
@@ -289,45 +304,51 @@ void worker_main(rng_server_s *S)
             progress = true;
         }
         if (progress) S->cv_done.notify_all();
-        // admit in arrival order while a slot and memory are free
-        while (!S->queue.empty()) {
-            ServerReq *q = S->queue.front();
-            const bool sweep = q->r.type == RNG_REQ_SWEEP;
-            int slot = -1;
-            if (sweep) {
-                if (!S->slot_req.back()) slot = static_cast<int>(S->slots.size()) - 1;
-            } else {
-                for (size_t i = 0; i + 1 < S->slots.size(); i++)
+        // admit while a slot and memory are free, in arrival order within
+        // each request type: a request that waits for a slot of its type (or
+        // for memory) holds back the later requests of its type only, so a
+        // sweep waiting for a sweep slot does not keep draws from idle draw
+        // slots, nor the other way round
+        for (int type = 0; type < 2; type++) {
+            const bool sweep = type == 1;
+            const size_t first_sweep = S->slots.size() - kSweepSlots;
+            while (true) {
+                auto it = S->queue.begin();
+                while (it != S->queue.end() && ((*it)->r.type == RNG_REQ_SWEEP) != sweep) ++it;
+                if (it == S->queue.end()) break;
+                ServerReq *q = *it;
+                int slot = -1;
+                for (size_t i = sweep ? first_sweep : 0; i < (sweep ? S->slots.size() : first_sweep); i++)
                     if (!S->slot_req[i]) {
                         slot = static_cast<int>(i);
                         break;
                     }
+                const uint64_t need = req_mem(S, q->r);
+                if (slot < 0 || S->in_use + need > S->budget) break;
+                S->queue.erase(it);
+                q->slot = slot;
+                q->state = 1;
+                q->res.t_start_ns = now_ns();
+                int st = RNG_OK;
+                q->out_bytes = out_bytes(S, q->r);
+                if (q->out_bytes) st = dalloc(&q->d_out, q->out_bytes, S->slots[slot]);
+                if (st == RNG_OK) {
+                    S->in_use += need;
+                    q->charged = need;
+                    st = sweep ? launch_sweep(S, q) : launch_draw(S, q);
+                }
+                if (st == RNG_OK && cudaEventRecord(q->ev, S->slots[slot]) != cudaSuccess) st = RNG_ECUDA;
+                if (st != RNG_OK) {
+                    finish(S, q, st);
+                    S->cv_done.notify_all();
+                    continue;
+                }
+                S->slot_req[slot] = q;
+                uint32_t busy = 0;
+                for (auto *x : S->slot_req) busy += x != nullptr;
+                if (busy > S->max_conc) S->max_conc = busy;
+                progress = true;
             }
-            const uint64_t need = req_mem(S, q->r);
-            if (slot < 0 || S->in_use + need > S->budget) break;
-            S->queue.pop_front();
-            q->slot = slot;
-            q->state = 1;
-            q->res.t_start_ns = now_ns();
-            int st = RNG_OK;
-            q->out_bytes = out_bytes(S, q->r);
-            if (q->out_bytes) st = dalloc(&q->d_out, q->out_bytes, S->slots[slot]);
-            if (st == RNG_OK) {
-                S->in_use += need;
-                q->charged = need;
-                st = sweep ? launch_sweep(S, q) : launch_draw(S, q);
-            }
-            if (st == RNG_OK && cudaEventRecord(q->ev, S->slots[slot]) != cudaSuccess) st = RNG_ECUDA;
-            if (st != RNG_OK) {
-                finish(S, q, st);
-                S->cv_done.notify_all();
-                continue;
-            }
-            S->slot_req[slot] = q;
-            uint32_t busy = 0;
-            for (auto *x : S->slot_req) busy += x != nullptr;
-            if (busy > S->max_conc) S->max_conc = busy;
-            progress = true;
         }
         bool any_running = false;
         for (auto *x : S->slot_req) any_running |= x != nullptr;
@@ -359,7 +380,12 @@ void release(rng_server_s *S, ServerReq *q)
 {
     cudaStream_t s = q->slot >= 0 ? S->slots[q->slot] : nullptr;
     if (q->d_out) dfree(q->d_out, s);
-    if (q->ising) ising_destroy(q->ising);
+    if (q->ising) {
+        // a finished lattice goes back to its slot's pool (a few per size)
+        auto &pool = S->lattice_pool[std::make_tuple(q->slot, q->r.L, q->r.kind)];
+        if (q->res.status == RNG_OK && pool.size() < 2) pool.push_back(q->ising);
+        else ising_destroy(q->ising);
+    }
     S->in_use -= q->charged;
     if (q->ev) cudaEventDestroy(q->ev);
     S->reqs.erase(q->ticket);
@@ -387,9 +413,9 @@ int rng_server_create(rng_server_t *out, uint32_t n_sets, uint32_t instances_per
     S->n_slots = n_slots;
     S->budget = mem_budget_bytes;
     int st = cudaGetDevice(&S->device) == cudaSuccess ? RNG_OK : RNG_ECUDA;
-    S->slots.resize(n_slots + 1, nullptr);
-    S->slot_req.resize(n_slots + 1, nullptr);
-    S->work.assign(n_slots + 1, std::vector<rng_t>(kNumKinds, nullptr));
+    S->slots.resize(n_slots + kSweepSlots, nullptr);
+    S->slot_req.resize(n_slots + kSweepSlots, nullptr);
+    S->work.assign(n_slots + kSweepSlots, std::vector<rng_t>(kNumKinds, nullptr));
     for (auto &s : S->slots)
         if (st == RNG_OK && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) st = RNG_ECUDA;
     if (st == RNG_OK) st = build_ladders(S, S->slots[0]);
@@ -552,6 +578,8 @@ int rng_server_destroy(rng_server_t S)
     for (auto &row : S->work)
         for (auto w : row)
             if (w) rng_destroy(w);
+    for (auto &kv : S->lattice_pool)
+        for (auto h : kv.second) ising_destroy(h);
     for (auto s : S->slots)
         if (s) {
             cudaStreamSynchronize(s);

@@ -594,3 +594,44 @@ def test_zero_sweeps_and_smallest_lattice(R, torch_cuda):
         assert obs["acc"] == acc.tolist() and obs["n_meas"] == nm
     finally:
         R.ising_destroy(h)
+
+
+# ------------------------------------------ long streams of few instances
+SPLIT_KINDS = [O.LCG32, O.LCG64, O.MWC, O.PHILOX4X32_10, O.PHILOX4X32_7]
+
+
+@pytest.mark.parametrize("kind", SPLIT_KINDS)
+@pytest.mark.parametrize("out", ["u32", "f32", "normal"])
+def test_split_form_for_long_streams_of_few_instances(R, torch_cuda, kind, out):
+    """Few instances and many draws: each instance's draws are cut into
+    ranges that threads make from jumped copies of its state.  Ragged range
+    lengths, a Philox position off a counter block (an odd first call),
+    and a second call that continues the streams."""
+    torch = torch_cuda
+    n, Ks = 1000, (6, 4098, 2050)  # the first call leaves Philox mid-block
+    got = run_gpu(R, torch, kind, n, Ks)  # u32 draws, whatever the form under test below
+    ref = O.generate(kind, SEED, n, sum(Ks))
+    pos = 0
+    for K, g in zip(Ks, got):
+        want = ref[:, pos:pos + K]
+        assert np.array_equal(g, want), (K, pos)
+        pos += K
+    if out == "u32":
+        return
+    # the f32 and normal forms of the split kernel, after an even first call
+    Ks = (2, 6146)
+    got = run_gpu(R, torch, kind, n, Ks, out=out)
+    ref = O.generate(kind, SEED, n, sum(Ks))[:, 2:]
+    if out == "f32":
+        assert np.array_equal(got[1], as_f32_oracle(ref))
+    else:
+        assert np.abs(got[1].astype(np.float64) - O.box_muller(ref.reshape(-1)).reshape(n, -1)).max() <= NORMAL_TOL
+
+
+@pytest.mark.parametrize("kind,flags", [(O.LCG32, O.SEED_LEAPFROG), (O.LCG64, O.SEED_LEAPFROG),
+                                        (O.MWC, O.MWC_SAME_A), (O.PHILOX4X32_7, O.PHILOX_INTRINSIC_KEY)])
+def test_split_form_other_seedings(R, torch_cuda, kind, flags):
+    torch = torch_cuda
+    n, K = 96, 8192
+    got = run_gpu(R, torch, kind, n, (K,), flags=flags)[0]
+    assert np.array_equal(got, O.generate(kind, SEED, n, K, flags=flags))

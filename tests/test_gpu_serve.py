@@ -133,3 +133,33 @@ def test_admission_by_memory_and_eviction(env):
             R.rng_server_submit(srv, draw_req(R, O.XORWOW, 1, 0, 63, R.RNG_OUT_NORMAL))
     finally:
         R.rng_server_destroy(srv)
+
+
+def test_reused_lattices_equal_fresh_ones(env):
+    """Sweep requests of one shape in a row: after the first ones are
+    fetched, their lattices are reset and reused (new seed, temperature,
+    initial spins and streams); each result equals the oracle's, and so does
+    a concurrent mix of such requests on the sweep slots."""
+    R, torch = env
+    srv = R.rng_server_create(4, N_SET, 2, 1 << 30)
+    try:
+        cases = [(O.XORWOW, 64, 0.30 + 0.02 * i, 500 + i, 7 + i) for i in range(6)] + \
+                [(O.XS1024W, 128, 0.44, 900 + i, 5) for i in range(4)]
+        # one at a time: every request after the first of its shape reuses a lattice
+        for kind, L, beta, seed, sweeps in cases:
+            t = R.rng_server_submit(srv, sweep_req(R, kind, seed, L, beta, sweeps))
+            res = R.rng_server_wait(srv, t, 60.0)
+            assert res.status == 0
+            spins = fetch(R, srv, t, res.bytes).view(np.int8).reshape(L, L)
+            ref, _, _ = O.ising_run(L, beta, kind, seed, sweeps)
+            assert np.array_equal(spins, ref), (kind, L, seed)
+            assert (res.E, res.M) == O.ising_energy(ref)
+        # all at once: every sweep slot busy, pooled lattices in use
+        tickets = [R.rng_server_submit(srv, sweep_req(R, k, s + 50, L, b, w)) for k, L, b, s, w in cases]
+        for (kind, L, beta, seed, sweeps), t in zip(cases, tickets):
+            res = R.rng_server_wait(srv, t, 60.0)
+            spins = fetch(R, srv, t, res.bytes).view(np.int8).reshape(L, L)
+            ref, _, _ = O.ising_run(L, beta, kind, seed + 50, sweeps)
+            assert np.array_equal(spins, ref), (kind, L, seed)
+    finally:
+        R.rng_server_destroy(srv)
