@@ -276,7 +276,8 @@ struct IsingLat {
 // Persistent launch plan of one group of lattices of one generator kind.
 struct Plan {
     int kind = 0, layout = 0, smax = 1;
-    int fixed_slots = 0;  // 1: each thread slot has a fixed role (kernel modes 2, 3); 2: whole lattices (mode 4)
+    int fixed_slots = 0;  // 1: each thread slot has a fixed role (kernel modes 2, 3); 2: whole lattices (mode 4);
+                          // 3: one strip per block, roles split by warp, a polling warp (mode 5)
     unsigned nblocks = 0, threads = 0;
     size_t smem = 0;
     uint32_t nsegs = 0, halo_row_bytes = 0;
@@ -479,16 +480,24 @@ int build_plan(ising_t h, int kind, int layout, const std::vector<uint32_t> &ids
     if (!h->batch && ids.size() == 1 && !h->cfg_threads && !h->cfg_ctas_per_sm && !h->cfg_min_sites) {
         // a single lattice without a tuned shape takes the shapes the
         // autotuner finds: one block with one stream per thread when its
-        // streams fit (no exchange at all), and two blocks of 512 threads
-        // with two resident streams each per SM when one block per SM would
-        // need more than 1024 streams (both always fit the device)
-        const uint64_t n = h->lats[ids[0]].nstreams;
+        // streams fit (no exchange at all); when one block per SM needs
+        // more than 1024 streams, one block of 1024 threads per SM whose
+        // last warp polls (kernel mode 5) if its strips fit that layout,
+        // else two blocks of 512 threads with two resident streams each per
+        // SM (all of these fit the device)
+        const IsingLat &t = h->lats[ids[0]];
+        const uint64_t n = t.nstreams;
         if (n <= 1024) {
             min_sites = static_cast<double>(total_sites);
             cfg_threads = static_cast<unsigned>(std::max<uint64_t>(32, (n + 31) / 32 * 32));
         } else if (n > static_cast<uint64_t>(sms) * 1024 && n <= static_cast<uint64_t>(sms) * 2048) {
-            per_sm = 2;
-            cfg_threads = 512;
+            const uint64_t spr = t.L / 2 / t.G, rmax = (t.L + sms - 1) / sms;
+            if (spr % 32 == 0 && 2 * spr <= 1024 - 32 && rmax * spr <= 2 * (1024 - 32) && t.L >= 2 * sms) {
+                cfg_threads = 1024;
+            } else {
+                per_sm = 2;
+                cfg_threads = 512;
+            }
         }
     }
     const uint64_t target_blocks = static_cast<uint64_t>(sms) * per_sm;
@@ -612,7 +621,23 @@ int materialize_plan(ising_t h, int kind, int layout, const std::vector<std::vec
     unsigned threads = cfg_threads ? cfg_threads : 256;
     while (!cfg_threads && threads < 1024 && (max_streams + threads - 1) / threads > 4) threads *= 2;
     uint64_t spt = std::min<uint64_t>(4, std::max<uint64_t>(1, (max_streams + threads - 1) / threads));
-    if (spt >= 2 && threads > 512) {  // multi-slot kernels are built for at most 512 threads
+    // exact checkerboard at 1024 threads: one strip per block with roles
+    // split by warp (kernel mode 5) when every block's strip fits: its
+    // first and last rows in slot 0 of the first threads, all its streams
+    // in two slots of the threads other than the polling last warp
+    bool split = !multihit && threads == 1024 && !blocks.empty();
+    for (size_t b = 0; b < blocks.size() && split; b++) {
+        if (blocks[b].size() != 1) {
+            split = false;
+            break;
+        }
+        const SegDev &d = segs[cta[b]];
+        const IsingLat &t = h->lats[d.lat];
+        const uint64_t spr = t.L / 2 / t.G, R = d.y1 - d.y0, nc = threads - 32;
+        if (d.up < 0 || R < 2 || spr % 32 || 2 * spr > nc || d.s1 - d.s0 != R * spr || R * spr > 2 * nc) split = false;
+    }
+    if (split) spt = 2;
+    if (spt >= 2 && threads > 512 && !split) {  // other multi-slot kernels are built for at most 512 threads
         threads = 512;
         spt = std::min<uint64_t>(4, (max_streams + threads - 1) / threads);
     }
@@ -659,6 +684,7 @@ int materialize_plan(ising_t h, int kind, int layout, const std::vector<std::vec
         }
     }
     P.fixed_slots = fixed && P.smax == 2 ? 1 : 0;
+    if (split) P.fixed_slots = 3;
     if (!multihit && P.smax == 1 && max_streams <= threads) {
         // every block one whole lattice whose streams fit one slot per thread
         bool whole = true;

@@ -87,13 +87,16 @@ int launch_persist_t(const PersistArgs &a, unsigned nblocks, unsigned threads, s
                      int *max_blocks)
 {
     // kernel modes: 0 exact, 1 multi-hit, 2 / 3 the same with fixed slot roles
-    // (SMAX = 2), 4 exact with one whole resident lattice per block (SMAX = 1)
+    // (SMAX = 2), 4 exact with one whole resident lattice per block (SMAX = 1),
+    // 5 exact with roles split by warp and a polling warp (SMAX = 2)
     const bool fixed = SMAX == 2 && a.fixed_slots == 1, whole = SMAX == 1 && a.fixed_slots == 2;
+    const bool split = SMAX == 2 && a.fixed_slots == 3 && !a.k_hits;
     auto kern = a.k_hits ? (fixed ? k_ising_persist<KIND, LAYOUT, SMAX, SMAX == 2 ? 2 : 1>
                                   : k_ising_persist<KIND, LAYOUT, SMAX, 1>)
                          : (fixed ? k_ising_persist<KIND, LAYOUT, SMAX, SMAX == 2 ? 3 : 0>
                                   : (whole ? k_ising_persist<KIND, LAYOUT, SMAX, SMAX == 1 ? 4 : 0>
-                                           : k_ising_persist<KIND, LAYOUT, SMAX, 0>));
+                                           : (split ? k_ising_persist<KIND, LAYOUT, SMAX, SMAX == 2 ? 5 : 0>
+                                                    : k_ising_persist<KIND, LAYOUT, SMAX, 0>)));
     RNGX_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     int per_sm = 0, dev = 0, sms = 0;
     RNGX_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));

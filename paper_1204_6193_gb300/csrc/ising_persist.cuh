@@ -36,7 +36,8 @@ struct PersistArgs {
     int32_t mute_seg;          // test hook: this segment never publishes (-1: none)
     uint64_t wait_budget_ns;   // limit of one neighbour wait
     uint32_t k_hits;           // 0: exact checkerboard; k > 0: multi-hit rounds of k sweeps per strip phase
-    uint32_t fixed_slots;      // 1: the plan fixes each slot's role (kernel modes 2, 3); 2: one whole lattice per block (mode 4)
+    uint32_t fixed_slots;      // 1: the plan fixes each slot's role (kernel modes 2, 3); 2: one whole lattice per block
+                               // (mode 4); 3: one strip per block of split roles with a polling warp (mode 5)
 };
 
 struct SegLocal {              // per-segment constants held in shared memory
@@ -269,17 +270,23 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
         const int8_t *o = reinterpret_cast<const int8_t *>(o_row);
         const int8_t *ou = o - half, *od = o + half;
         if (G == 2) {
-            // the two sites xh, xh + 1 (xh even) share their middle row
-            // neighbour; draws are taken in site order before either update
+            // the two sites xh, xh + 1 (xh even) as one 16-bit word, and so
+            // their neighbours above, below and in the row (xh and every row
+            // offset are even).  Per byte, (s ^ n) & 2 is 2 when n is
+            // anti-aligned with s (+1 = 0x01, -1 = 0xff), so one sum of four
+            // masked words gives 2k, k the anti-aligned neighbours, of both
+            // sites at once (2k <= 8: no carries); s_i sum_nn s_j = 4 - 2k.
+            // Draws are taken in site order before either update.
             const uint32_t r0 = gen.next(), r1 = gen.next();
             if (!sl.val()) return;
             const int8_t *ox = o + sl.xh0;
             int8_t *ow = own + sl.xh0;
             const int hf = static_cast<int>(half);
-            const int dl = p ? 0 : ((sl.flags & SL_ROW_FIRST) ? hf - 1 : -1);
-            const int dr = p ? ((sl.flags & SL_ROW_LAST) ? 2 - hf : 2) : 1;
-            if (!RNGX_SMEM_OK(ow, smem, 2, kSitePersist + __LINE__) || !RNGX_SMEM_OK(ox + dl, smem, 1, kSitePersist + __LINE__) ||
-                !RNGX_SMEM_OK(ox + dr, smem, 1, kSitePersist + __LINE__) ||
+            // the row neighbour outside the pair: left of xh (p = 0) or right
+            // of xh + 1 (p = 1), wrapped at the row's ends
+            const int eo = p ? ((sl.flags & SL_ROW_LAST) ? 2 - hf : 2) : ((sl.flags & SL_ROW_FIRST) ? hf - 1 : -1);
+            if (!RNGX_SMEM_OK(ow, smem, 2, kSitePersist + __LINE__) || !RNGX_SMEM_OK(ox, smem, 2, kSitePersist + __LINE__) ||
+                !RNGX_SMEM_OK(ox + eo, smem, 1, kSitePersist + __LINE__) ||
                 !RNGX_SMEM_OK(ox - hf, smem, 2, kSitePersist + __LINE__) || !RNGX_SMEM_OK(ox + hf, smem, 2, kSitePersist + __LINE__))
                 return;
             if constexpr (DUP) {
@@ -288,21 +295,31 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
                                   kSitePersist + __LINE__))
                     return;
             }
-            const int mid = ox[p];
-            const int s0 = ow[0], s1 = ow[1];
-            const int a0 = s0 * (ox[dl] + mid + ox[-hf] + ox[hf]);
-            const int a1 = s1 * (mid + ox[dr] + ox[1 - hf] + ox[1 + hf]);
-            // a <= 0 always flips (and every a where T = 2^32, beta = 0)
-            const int am = sg.a_max;
+            const uint32_t o2 = *reinterpret_cast<const uint16_t *>(ow);
+            const uint32_t m2 = *reinterpret_cast<const uint16_t *>(ox);
+            const uint32_t u2 = *reinterpret_cast<const uint16_t *>(ox - hf);
+            const uint32_t d2 = *reinterpret_cast<const uint16_t *>(ox + hf);
+            const uint32_t e = static_cast<uint8_t>(ox[eo]);
+            // row neighbours of (xh, xh + 1) in the (low, high) bytes:
+            // p = 0: (e, m.lo) and (m.lo, m.hi); p = 1: (m.lo, m.hi) and (m.hi, e)
+            const uint32_t na = p ? m2 : (((m2 << 8) | e) & 0xffffu);
+            const uint32_t nb = p ? ((m2 >> 8) | (e << 8)) : m2;
+            const uint32_t k2 = ((o2 ^ u2) & 0x0202u) + ((o2 ^ d2) & 0x0202u) + ((o2 ^ na) & 0x0202u) +
+                                ((o2 ^ nb) & 0x0202u);
+            const uint32_t k0 = k2 & 0xffu, k1 = k2 >> 8;
+            // flip when 4 - 2k <= a_max (every k >= 2, and every k where
+            // T = 2^32), else iff r < T(4 - 2k): T8 for k = 0, T4 for k = 1
+            const uint32_t kf = static_cast<uint32_t>(4 - sg.a_max);
             const uint32_t t4 = sg.t4, t8 = sg.t8;
-            const bool f0 = a0 <= am || r0 < (a0 == 2 ? t4 : t8), f1 = a1 <= am || r1 < (a1 == 2 ? t4 : t8);
-            if (f0) ow[0] = static_cast<int8_t>(-s0);
-            if (f1) ow[1] = static_cast<int8_t>(-s1);
-            if constexpr (DUP) {
-                if (sl.flags & (SL_DUP_DOWN | SL_DUP_UP)) {
-                    const int d = static_cast<int>(sg.R * half) * ((sl.flags & SL_DUP_DOWN) ? 1 : -1);
-                    if (f0) ow[d] = static_cast<int8_t>(-s0);
-                    if (f1) ow[d + 1] = static_cast<int8_t>(-s1);
+            const bool f0 = k0 >= kf || r0 < (k0 ? t4 : t8), f1 = k1 >= kf || r1 < (k1 ? t4 : t8);
+            if (f0 || f1) {
+                // -s = s ^ 0xfe for s = 0x01, 0xff
+                const uint16_t n2 = static_cast<uint16_t>(o2 ^ ((f0 ? 0x00feu : 0u) | (f1 ? 0xfe00u : 0u)));
+                *reinterpret_cast<uint16_t *>(ow) = n2;
+                if constexpr (DUP) {
+                    if (sl.flags & (SL_DUP_DOWN | SL_DUP_UP))
+                        *reinterpret_cast<uint16_t *>(ow + static_cast<int>(sg.R * half) *
+                                                                ((sl.flags & SL_DUP_DOWN) ? 1 : -1)) = n2;
                 }
             }
             return;
@@ -482,9 +499,10 @@ __device__ __forceinline__ uint64_t *halo_row(const PersistArgs &a, int gid, uin
 
 // Publishes the first and last rows of colour c of strip sg as 64-bit
 // (tag, 32 data bits) words: one relaxed atomic store each, no fence.
+// Threads tid = 0 .. nthr-1 share the stores.
 template <int LAYOUT>
-__device__ __forceinline__ void publish_rows(uint8_t *smem, const SegLocal &sg, const PersistArgs &a, uint32_t slot,
-                                             uint32_t tag, int c)
+__device__ __forceinline__ void publish_rows_by(uint8_t *smem, const SegLocal &sg, const PersistArgs &a, uint32_t slot,
+                                                uint32_t tag, int c, uint32_t tid, uint32_t nthr)
 {
     if (sg.gid == a.mute_seg) return;  // test hook: a strip that never publishes
     const uint32_t words = row_bytes<LAYOUT>(sg) / 4;
@@ -493,7 +511,7 @@ __device__ __forceinline__ void publish_rows(uint8_t *smem, const SegLocal &sg, 
     uint64_t *d0 = halo_row(a, sg.gid, slot, 0, c), *d1 = halo_row(a, sg.gid, slot, 1, c);
     const uint64_t t = static_cast<uint64_t>(tag) << 32;
     const uint64_t *hb = reinterpret_cast<const uint64_t *>(a.halo);
-    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) {
+    for (uint32_t i = tid; i < words; i += nthr) {
         if (!RNGX_IDX_OK(d0 + i - hb, a.halo_bytes / 8, kSitePersist + __LINE__) ||
             !RNGX_IDX_OK(d1 + i - hb, a.halo_bytes / 8, kSitePersist + __LINE__) ||
             !RNGX_SMEM_OK(row0 + i, smem, 4, kSitePersist + __LINE__) || !RNGX_SMEM_OK(rowl + i, smem, 4, kSitePersist + __LINE__))
@@ -501,6 +519,13 @@ __device__ __forceinline__ void publish_rows(uint8_t *smem, const SegLocal &sg, 
         st_relaxed_u64(d0 + i, t | row0[i]);
         st_relaxed_u64(d1 + i, t | rowl[i]);
     }
+}
+
+template <int LAYOUT>
+__device__ __forceinline__ void publish_rows(uint8_t *smem, const SegLocal &sg, const PersistArgs &a, uint32_t slot,
+                                             uint32_t tag, int c)
+{
+    publish_rows_by<LAYOUT>(smem, sg, a, slot, tag, c, threadIdx.x, blockDim.x);
 }
 
 // Polls the neighbours' rows of colour c into strip sg's halo rows (the up
@@ -544,6 +569,69 @@ __device__ __forceinline__ bool poll_rows(uint8_t *smem, const SegLocal &sg, con
     return true;
 }
 
+// The same poll by one warp (lane = its lane) that does nothing else while
+// the block's other warps update their rows: each lane keeps up to eight
+// independent loads in flight and re-reads only the words whose tag is not
+// there yet.  The wait is bounded like poll_rows', and ends early when
+// another block has recorded an error.
+template <int LAYOUT>
+__device__ __forceinline__ bool poll_rows_warp(uint8_t *smem, const SegLocal &sg, const PersistArgs &a, uint32_t slot,
+                                               uint32_t tag, int c, int lane)
+{
+    constexpr int K = 8;
+    const uint32_t words = row_bytes<LAYOUT>(sg) / 4, total = 2 * words;
+    const uint64_t *up_last = halo_row(a, sg.up, slot, 1, c), *dn_first = halo_row(a, sg.down, slot, 0, c);
+    uint32_t *top = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, -1));
+    uint32_t *bot = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, sg.R));
+    const uint64_t *hb = reinterpret_cast<const uint64_t *>(a.halo);
+    const uint64_t t0 = global_ns();
+    const long long c0 = clock64();
+    for (uint32_t base = 0; base < total; base += 32 * K) {
+        uint32_t pend = 0;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const uint32_t i = base + lane + 32 * k;
+            // an index outside the halo buffer or the halo rows is recorded
+            // and skipped, never waited on
+            if (i < total &&
+                RNGX_IDX_OK((i < words ? up_last + i : dn_first + (i - words)) - hb, a.halo_bytes / 8,
+                            kSitePersist + __LINE__) &&
+                RNGX_SMEM_OK(i < words ? top + i : bot + (i - words), smem, 4, kSitePersist + __LINE__))
+                pend |= 1u << k;
+        }
+        uint32_t spins = 0;
+        while (pend) {
+            uint64_t v[K];
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const uint32_t i = base + lane + 32 * k;
+                v[k] = ((pend >> k) & 1u) ? ld_relaxed_u64(i < words ? up_last + i : dn_first + (i - words)) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const uint32_t i = base + lane + 32 * k;
+                if (((pend >> k) & 1u) && (v[k] >> 32) == tag) {
+                    (i < words ? top[i] : bot[i - words]) = static_cast<uint32_t>(v[k]);
+                    pend &= ~(1u << k);
+                }
+            }
+            if (pend && (++spins & 7u) == 0 &&
+                (global_ns() - t0 > a.wait_budget_ns || static_cast<uint64_t>(clock64() - c0) > 4 * a.wait_budget_ns ||
+                 ld_acquire(reinterpret_cast<const uint32_t *>(a.err)) != 0)) {
+                atomicCAS(a.err, 0, RNG_ETIMEOUT);
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+// Barrier 1 among the first nthr threads of the block (a multiple of 32).
+__device__ __forceinline__ void bar_sync_first(uint32_t nthr)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
+}
+
 template <int LAYOUT>
 __device__ void measure_strips(uint8_t *smem, const SegLocal *S, uint32_t nseg, const PersistArgs &a,
                                uint64_t meas_idx, long long *red)
@@ -577,15 +665,22 @@ __device__ void measure_strips(uint8_t *smem, const SegLocal *S, uint32_t nseg, 
 //      between (the interior pass);
 //   4: (SMAX = 1 only) exact checkerboard, every block one whole lattice
 //      with resident states: a half-sweep is one pass and one barrier, the
-//      edge rows writing their flips into the halo rows as well.
+//      edge rows writing their flips into the halo rows as well;
+//   5: (SMAX = 2 only) exact checkerboard, one strip per block of roles
+//      split by warp: the warps of the first and last rows update them and
+//      publish them first, then all but the last warp update the rows
+//      between, and the last warp holds no stream: it polls the
+//      neighbours' rows for the whole half-sweep, so that their arrival
+//      overlaps the interior work (one block of 1024 threads per SM).
 // Launch bounds: the exact-checkerboard kernel runs multi-slot shapes with
-// at most 512 threads; the multi-hit kernel also runs two slots with up to
-// 1024 threads.
+// at most 512 threads, except mode 5; the multi-hit kernel also runs two
+// slots with up to 1024 threads.
 template <int KIND, int LAYOUT, int SMAX, int MODE>
-__global__ void __launch_bounds__(SMAX >= ((MODE == 1 || MODE == 2) ? 4 : 2) ? 512 : 1024,
+__global__ void __launch_bounds__(MODE == 5 ? 1024 : (SMAX >= ((MODE == 1 || MODE == 2) ? 4 : 2) ? 512 : 1024),
                                   ((MODE == 0 || MODE == 3 || MODE == 4) && SMAX == 2) ? 2 : 1)
     k_ising_persist(PersistArgs a)
 {
+    static_assert(MODE != 5 || SMAX == 2, "mode 5 holds two stream slots per thread");
     constexpr bool MH = MODE == 1 || MODE == 2;
     constexpr bool EXACT_LOOPS = MODE == 0 || MODE == 3;
     extern __shared__ __align__(16) uint8_t smem[];
@@ -664,6 +759,30 @@ __global__ void __launch_bounds__(SMAX >= ((MODE == 1 || MODE == 2) ? 4 : 2) ? 5
                 slot[k].seg = 0;
                 slot[k].s = static_cast<uint32_t>(sg.s0 + (in ? f : 0));
                 finish_slot<LAYOUT>(sg, in, in && slot[k].s < sg.n_valid, slot[k]);
+            } else if constexpr (MODE == 5) {
+                // compute threads t < nc = blockDim - 32.  Slot 0: rows 0
+                // and R-1 for t < 2 spr, then the first interior streams;
+                // slot 1: the remaining interior streams.  The last warp
+                // holds none.
+                const SegLocal &sg = S[0];
+                const uint32_t spr = sg.half / sg.G, t = threadIdx.x, nc = blockDim.x - 32;
+                const int64_t ni = sg.R >= 2 ? static_cast<int64_t>(sg.R - 2) * spr : 0;
+                bool in = false;
+                uint64_t f = 0;
+                if (t < nc) {
+                    if (k == 0 && t < 2 * spr) {
+                        in = true;
+                        f = t < spr ? t : static_cast<uint64_t>(sg.R - 1) * spr + (t - spr);
+                    } else {
+                        const int64_t i = k == 0 ? static_cast<int64_t>(t) - 2 * static_cast<int64_t>(spr)
+                                                 : static_cast<int64_t>(nc) - 2 * static_cast<int64_t>(spr) + t;
+                        in = i >= 0 && i < ni;
+                        f = in ? spr + static_cast<uint64_t>(i) : 0;
+                    }
+                }
+                slot[k].seg = 0;
+                slot[k].s = static_cast<uint32_t>(sg.s0 + (in ? f : 0));
+                finish_slot<LAYOUT>(sg, in, in && slot[k].s < sg.n_valid, slot[k]);
             } else {
                 setup_slot<LAYOUT>(S, nseg, prefix_end, threadIdx.x + static_cast<uint64_t>(k) * blockDim.x, slot[k]);
             }
@@ -702,6 +821,47 @@ __global__ void __launch_bounds__(SMAX >= ((MODE == 1 || MODE == 2) ? 4 : 2) ? 5
         if (!__syncthreads_and(ok)) {
             if (threadIdx.x == 0) atomicCAS(a.err, 0, RNG_EINVAL);
             goto done;
+        }
+    }
+    if constexpr (MODE == 5) {
+        // the host chose this kernel for one strip per block whose first and
+        // last rows fill slot 0 of the first 2 spr threads and whose rows
+        // between fit the rest of the compute threads' two slots
+        const SegLocal &sg = S[0];
+        const uint32_t spr = sg.half / sg.G, nc = blockDim.x - 32;
+        const bool ok = resident && nseg == 1 && sg.up >= 0 && sg.R >= 2 && spr % 32 == 0 && blockDim.x % 32 == 0 &&
+                        blockDim.x >= 64 && 2 * spr <= nc && prefix_end == static_cast<uint64_t>(sg.R) * spr &&
+                        prefix_end <= 2ull * nc;
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) atomicCAS(a.err, 0, RNG_EINVAL);
+            goto done;
+        }
+        const bool poller = threadIdx.x >= nc;
+        const bool bnd = threadIdx.x < 2 * spr;  // warp-uniform: 2 spr is a multiple of 32
+        for (uint64_t t = 0; t < a.n_sweeps; t++) {
+            for (int c = 0; c < 2; c++) {
+                const uint32_t h = static_cast<uint32_t>(2 * t + c);
+                if (poller) {
+                    // the neighbours' rows of colour c go to the halo rows of
+                    // plane c, which no update of colour c reads
+                    if (!poll_rows_warp<LAYOUT>(smem, sg, a, h & 1, h + 1, c, lane)) s_abort = 1;
+                } else {
+                    // the strip's first and last rows first, then published;
+                    // the other compute warps wait, so that these rows are
+                    // ready as early as possible
+                    if (bnd) update_slot<KIND, LAYOUT>(smem, sg, slot[0], gen[0], c, lane);
+                    bar_sync_first(nc);
+                    publish_rows_by<LAYOUT>(smem, sg, a, h & 1, h + 1, c, threadIdx.x, nc);
+                    if (!bnd && (slot[0].flags & SL_WARP_IN)) update_slot<KIND, LAYOUT>(smem, sg, slot[0], gen[0], c, lane);
+                    if (slot[1].flags & SL_WARP_IN) update_slot<KIND, LAYOUT>(smem, sg, slot[1], gen[1], c, lane);
+                }
+                __syncthreads();
+                if (s_abort) goto done;
+            }
+            if (a.measure_every && (a.sweep0 + t + 1) % a.measure_every == 0) {
+                measure_strips<LAYOUT>(smem, S, nseg, a, meas_idx, red);
+                meas_idx++;
+            }
         }
     }
     if constexpr (EXACT_LOOPS) {

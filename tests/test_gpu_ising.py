@@ -201,10 +201,11 @@ def test_whole_lattice_in_one_block(R, L, layout, kind):
 def test_fixed_slot_exact_checkerboard(R, L, layout, kind, flags):
     # two blocks of 512 per SM: one strip of 2 to 4 rows per block, whose
     # first and last rows fill every thread's slot 0 and the rows between its
-    # slot 1 (the fixed-slot kernel; the default shape at L = 1024); one block
-    # of 512 per SM runs the general loop with up to four slots per thread
+    # slot 1 (the fixed-slot kernel); one block of 1024 per SM with its roles
+    # split by warp and a polling warp (the default shape at L = 1024); one
+    # block of 512 per SM runs the general loop with up to four slots per thread
     ref, acc, nm = O.ising_run(L, BETA_C, kind, SEED, 30, flags=flags, measure_every=3)
-    for shape in ((512, 2, 0), (0, 0, 0), (512, 1, 0)):
+    for shape in ((512, 2, 0), (0, 0, 0), (1024, 1, 0), (512, 1, 0)):
         h = R.ising_create(L, BETA_C, layout, kind, flags, SEED, 2)
         try:
             R.ising_set_launch(h, *shape)
@@ -214,6 +215,40 @@ def test_fixed_slot_exact_checkerboard(R, L, layout, kind, flags):
             assert obs["acc"] == acc.tolist() and obs["n_meas"] == nm, shape
         finally:
             R.ising_destroy(h)
+
+
+@pytest.mark.parametrize("L,G,kind,layout", [(1024, 2, O.XORWOW, 0), (1024, 2, O.XS1024W, 1), (768, 2, O.PHILOX4X32_10, 0),
+                                             (768, 2, O.LCG64, 1), (1024, 4, O.MWC, 0), (512, 1, O.LCG32, 0),
+                                             (1024, 2, O.PHILOX4X32_7, 1)])
+def test_split_role_exact_checkerboard(R, L, G, kind, layout):
+    # one block of 1024 threads per SM, one strip of R rows each (R = 3 .. 7
+    # here, uneven): the first 2 L/(2G) threads hold the first and last rows
+    # in slot 0, the other compute threads the first rows between, slot 1 the
+    # rest, and the last warp polls the neighbours' rows
+    ref, acc, nm = O.ising_run(L, BETA_C, kind, SEED, 30, G=G, measure_every=3)
+    h = R.ising_create(L, BETA_C, layout, kind, 0, SEED, G)
+    try:
+        R.ising_set_launch(h, 1024, 1, 0)
+        info = R.ising_plan_info(h)
+        assert info["threads"] == 1024 and info["blocks"] == info["strips"] >= 2
+        R.ising_sweep(h, 30, 3)
+        obs = R.ising_observables(h)
+        assert np.array_equal(R.ising_get_spins(h), ref)
+        assert obs["acc"] == acc.tolist() and obs["n_meas"] == nm
+    finally:
+        R.ising_destroy(h)
+
+
+def test_default_shape_at_L1024_is_split_role(R):
+    # one strip of 6 or 7 rows per SM, 1024 threads
+    import torch
+    h = R.ising_create(1024, BETA_C, 0, O.XORWOW, 0, SEED, 2)
+    try:
+        info = R.ising_plan_info(h)
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        assert info == {"groups": 1, "blocks": sms, "strips": sms, "threads": 1024}
+    finally:
+        R.ising_destroy(h)
 
 
 @pytest.mark.parametrize("layout", [0, 1])
