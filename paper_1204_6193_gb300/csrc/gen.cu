@@ -313,7 +313,9 @@ __device__ __forceinline__ void mt_twist_regs(uint32_t (&x)[kMtRegs], int lane)
 template <int OUT, int LAYOUT>
 __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out_, uint64_t K)
 {
-    __shared__ __align__(16) uint32_t tb_s[OUT == OUT_NORMAL ? kMtWarps : 1][MT_N + 2];  // normals: tempered words, pair-aligned
+    // normals: tempered words, pair-aligned (rows of a multiple of 4 words,
+    // so that every row starts on a 16-byte boundary)
+    __shared__ __align__(16) uint32_t tb_s[OUT == OUT_NORMAL ? kMtWarps : 1][MT_N + 4];
     BmTables bt{};
     if constexpr (OUT == OUT_NORMAL) bt = bm_stage();  // every thread, before any leaves
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -337,6 +339,7 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
     uint32_t *tb = tb_s[OUT == OUT_NORMAL ? w : 0];
     uint32_t pending = 0;  // normals: tempered word waiting for its partner (odd call index)
     const bool out_even = (reinterpret_cast<uintptr_t>(out_) & 7) == 0;
+    const bool out_quad = (reinterpret_cast<uintptr_t>(out_) & 15) == 0 && (K & 3) == 0;
 
     // Hands the words lo .. hi-1 of the state (call index kb for word lo) to
     // the output.  FULL: the whole block (lo = 0, hi = MT_N).
@@ -356,6 +359,33 @@ __global__ void __launch_bounds__(kMtBlock) k_generate_mt(DevParams p, void *out
                 }
             }
         } else {
+            if constexpr (FULLB && LAYOUT == RNG_INSTANCE_MAJOR) {
+                if (out_quad && (kb & 3) == 0) {
+                    // a whole block at a 16-byte aligned place of the row:
+                    // lane l takes words 4q .. 4q+3 (q = l + 32 i) in one
+                    // 16-byte read, makes their two pairs and writes the four
+                    // normals with one 16-byte store; no word is left over
+#pragma unroll
+                    for (int j = 0; j < kMtRegs; j++)
+                        if (j < kMtRegs - 1 || 32 * j + lane < MT_N) tb[32 * j + lane] = mt_temper_mul(x[j]);
+                    __syncwarp();
+                    const uint4 *tq = reinterpret_cast<const uint4 *>(tb);
+                    float4 *oq = reinterpret_cast<float4 *>(static_cast<float *>(out_) + gidx * K + kb);
+#pragma unroll
+                    for (int i = 0; i < (MT_N / 4 + 31) / 32; i++) {
+                        const int q = lane + 32 * i;
+                        if (q < MT_N / 4 && RNGX_IDX_OK(gidx * K + kb + 4 * q + 3, n_out, kSiteGen + __LINE__)) {
+                            const uint4 w = tq[q];
+                            float4 z;
+                            box_muller(w.x, w.y, z.x, z.y, bt);
+                            box_muller(w.z, w.w, z.z, z.w, bt);
+                            __stcs(oq + q, z);
+                        }
+                    }
+                    __syncwarp();
+                    return;
+                }
+            }
             // pairs start at even call indices: an odd kb continues the pending word
             const int off = static_cast<int>(kb & 1);
             if (off && lane == 0) tb[0] = pending;

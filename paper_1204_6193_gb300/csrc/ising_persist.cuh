@@ -215,6 +215,7 @@ enum : uint32_t {
     SL_ROW_LAST = 128u, // the slot's sites end its row (right neighbour wraps)
     SL_DUP_DOWN = 256u, // whole lattice, first row: its flips also go to the halo row below the last
     SL_DUP_UP = 512u,   // whole lattice, last row: its flips also go to the halo row above the first
+    SL_MS_PAIR = 1024u, // multispin, G = 2: lanes 16h .. 16h+15 hold the 16 streams of one word, in bit order
 };
 
 template <int LAYOUT>
@@ -226,7 +227,12 @@ __device__ __forceinline__ void finish_slot(const SegLocal &sg, bool in, bool va
     o.base = sg.off + (row - sg.y0 + 1) * row_bytes<LAYOUT>(sg);
     const bool wi = __any_sync(0xffffffffu, in);
     const bool wb = __any_sync(0xffffffffu, in && (row == sg.y0 || row + 1 == sg.y0 + sg.R));
+    // multispin with two sites per stream: every lane inside the block holds
+    // sites 2l, 2l + 1 (l = lane mod 16) of its word
+    const bool pair = LAYOUT != ISING_INT8 && sg.G == 2 &&
+                      __all_sync(0xffffffffu, !in || (o.xh0 & 31u) == 2u * (threadIdx.x & 15u));
     o.flags = (in ? SL_IN : 0u) | (val ? SL_VAL : 0u) | (wi ? SL_WARP_IN : 0u) | (wb ? SL_WARP_BND : 0u) |
+              (pair ? SL_MS_PAIR : 0u) |
               (sg.coarse ? SL_COARSE : 0u) | ((row & 1u) ? SL_ODD_ROW : 0u) | (o.xh0 == 0 ? SL_ROW_FIRST : 0u) |
               (o.xh0 + sg.G == sg.half ? SL_ROW_LAST : 0u) | (sg.up < 0 && row == sg.y0 ? SL_DUP_DOWN : 0u) |
               (sg.up < 0 && row + 1 == sg.y0 + sg.R ? SL_DUP_UP : 0u);
@@ -342,55 +348,77 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
                 }
             }
         }
+    } else if (G == 2 && (sl.flags & SL_MS_PAIR)) {
+        // Two sites per stream, and the 16 streams of a word in 16 lanes in
+        // bit order (half-warp h holds word h of the warp's two).  The
+        // anti-aligned neighbours k of all 32 sites of the word are counted
+        // at once, bit-sliced, from the word, its row neighbours (shifted by
+        // one site, the carry bit from the next or previous word) and the
+        // words above and below, and kept as three masks: k >= 2 (always
+        // flips, s_i sum_nn s_j = 4 - 2k <= 0), k = 1 (flips iff r < T4) and
+        // k = 0 (iff r < T8).  Each lane sets its two draws' acceptance bits
+        // at its sites' positions; one OR-reduction per half-warp then gives
+        // the word's flips, which its first lane applies.
+        const uint32_t W = sg.W;
+        uint32_t *own = reinterpret_cast<uint32_t *>(own_row);
+        const uint32_t *o = reinterpret_cast<const uint32_t *>(o_row);
+        const uint32_t r0 = gen.next(), r1 = gen.next();
+        const uint32_t wi = sl.xh0 >> 5, b0 = sl.xh0 & 31u;
+        const bool ok = sl.val() && RNGX_IDX_OK(wi, W, kSitePersist + __LINE__) &&
+                        RNGX_SMEM_OK(o - W + wi, smem, 4, kSitePersist + __LINE__) &&
+                        RNGX_SMEM_OK(o + W + wi, smem, 4, kSitePersist + __LINE__) &&
+                        RNGX_SMEM_OK(own + wi, smem, 4, kSitePersist + __LINE__);
+        uint32_t fl = 0, ow = 0;
+        if (ok) {
+            ow = own[wi];
+            const uint32_t mw = o[wi];
+            const uint32_t n2 = p ? (mw >> 1) | (o[wi + 1 == W ? 0 : wi + 1] << 31)
+                                  : (mw << 1) | (o[wi == 0 ? W - 1 : wi - 1] >> 31);
+            const uint32_t a1 = ow ^ mw, a2 = ow ^ n2, a3 = ow ^ o[wi - W], a4 = ow ^ o[wi + W];
+            const uint32_t s1 = a1 ^ a2, c1 = a1 & a2, s2 = a3 ^ a4, c2 = a3 & a4;
+            const uint32_t k0 = s1 ^ s2, t = s1 & s2;
+            const uint32_t k1 = c1 ^ c2 ^ t, k2 = (c1 & c2) | ((c1 ^ c2) & t);
+            const uint32_t ge2 = k1 | k2, eq1 = k0 & ~ge2, eq0 = ~(k0 | ge2);
+            const bool f4 = sg.a_max >= 2, f8 = sg.a_max >= 4;  // T4 / T8 = 2^32: always
+            const uint32_t t4 = sg.t4, t8 = sg.t8;
+            const uint32_t acc4 = ((f4 || r0 < t4) ? 1u : 0u) | ((f4 || r1 < t4) ? 2u : 0u);
+            const uint32_t acc8 = ((f8 || r0 < t8) ? 1u : 0u) | ((f8 || r1 < t8) ? 2u : 0u);
+            fl = (ge2 & (3u << b0)) | (eq1 & (acc4 << b0)) | (eq0 & (acc8 << b0));
+        }
+        const uint32_t fa = __reduce_or_sync(0xffffffffu, lane < 16 ? fl : 0u);
+        const uint32_t fb = __reduce_or_sync(0xffffffffu, lane < 16 ? 0u : fl);
+        const uint32_t fw = lane < 16 ? fa : fb;
+        if (ok && (lane & 15) == 0 && fw) {
+            own[wi] = ow ^ fw;
+            if constexpr (DUP) {  // the halo copy of a whole lattice's edge row
+                if (sl.flags & (SL_DUP_DOWN | SL_DUP_UP)) {
+                    uint32_t *cp = own + wi + static_cast<int>(sg.R * W) * ((sl.flags & SL_DUP_DOWN) ? 1 : -1);
+                    if (RNGX_SMEM_OK(cp, smem, 4, kSitePersist + __LINE__)) *cp = ow ^ fw;
+                }
+            }
+        }
     } else {
+        // any G, site by site: the warp's 32 G sites are G consecutive words
+        // of plane c, assembled by one OR-reduction each
         const uint32_t W = sg.W;
         const uint32_t *own = reinterpret_cast<const uint32_t *>(own_row);
         const uint32_t *o = reinterpret_cast<const uint32_t *>(o_row);
         const uint32_t *ou = o - W, *od = o + W;
         const uint32_t lq0 = lane * G;
         uint32_t c_lo = 0, c_hi = 0;
-        if (G == 2) {
-            // both sites in one word: the anti-aligned neighbours of all 32
-            // sites of the word are counted at once, bit-sliced, from the
-            // word, its row neighbours (shifted by one site) and the words
-            // above and below
-            const uint32_t r0 = gen.next(), r1 = gen.next();
-            if (sl.val() && RNGX_IDX_OK(sl.xh0 >> 5, W, kSitePersist + __LINE__) &&
-                RNGX_SMEM_OK(ou + (sl.xh0 >> 5), smem, 4, kSitePersist + __LINE__) &&
-                RNGX_SMEM_OK(od + (sl.xh0 >> 5), smem, 4, kSitePersist + __LINE__) &&
-                RNGX_SMEM_OK(own + (sl.xh0 >> 5), smem, 4, kSitePersist + __LINE__)) {
-                const uint32_t wi = sl.xh0 >> 5, b0 = sl.xh0 & 31u;
-                const uint32_t ow = own[wi], mw = o[wi];
-                const uint32_t n2 = p ? (mw >> 1) | (o[wi + 1 == W ? 0 : wi + 1] << 31)
-                                      : (mw << 1) | (o[wi == 0 ? W - 1 : wi - 1] >> 31);
-                const uint32_t a1 = ow ^ mw, a2 = ow ^ n2, a3 = ow ^ ou[wi], a4 = ow ^ od[wi];
-                const uint32_t s1 = a1 ^ a2, c1 = a1 & a2, s2 = a3 ^ a4, c2 = a3 & a4;
-                const uint32_t k0 = s1 ^ s2, t = s1 & s2;
-                const uint32_t k1 = c1 ^ c2 ^ t, k2 = (c1 & c2) | ((c1 ^ c2) & t);
-                // site bit b: k anti-aligned neighbours, s_i sum s_j = 4 - 2k
-                auto flips = [&](uint32_t b, uint32_t r) -> uint32_t {
-                    const int k = static_cast<int>(((k0 >> b) & 1u) | (((k1 >> b) & 1u) << 1) | (((k2 >> b) & 1u) << 2));
-                    const int a = 4 - 2 * k;
-                    return (a <= sg.a_max || r < (a == 2 ? sg.t4 : sg.t8)) ? 1u : 0u;
-                };
-                c_lo = (flips(b0, r0) << b0) | (flips(b0 + 1, r1) << (b0 + 1));
-            }
-        } else {
-            for (uint32_t g = 0; g < G; g++) {
-                const uint32_t rr = gen.next();
-                if (!sl.val()) continue;
-                const uint32_t xh = sl.xh0 + g;
-                const int nn = bit_spin(o, col_left(xh, p, half)) + bit_spin(o, col_right(xh, p, half)) +
-                               bit_spin(ou, xh) + bit_spin(od, xh);
-                const int sp = bit_spin(own, xh);
-                if (accept_a(sp * nn, rr, T4, T8)) {
-                    const uint32_t lq = lq0 + g;
-                    if ((lq >> 5) == (lq0 >> 5)) c_lo |= 1u << (lq & 31);
-                    else c_hi |= 1u << (lq & 31);
-                }
+        for (uint32_t g = 0; g < G; g++) {
+            const uint32_t rr = gen.next();
+            if (!sl.val()) continue;
+            const uint32_t xh = sl.xh0 + g;
+            const int nn = bit_spin(o, col_left(xh, p, half)) + bit_spin(o, col_right(xh, p, half)) +
+                           bit_spin(ou, xh) + bit_spin(od, xh);
+            const int sp = bit_spin(own, xh);
+            if (accept_a(sp * nn, rr, T4, T8)) {
+                const uint32_t lq = lq0 + g;
+                if ((lq >> 5) == (lq0 >> 5)) c_lo |= 1u << (lq & 31);
+                else c_hi |= 1u << (lq & 31);
             }
         }
-        // the warp's 32 G sites are G consecutive words of plane c
         const uint32_t f0 = __shfl_sync(0xffffffffu, static_cast<uint32_t>(sl.s - sg.s0), 0);
         const uint64_t q_first = (sg.s0 + f0) * G;
         const uint32_t wbase = static_cast<uint32_t>((q_first - static_cast<uint64_t>(sg.y0) * half) >> 5);
