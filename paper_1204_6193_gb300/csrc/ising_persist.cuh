@@ -368,7 +368,7 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
                         RNGX_SMEM_OK(o - W + wi, smem, 4, kSitePersist + __LINE__) &&
                         RNGX_SMEM_OK(o + W + wi, smem, 4, kSitePersist + __LINE__) &&
                         RNGX_SMEM_OK(own + wi, smem, 4, kSitePersist + __LINE__);
-        uint32_t fl = 0, ow = 0;
+        uint32_t fl = 0, ow = 0, ge2 = 0;
         if (ok) {
             ow = own[wi];
             const uint32_t mw = o[wi];
@@ -377,17 +377,21 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
             const uint32_t a1 = ow ^ mw, a2 = ow ^ n2, a3 = ow ^ o[wi - W], a4 = ow ^ o[wi + W];
             const uint32_t s1 = a1 ^ a2, c1 = a1 & a2, s2 = a3 ^ a4, c2 = a3 & a4;
             const uint32_t k0 = s1 ^ s2, t = s1 & s2;
-            const uint32_t k1 = c1 ^ c2 ^ t, k2 = (c1 & c2) | ((c1 ^ c2) & t);
-            const uint32_t ge2 = k1 | k2, eq1 = k0 & ~ge2, eq0 = ~(k0 | ge2);
-            const bool f4 = sg.a_max >= 2, f8 = sg.a_max >= 4;  // T4 / T8 = 2^32: always
+            // k >= 2: c1 c2 | (c1 ^ c2) t | (c1 ^ c2 ^ t) = c1 | c2 | t
+            ge2 = c1 | c2 | t;
+            // r < T8 <= T4 accepts at k = 0 and 1, r < T4 at k = 1 (k0 set,
+            // k < 2); T = 2^32 (a_max) accepts every draw
+            const bool f4 = sg.a_max >= 2, f8 = sg.a_max >= 4;
             const uint32_t t4 = sg.t4, t8 = sg.t8;
             const uint32_t acc4 = ((f4 || r0 < t4) ? 1u : 0u) | ((f4 || r1 < t4) ? 2u : 0u);
             const uint32_t acc8 = ((f8 || r0 < t8) ? 1u : 0u) | ((f8 || r1 < t8) ? 2u : 0u);
-            fl = (ge2 & (3u << b0)) | (eq1 & (acc4 << b0)) | (eq0 & (acc8 << b0));
+            fl = ((k0 & (acc4 << b0)) | (acc8 << b0));
         }
+        // the word's flips: k >= 2 (the same in all its lanes) and the
+        // lanes' accepted draws
         const uint32_t fa = __reduce_or_sync(0xffffffffu, lane < 16 ? fl : 0u);
         const uint32_t fb = __reduce_or_sync(0xffffffffu, lane < 16 ? 0u : fl);
-        const uint32_t fw = lane < 16 ? fa : fb;
+        const uint32_t fw = (lane < 16 ? fa : fb) | ge2;
         if (ok && (lane & 15) == 0 && fw) {
             own[wi] = ow ^ fw;
             if constexpr (DUP) {  // the halo copy of a whole lattice's edge row
