@@ -372,8 +372,11 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
         if (ok) {
             ow = own[wi];
             const uint32_t mw = o[wi];
-            const uint32_t n2 = p ? (mw >> 1) | (o[wi + 1 == W ? 0 : wi + 1] << 31)
-                                  : (mw << 1) | (o[wi == 0 ? W - 1 : wi - 1] >> 31);
+            // the row neighbours' word: the next one (p = 1) or the previous
+            // one (p = 0), wrapped; its edge bit enters the shifted word
+            const uint32_t nwi = p ? (wi + 1 == W ? 0u : wi + 1) : (wi == 0 ? W - 1 : wi - 1);
+            const uint32_t nw = o[nwi];
+            const uint32_t n2 = p ? __funnelshift_r(mw, nw, 1) : __funnelshift_l(nw, mw, 1);
             const uint32_t a1 = ow ^ mw, a2 = ow ^ n2, a3 = ow ^ o[wi - W], a4 = ow ^ o[wi + W];
             const uint32_t s1 = a1 ^ a2, c1 = a1 & a2, s2 = a3 ^ a4, c2 = a3 & a4;
             const uint32_t k0 = s1 ^ s2, t = s1 & s2;
