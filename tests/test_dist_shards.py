@@ -1,7 +1,9 @@
-"""The multi-rank path on CPU: two gloo ranks each take their shard of
-instances by global index (bench.py's plan), compute it with the oracle,
-and all-gather; the union equals one rank computing everything, and the
-timing reduction takes the slowest rank."""
+"""The multi-rank plan on CPU (host logic only, not a test of the library
+across ranks): two gloo ranks each take their shard of instances by global
+index (bench.py's plan), compute it with the oracle, and all-gather; the
+union equals one rank computing everything, and the timing reduction takes
+the slowest rank.  The library's own sharded handles (rng_create_shard) are
+checked against one handle on a single GPU in the -m gpu tests."""
 import os
 import socket
 
