@@ -562,7 +562,8 @@ def ising_section(R, torch, args):
                         "flips_per_ns": round(L * L * n / (ms * 1e6), 2),
                         "us_per_sweep": round(1e3 * ms / n, 3),
                         "plain_flips_per_ns": round(L * L * nplain / (ms_plain * 1e6), 3),
-                        "sweeps_timed": n, "launch": tuned, "plan": R.ising_plan_info(h),
+                        "sweeps_timed": n, "launch": tuned, "halo_depth": R.ising_get_halo_depth(h),
+                        "plan": R.ising_plan_info(h),
                     }
                 finally:
                     R.ising_destroy(h)
@@ -979,6 +980,8 @@ def run_case(args):
         h = R.ising_create(args.L, BETA_C, layout, kind, 0, SEED, 2)
         if args.launch:
             R.ising_set_launch(h, *(int(v) for v in args.launch.split(",")))
+        if args.halo_depth is not None:
+            R.ising_set_halo_depth(h, args.halo_depth)
         if args.hits:
             R.ising_sweep_multihit(h, args.sweeps, args.hits, args.strips)
         else:
@@ -1034,6 +1037,7 @@ def main():
     ap.add_argument("--hits", type=int, default=0, help="k > 0: multi-hit rounds of k sweeps per strip phase")
     ap.add_argument("--strips", type=int, default=256)
     ap.add_argument("--launch", default="", help="threads,ctas_per_sm,min_sites_per_block of the Ising launch")
+    ap.add_argument("--halo-depth", type=int, default=None, help="Ising exact checkerboard: 1 or 2 halo rows")
     ap.add_argument("--outputs", type=int, default=1 << 26, help="outputs per call with --case all")
     args = ap.parse_args()
     if args.case:

@@ -288,6 +288,23 @@ int ising_observables(ising_t h, int64_t *E, int64_t *M, int64_t acc[4], uint64_
  * numbering alone. */
 int ising_set_launch(ising_t h, uint32_t threads, int ctas_per_sm, uint32_t min_sites_per_block);
 
+/* How far the strips of the exact checkerboard exchange boundary rows
+ * (Sec. 2 application test; the exchange itself is this library's):
+ * depth 1, after every half-sweep, each strip updating only its own rows;
+ * depth 2, once per sweep, each strip also updating colour 0 of the row just
+ * outside it on either side with copies of the neighbours' streams, which
+ * draw exactly as their owners do (the spins are the same either way).
+ * Depth 2 needs a plan of one strip of 4 to 10 rows per block of 1024
+ * threads whose rows hold at most 256 streams (else depth 1 runs).  0 (the
+ * default) takes depth 2 there for the generators with cheap draws (LCG32,
+ * LCG64, MWC, XORWOW); ising_autotune times both.  Other values:
+ * RNG_EINVAL.  Takes effect at the next sweep (replans). */
+int ising_set_halo_depth(ising_t h, uint32_t depth);
+
+/* The depth last set by ising_set_halo_depth or chosen by ising_autotune
+ * (0: automatic). */
+int ising_get_halo_depth(ising_t h, uint32_t *depth);
+
 /* The launch shape last set by ising_set_launch or chosen by
  * ising_autotune (zeros: heuristic), so that a tuned shape can be stored
  * and set again on a handle of the same lattices.  Any pointer may be

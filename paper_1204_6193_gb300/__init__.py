@@ -70,6 +70,8 @@ _SIGS = {
     "ising_set_spins": [_p, _p],
     "ising_get_rng": [_p, _pp],
     "ising_set_launch": [_p, _u32, _i32, _u32],
+    "ising_set_halo_depth": [_p, _u32],
+    "ising_get_halo_depth": [_p, _p],
     "ising_get_launch": [_p, _p, _p, _p],
     "ising_autotune": [_p, _u32, _p, _p],
     "ising_info": [_p, _u32, _p, _p, _p, _p, _p],
@@ -320,6 +322,16 @@ def ising_set_launch(h: int, threads: int = 0, ctas_per_sm: int = 0, min_sites_p
     _call("ising_set_launch", h, threads, ctas_per_sm, min_sites_per_block)
 
 
+def ising_set_halo_depth(h: int, depth: int = 0) -> None:
+    _call("ising_set_halo_depth", h, depth)
+
+
+def ising_get_halo_depth(h: int) -> int:
+    d = _u32()
+    _call("ising_get_halo_depth", h, ctypes.byref(d))
+    return d.value
+
+
 def ising_autotune(h: int, probe_sweeps: int = 64) -> dict:
     t, c = _u32(), _i32()
     _call("ising_autotune", h, probe_sweeps, ctypes.byref(t), ctypes.byref(c))
@@ -369,9 +381,10 @@ def ising_autotune_cached(h: int, probe_sweeps: int = 64, path: str | None = Non
     if key in cache:
         c = cache[key]
         ising_set_launch(h, c["threads"], c["ctas_per_sm"], c["min_sites"])
+        ising_set_halo_depth(h, c.get("halo_depth", 0))
         return dict(c, cached=True)
     ising_autotune(h, probe_sweeps)
-    c = ising_get_launch(h)
+    c = dict(ising_get_launch(h), halo_depth=ising_get_halo_depth(h))
     cache[key] = c
     os.makedirs(os.path.dirname(path), exist_ok=True)
     tmp = f"{path}.tmp{os.getpid()}"

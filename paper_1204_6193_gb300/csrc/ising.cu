@@ -277,15 +277,17 @@ struct IsingLat {
 struct Plan {
     int kind = 0, layout = 0, smax = 1;
     int fixed_slots = 0;  // 1: each thread slot has a fixed role (kernel modes 2, 3); 2: whole lattices (mode 4);
-                          // 3: one strip per block, roles split by warp, a polling warp (mode 5)
+                          // 3: one strip per block, roles split by warp, a polling warp (mode 5);
+                          // 4: one strip per block with a halo of two rows, one exchange per sweep (mode 6)
     unsigned nblocks = 0, threads = 0;
     size_t smem = 0;
     uint32_t nsegs = 0, halo_row_bytes = 0;
     SegDev *d_segs = nullptr;
     uint32_t *d_cta = nullptr;
     uint8_t *d_halo = nullptr;
-    // per strip: 2 slots x 2 rows x 2 colours of (tag, data) words
-    size_t halo_bytes() const { return static_cast<size_t>(nsegs) * 8 * halo_row_bytes; }
+    // per strip: 2 slots x 2 rows x 2 colours of (tag, data) words (mode 6:
+    // 2 parities x 6 half-rows)
+    size_t halo_bytes() const { return static_cast<size_t>(nsegs) * (fixed_slots == 4 ? 12 : 8) * halo_row_bytes; }
 };
 
 struct ising_s {
@@ -303,6 +305,7 @@ struct ising_s {
     unsigned cfg_threads = 0;    // 0: heuristic
     int cfg_ctas_per_sm = 0;     // 0: heuristic
     uint32_t cfg_min_sites = 0;  // 0: heuristic (1024)
+    uint32_t cfg_halo_depth = 0; // 0: two-row halo where a plan fits it, 1: one row
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
     int32_t mute_seg = -1;                  // test hook (see ising_debug_mute_strip)
@@ -449,10 +452,10 @@ uint32_t align_rows(const IsingLat &t)
     return 32 / gcd32(spr, 32);
 }
 
-size_t seg_smem(const IsingLat &t, uint32_t rows)
+size_t seg_smem(const IsingLat &t, uint32_t rows, uint32_t hd = 1)
 {
     const size_t rb = t.layout == ISING_INT8 ? t.L / 2 : t.W * 4;
-    return (2 * (rows + 2) * rb + 15) / 16 * 16;
+    return (2 * (rows + 2 * hd) * rb + 15) / 16 * 16;
 }
 
 struct SegPlan {
@@ -636,8 +639,34 @@ int materialize_plan(ising_t h, int kind, int layout, const std::vector<std::vec
         const uint64_t spr = t.L / 2 / t.G, R = d.y1 - d.y0, nc = threads - 32;
         if (d.up < 0 || R < 2 || spr % 32 || 2 * spr > nc || d.s1 - d.s0 != R * spr || R * spr > 2 * nc) split = false;
     }
+    // the same with a halo of two rows (kernel mode 6): every block one
+    // strip of 4 .. 10 rows whose rows and the two halo copies fill the
+    // cells of the kernel's layout (four cells of one row's streams per slot)
+    // (automatic choice: the generators whose draws cost a few instructions;
+    // for Philox and the 1024-bit generator the copies' extra draws cost more
+    // than the exchanges they save, measured on GB300)
+    const bool cheap_draws = kind == RNG_LCG32 || kind == RNG_LCG64 || kind == RNG_MWC || kind == RNG_XORWOW;
+    bool deep = !multihit && threads == 1024 && !blocks.empty() &&
+                (h->cfg_halo_depth == 2 || (h->cfg_halo_depth == 0 && cheap_draws));
+    size_t deep_smem = 0;
+    for (size_t b = 0; b < blocks.size() && deep; b++) {
+        if (blocks[b].size() != 1) {
+            deep = false;
+            break;
+        }
+        const SegDev &d = segs[cta[b]];
+        const IsingLat &t = h->lats[d.lat];
+        const uint64_t spr = t.L / 2 / t.G, R = d.y1 - d.y0;
+        const uint64_t row_words = (t.layout == ISING_INT8 ? t.L / 2 : t.W * 4) / 4;
+        if (d.up < 0 || R < 4 || R > 10 || spr % 32 || 4 * spr > threads || 6 * row_words > threads ||
+            d.s1 - d.s0 != R * spr || seg_smem(t, static_cast<uint32_t>(R), 2) > kSmemCap)
+            deep = false;
+        else
+            deep_smem = std::max(deep_smem, seg_smem(t, static_cast<uint32_t>(R), 2));
+    }
+    if (deep) split = false;
     if (split) spt = 2;
-    if (spt >= 2 && threads > 512 && !split) {  // other multi-slot kernels are built for at most 512 threads
+    if (spt >= 2 && threads > 512 && !split && !deep) {  // other multi-slot kernels are built for at most 512 threads
         threads = 512;
         spt = std::min<uint64_t>(4, (max_streams + threads - 1) / threads);
     }
@@ -667,6 +696,10 @@ int materialize_plan(ising_t h, int kind, int layout, const std::vector<std::vec
     P.kind = kind;
     P.layout = layout;
     P.smax = spt <= 1 ? 1 : (spt <= 2 ? 2 : 4);
+    if (deep) {
+        P.smax = 3;
+        smem_max = deep_smem;  // one strip per block at offset 0
+    }
     if (!multihit && P.smax == 2) {
         // exact checkerboard: one strip per block whose first and last rows
         // fill at most one slot of every thread and the rows between another
@@ -685,6 +718,7 @@ int materialize_plan(ising_t h, int kind, int layout, const std::vector<std::vec
     }
     P.fixed_slots = fixed && P.smax == 2 ? 1 : 0;
     if (split) P.fixed_slots = 3;
+    if (deep) P.fixed_slots = 4;
     if (!multihit && P.smax == 1 && max_streams <= threads) {
         // every block one whole lattice whose streams fit one slot per thread
         bool whole = true;
@@ -1261,6 +1295,27 @@ int ising_set_launch(ising_t h, uint32_t threads, int ctas_per_sm, uint32_t min_
     return RNG_OK;
 }
 
+int ising_set_halo_depth(ising_t h, uint32_t depth)
+{
+    RNGX_CHECK(valid(h));
+    if (depth > 2) {
+        set_error("halo depth must be 0 (automatic), 1 or 2");
+        return RNG_EINVAL;
+    }
+    RNGX_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+    free_plans(h);
+    h->plan_unfit = false;
+    h->cfg_halo_depth = depth;
+    return RNG_OK;
+}
+
+int ising_get_halo_depth(ising_t h, uint32_t *depth)
+{
+    RNGX_CHECK(valid(h));
+    if (depth) *depth = h->cfg_halo_depth;
+    return RNG_OK;
+}
+
 int ising_batch_sweep(ising_t h, uint64_t n_sweeps, uint32_t measure_every, void *cuda_stream)
 {
     RNGX_CHECK(valid(h));
@@ -1316,7 +1371,7 @@ extern "C" int ising_autotune(ising_t h, uint32_t probe_sweeps, uint32_t *thread
     static const int kPerSm[] = {1, 2, 4};
     static const uint32_t kMinSites[] = {1024, 8192, 65536};
     float best = -1.0f;
-    uint32_t best_t = 0, best_m = 0;
+    uint32_t best_t = 0, best_m = 0, best_d = 0;
     int best_c = 0;
     cudaEvent_t e0, e1;
     RNGX_CHECK_CUDA(cudaEventCreate(&e0));
@@ -1326,7 +1381,9 @@ extern "C" int ising_autotune(ising_t h, uint32_t probe_sweeps, uint32_t *thread
     for (uint32_t ms : kMinSites) {
         if (ms > 1024 && ms / 8 > total_sites) continue;  // same plan as a smaller minimum
         for (uint32_t th : kThreads) {
-            for (int pc : kPerSm) {
+          for (int pc : kPerSm) {
+            // a single lattice in blocks of 1024 threads: both halo depths
+            for (uint32_t hd = (th == 1024 && !h->batch) ? 1 : 0; hd <= ((th == 1024 && !h->batch) ? 2u : 0u); hd++) {
                 // probe a clone: the launch shape never changes results, and
                 // the handle itself must not advance
                 ising_t c = nullptr;
@@ -1350,6 +1407,7 @@ extern "C" int ising_autotune(ising_t h, uint32_t probe_sweeps, uint32_t *thread
                 c->cfg_threads = th;
                 c->cfg_ctas_per_sm = pc;
                 c->cfg_min_sites = ms;
+                c->cfg_halo_depth = hd;
                 st = ising_sweep(c, std::max<uint32_t>(1, probe_sweeps / 4), 0, h->stream);
                 float msec = 0.0f;
                 if (st == RNG_OK) {
@@ -1366,8 +1424,10 @@ extern "C" int ising_autotune(ising_t h, uint32_t probe_sweeps, uint32_t *thread
                     best_t = th;
                     best_c = pc;
                     best_m = ms;
+                    best_d = hd;
                 }
             }
+          }
         }
     }
     cudaEventDestroy(e0);
@@ -1377,6 +1437,7 @@ extern "C" int ising_autotune(ising_t h, uint32_t probe_sweeps, uint32_t *thread
         return RNG_EUNSUPPORTED;
     }
     RNGX_CHECK(ising_set_launch(h, best_t, best_c, best_m));
+    RNGX_CHECK(ising_set_halo_depth(h, best_d));
     if (threads_out) *threads_out = best_t;
     if (ctas_per_sm_out) *ctas_per_sm_out = best_c;
     return RNG_OK;

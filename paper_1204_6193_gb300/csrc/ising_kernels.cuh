@@ -88,15 +88,25 @@ int launch_persist_t(const PersistArgs &a, unsigned nblocks, unsigned threads, s
 {
     // kernel modes: 0 exact, 1 multi-hit, 2 / 3 the same with fixed slot roles
     // (SMAX = 2), 4 exact with one whole resident lattice per block (SMAX = 1),
-    // 5 exact with roles split by warp and a polling warp (SMAX = 2)
-    const bool fixed = SMAX == 2 && a.fixed_slots == 1, whole = SMAX == 1 && a.fixed_slots == 2;
-    const bool split = SMAX == 2 && a.fixed_slots == 3 && !a.k_hits;
-    auto kern = a.k_hits ? (fixed ? k_ising_persist<KIND, LAYOUT, SMAX, SMAX == 2 ? 2 : 1>
-                                  : k_ising_persist<KIND, LAYOUT, SMAX, 1>)
-                         : (fixed ? k_ising_persist<KIND, LAYOUT, SMAX, SMAX == 2 ? 3 : 0>
-                                  : (whole ? k_ising_persist<KIND, LAYOUT, SMAX, SMAX == 1 ? 4 : 0>
-                                           : (split ? k_ising_persist<KIND, LAYOUT, SMAX, SMAX == 2 ? 5 : 0>
-                                                    : k_ising_persist<KIND, LAYOUT, SMAX, 0>)));
+    // 5 exact with roles split by warp and a polling warp (SMAX = 2), 6 exact
+    // with a halo of two rows and one exchange per sweep (SMAX = 3, only)
+    void (*kern)(PersistArgs);
+    if constexpr (SMAX == 3) {
+        if (a.k_hits || a.fixed_slots != 4) {
+            set_error("persistent Ising: three slots per thread are the two-row-halo kernel's only");
+            return RNG_EINVAL;
+        }
+        kern = k_ising_persist<KIND, LAYOUT, 3, 6>;
+    } else {
+        const bool fixed = SMAX == 2 && a.fixed_slots == 1, whole = SMAX == 1 && a.fixed_slots == 2;
+        const bool split = SMAX == 2 && a.fixed_slots == 3 && !a.k_hits;
+        kern = a.k_hits ? (fixed ? k_ising_persist<KIND, LAYOUT, SMAX, SMAX == 2 ? 2 : 1>
+                                 : k_ising_persist<KIND, LAYOUT, SMAX, 1>)
+                        : (fixed ? k_ising_persist<KIND, LAYOUT, SMAX, SMAX == 2 ? 3 : 0>
+                                 : (whole ? k_ising_persist<KIND, LAYOUT, SMAX, SMAX == 1 ? 4 : 0>
+                                          : (split ? k_ising_persist<KIND, LAYOUT, SMAX, SMAX == 2 ? 5 : 0>
+                                                   : k_ising_persist<KIND, LAYOUT, SMAX, 0>)));
+    }
     RNGX_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     int per_sm = 0, dev = 0, sms = 0;
     RNGX_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
@@ -123,12 +133,14 @@ int launch_persist(int layout, int smax, const PersistArgs &a, unsigned nblocks,
         switch (smax) {
         case 1: return launch_persist_t<KIND, ISING_INT8, 1>(a, nblocks, threads, smem, s, max_blocks);
         case 2: return launch_persist_t<KIND, ISING_INT8, 2>(a, nblocks, threads, smem, s, max_blocks);
+        case 3: return launch_persist_t<KIND, ISING_INT8, 3>(a, nblocks, threads, smem, s, max_blocks);
         default: return launch_persist_t<KIND, ISING_INT8, 4>(a, nblocks, threads, smem, s, max_blocks);
         }
     }
     switch (smax) {
     case 1: return launch_persist_t<KIND, ISING_MULTISPIN32, 1>(a, nblocks, threads, smem, s, max_blocks);
     case 2: return launch_persist_t<KIND, ISING_MULTISPIN32, 2>(a, nblocks, threads, smem, s, max_blocks);
+    case 3: return launch_persist_t<KIND, ISING_MULTISPIN32, 3>(a, nblocks, threads, smem, s, max_blocks);
     default: return launch_persist_t<KIND, ISING_MULTISPIN32, 4>(a, nblocks, threads, smem, s, max_blocks);
     }
 }

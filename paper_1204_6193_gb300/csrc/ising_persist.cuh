@@ -42,6 +42,7 @@ struct PersistArgs {
 
 struct SegLocal {              // per-segment constants held in shared memory
     uint32_t L, half, W, G, y0, R, off, lat, coarse;
+    uint32_t hd;               // halo rows above and below the strip (1; 2 in kernel mode 6)
     uint32_t pstride;          // plane 1 - plane 0 offset in shared memory
     int32_t up, down, gid;
     uint64_t s0, prefix, T4, T8;
@@ -57,24 +58,24 @@ __device__ __forceinline__ uint32_t row_bytes(const SegLocal &S)
     return LAYOUT == ISING_INT8 ? S.half : S.W * 4u;
 }
 
-// Address of plane c, local row r (r in [-1, R]) of a segment.
+// Address of plane c, local row r (r in [-hd, R + hd - 1]) of a segment.
 template <int LAYOUT>
 __device__ __forceinline__ uint8_t *plane_row(uint8_t *smem, const SegLocal &S, int c, int r)
 {
     const uint32_t rb = row_bytes<LAYOUT>(S);
-    return smem + S.off + (static_cast<uint32_t>(c) * (S.R + 2) + static_cast<uint32_t>(r + 1)) * rb;
+    return smem + S.off + (static_cast<uint32_t>(c) * (S.R + 2 * S.hd) + static_cast<uint32_t>(r + static_cast<int>(S.hd))) * rb;
 }
 
-// Global spins -> shared planes for rows y0-1 .. y0+R (all threads).
+// Global spins -> shared planes for rows y0-hd .. y0+R+hd-1 (all threads).
 template <int LAYOUT>
 __device__ void load_segment(uint8_t *smem, const SegLocal &S, const void *spins)
 {
-    const int rows = static_cast<int>(S.R) + 2;
+    const int rows = static_cast<int>(S.R + 2 * S.hd);
     if (LAYOUT == ISING_INT8) {
         const int8_t *g = static_cast<const int8_t *>(spins);
         const uint32_t total = rows * S.L;
         for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            const int r = static_cast<int>(idx / S.L) - 1;
+            const int r = static_cast<int>(idx / S.L) - static_cast<int>(S.hd);
             const uint32_t x = idx % S.L;
             const uint32_t y = (S.y0 + S.L + r) % S.L;
             const int c = (x + y) & 1;
@@ -89,7 +90,7 @@ __device__ void load_segment(uint8_t *smem, const SegLocal &S, const void *spins
         for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
             const int c = idx / (rows * S.W);
             const uint32_t rem = idx % (rows * S.W);
-            const int r = static_cast<int>(rem / S.W) - 1;
+            const int r = static_cast<int>(rem / S.W) - static_cast<int>(S.hd);
             const uint32_t w = rem % S.W;
             const uint32_t y = (S.y0 + S.L + r) % S.L;
             uint32_t *dst = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, S, c, r)) + w;
@@ -216,6 +217,12 @@ enum : uint32_t {
     SL_DUP_DOWN = 256u, // whole lattice, first row: its flips also go to the halo row below the last
     SL_DUP_UP = 512u,   // whole lattice, last row: its flips also go to the halo row above the first
     SL_MS_PAIR = 1024u, // multispin, G = 2: lanes 16h .. 16h+15 hold the 16 streams of one word, in bit order
+    // kernel mode 6 (halo of two rows, one exchange per sweep): the phases a slot takes part in
+    SL_PH_A = 2048u,    // colour 0, the rows between the first and the last (no halo needed)
+    SL_PH_B = 4096u,    // colour 0, the first and last rows and the halo rows -1 and R (after the poll)
+    SL_PH_C = 8192u,    // colour 1, rows 0, 1, R-2, R-1 (published next)
+    SL_PH_D = 16384u,   // colour 1, rows 2 .. R-3
+    SL_REPLICA = 32768u // a copy of a neighbour's stream (halo row -1 or R): never stored
 };
 
 template <int LAYOUT>
@@ -224,7 +231,7 @@ __device__ __forceinline__ void finish_slot(const SegLocal &sg, bool in, bool va
     const uint32_t q0 = o.s * sg.G;
     const uint32_t row = q0 / sg.half;
     o.xh0 = q0 - row * sg.half;
-    o.base = sg.off + (row - sg.y0 + 1) * row_bytes<LAYOUT>(sg);
+    o.base = sg.off + (row - sg.y0 + sg.hd) * row_bytes<LAYOUT>(sg);
     const bool wi = __any_sync(0xffffffffu, in);
     const bool wb = __any_sync(0xffffffffu, in && (row == sg.y0 || row + 1 == sg.y0 + sg.R));
     // multispin with two sites per stream: every lane inside the block holds
@@ -426,20 +433,23 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
                 else c_hi |= 1u << (lq & 31);
             }
         }
-        const uint32_t f0 = __shfl_sync(0xffffffffu, static_cast<uint32_t>(sl.s - sg.s0), 0);
-        const uint64_t q_first = (sg.s0 + f0) * G;
-        const uint32_t wbase = static_cast<uint32_t>((q_first - static_cast<uint64_t>(sg.y0) * half) >> 5);
+        // the warp's first word, counted from row 0 of plane c (rows are
+        // contiguous; a halo copy's row -1 gives a negative count)
+        const uint32_t base0 = __shfl_sync(0xffffffffu, sl.base, 0), x0 = __shfl_sync(0xffffffffu, sl.xh0, 0);
         uint32_t *plane_c = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, 0));
-        const uint32_t own_words = sg.R * W;
+        const int wbase = static_cast<int>(reinterpret_cast<uint32_t *>(smem + base0 + (c ? pstride : 0u)) - plane_c) +
+                          static_cast<int>(x0 >> 5);
+        const int own_words = static_cast<int>(sg.R * W), lo = -static_cast<int>(sg.hd - 1) * static_cast<int>(W),
+                  hi = own_words + static_cast<int>(sg.hd - 1) * static_cast<int>(W);
         for (uint32_t m = 0; m < G; m++) {
             const uint32_t mine = ((lq0 >> 5) == m ? c_lo : 0u) | ((lq0 >> 5) + 1 == m ? c_hi : 0u);
             const uint32_t word = __reduce_or_sync(0xffffffffu, mine);
-            if (lane == 0 && word && wbase + m < own_words &&
-                RNGX_SMEM_OK(plane_c + wbase + m, smem, 4, kSitePersist + __LINE__)) {
-                plane_c[wbase + m] ^= word;
+            const int wm = wbase + static_cast<int>(m);
+            if (lane == 0 && word && wm >= lo && wm < hi && RNGX_SMEM_OK(plane_c + wm, smem, 4, kSitePersist + __LINE__)) {
+                plane_c[wm] ^= word;
                 if constexpr (DUP) {  // the halo copies of the whole lattice's edge rows
-                    if (wbase + m < W) plane_c[wbase + m + own_words] ^= word;
-                    if (wbase + m >= own_words - W) plane_c[wbase + m - own_words] ^= word;
+                    if (wm < static_cast<int>(W)) plane_c[wm + own_words] ^= word;
+                    if (wm >= own_words - static_cast<int>(W)) plane_c[wm - own_words] ^= word;
                 }
             }
         }
@@ -545,7 +555,7 @@ __device__ __forceinline__ void publish_rows_by(uint8_t *smem, const SegLocal &s
     const uint32_t *rowl = reinterpret_cast<const uint32_t *>(plane_row<LAYOUT>(smem, sg, c, sg.R - 1));
     uint64_t *d0 = halo_row(a, sg.gid, slot, 0, c), *d1 = halo_row(a, sg.gid, slot, 1, c);
     const uint64_t t = static_cast<uint64_t>(tag) << 32;
-    const uint64_t *hb = reinterpret_cast<const uint64_t *>(a.halo);
+    [[maybe_unused]] const uint64_t *hb = reinterpret_cast<const uint64_t *>(a.halo);
     for (uint32_t i = tid; i < words; i += nthr) {
         if (!RNGX_IDX_OK(d0 + i - hb, a.halo_bytes / 8, kSitePersist + __LINE__) ||
             !RNGX_IDX_OK(d1 + i - hb, a.halo_bytes / 8, kSitePersist + __LINE__) ||
@@ -575,7 +585,7 @@ __device__ __forceinline__ bool poll_rows(uint8_t *smem, const SegLocal &sg, con
     const uint64_t *up_last = halo_row(a, sg.up, slot, 1, c), *dn_first = halo_row(a, sg.down, slot, 0, c);
     uint32_t *top = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, -1));
     uint32_t *bot = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, sg.R));
-    const uint64_t *hb = reinterpret_cast<const uint64_t *>(a.halo);
+    [[maybe_unused]] const uint64_t *hb = reinterpret_cast<const uint64_t *>(a.halo);
     for (uint32_t i = threadIdx.x; i < 2 * words; i += blockDim.x) {
         const uint64_t *src = i < words ? up_last + i : dn_first + (i - words);
         // an index outside the halo buffer or the halo rows is recorded
@@ -618,7 +628,7 @@ __device__ __forceinline__ bool poll_rows_warp(uint8_t *smem, const SegLocal &sg
     const uint64_t *up_last = halo_row(a, sg.up, slot, 1, c), *dn_first = halo_row(a, sg.down, slot, 0, c);
     uint32_t *top = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, -1));
     uint32_t *bot = reinterpret_cast<uint32_t *>(plane_row<LAYOUT>(smem, sg, c, sg.R));
-    const uint64_t *hb = reinterpret_cast<const uint64_t *>(a.halo);
+    [[maybe_unused]] const uint64_t *hb = reinterpret_cast<const uint64_t *>(a.halo);
     const uint64_t t0 = global_ns();
     const long long c0 = clock64();
     for (uint32_t base = 0; base < total; base += 32 * K) {
@@ -658,6 +668,120 @@ __device__ __forceinline__ bool poll_rows_warp(uint8_t *smem, const SegLocal &sg
             }
         }
     }
+    return true;
+}
+
+// ---- kernel mode 6: a halo of two rows, one exchange per sweep.
+// Each strip also updates colour 0 of the rows just outside it (-1 and R),
+// with copies of the neighbours' streams that draw exactly as the owners
+// do, so that colour 1 of its own rows needs nothing from outside; after
+// colour 1 of its rows 0, 1, R-2 and R-1 it publishes six half-rows, which
+// the neighbours take into rows -2 .. -1 and R .. R+1 before their next
+// sweep's edge rows.
+constexpr int kNoRow = -1000;
+
+// Local row held by slot k, cell `cell` (cell = thread / streams per row) of
+// a strip of R rows (4 <= R <= 10): the edge rows and the halo copies each
+// fill one cell of different warps, so that each phase spreads over the
+// block.  slot 0: rows 0, R-1, D2, D3; slot 1: D0, D1, 1, R-2; slot 2: D4,
+// D5, -1, R; D_i = 2 + i, the rows 2 .. R-3.
+__device__ __forceinline__ int mode6_row(int k, uint32_t cell, int R)
+{
+    auto D = [&](int i) { return 2 + i <= R - 3 ? 2 + i : kNoRow; };
+    if (cell >= 4) return kNoRow;
+    if (k == 0) return cell == 0 ? 0 : (cell == 1 ? R - 1 : D(static_cast<int>(cell)));
+    if (k == 1) return cell == 0 ? D(0) : (cell == 1 ? D(1) : (cell == 2 ? 1 : R - 2));
+    return cell == 0 ? D(4) : (cell == 1 ? D(5) : (cell == 2 ? -1 : R));
+}
+
+// Mode 6 halo buffer: per strip, 2 parities x 6 half-rows: the first row
+// (colours 0, 1), the second row (colour 1), the last row (colours 0, 1), the
+// second-last row (colour 1).
+__device__ __forceinline__ uint64_t *halo_row6(const PersistArgs &a, int gid, uint32_t par, uint32_t which)
+{
+    return reinterpret_cast<uint64_t *>(a.halo + ((static_cast<size_t>(gid) * 2 + par) * 6 + which) * a.halo_row_bytes);
+}
+
+__device__ __forceinline__ void mode6_half_row(const SegLocal &sg, uint32_t which, int &row, int &colour)
+{
+    row = which <= 1 ? 0 : (which == 2 ? 1 : (which == 5 ? static_cast<int>(sg.R) - 2 : static_cast<int>(sg.R) - 1));
+    colour = (which == 0 || which == 3) ? 0 : 1;
+}
+
+// Each thread publishes at most one word and polls at most one (6 half-rows
+// of at most blockDim / 6 words): its addresses are worked out once per
+// launch into shared tables (parity 0; parity 1 lies 6 half-rows further).
+struct Mode6Tab {
+    uint64_t *pub_dst;         // halo buffer word this thread publishes
+    const uint64_t *poll_src;  // halo buffer word this thread polls
+    uint32_t pub_src, poll_dst;  // shared-memory byte offsets of the word published / filled
+};
+
+template <int LAYOUT>
+__device__ __forceinline__ void mode6_table(uint8_t *smem, const SegLocal &sg, const PersistArgs &a, Mode6Tab *tab)
+{
+    const uint32_t words = row_bytes<LAYOUT>(sg) / 4, i = threadIdx.x;
+    Mode6Tab e{nullptr, nullptr, 0u, 0u};
+    if (i < 6 * words) {
+        const uint32_t which = i / words, w = i - which * words;
+        int row, colour;
+        mode6_half_row(sg, which, row, colour);
+        e.pub_src = static_cast<uint32_t>(plane_row<LAYOUT>(smem, sg, colour, row) - smem) + 4 * w;
+        e.pub_dst = halo_row6(a, sg.gid, 0, which) + w;
+        // which 0..2: the upper neighbour's half-rows 3..5 into rows -1, -1, -2;
+        // 3..5: the lower neighbour's 0..2 into rows R, R, R+1
+        e.poll_src = which < 3 ? halo_row6(a, sg.up, 0, which + 3) + w : halo_row6(a, sg.down, 0, which - 3) + w;
+        const int prow = which <= 1 ? -1 : (which == 2 ? -2 : (which == 5 ? static_cast<int>(sg.R) + 1 : static_cast<int>(sg.R)));
+        const int pcol = (which == 0 || which == 3) ? 0 : 1;
+        e.poll_dst = static_cast<uint32_t>(plane_row<LAYOUT>(smem, sg, pcol, prow) - smem) + 4 * w;
+    }
+    tab[threadIdx.x] = e;
+}
+
+// Publishes this thread's word as (tag, 32 data bits), one relaxed store.
+__device__ __forceinline__ void publish6(uint8_t *smem, const SegLocal &sg, const PersistArgs &a, const Mode6Tab &e,
+                                         uint32_t par, uint32_t tag)
+{
+    if (e.pub_dst == nullptr || sg.gid == a.mute_seg) return;  // mute_seg: test hook, a strip that never publishes
+    uint64_t *dst = e.pub_dst + par * (6 * a.halo_row_bytes / 8);
+    [[maybe_unused]] const uint64_t *hb = reinterpret_cast<const uint64_t *>(a.halo);
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(smem + e.pub_src);
+    if (!RNGX_IDX_OK(dst - hb, a.halo_bytes / 8, kSitePersist + __LINE__) || !RNGX_SMEM_OK(src, smem, 4, kSitePersist + __LINE__))
+        return;
+    st_relaxed_u64(dst, (static_cast<uint64_t>(tag) << 32) | *src);
+}
+
+// Waits (bounded like poll_rows) for this thread's word to carry `tag` and
+// puts its data into the halo; false when the wait ran out or another block
+// recorded an error.
+__device__ __forceinline__ bool poll6(uint8_t *smem, const PersistArgs &a, const Mode6Tab &e, uint32_t par,
+                                      uint32_t tag)
+{
+    if (e.poll_src == nullptr) return true;
+    const uint64_t *src = e.poll_src + par * (6 * a.halo_row_bytes / 8);
+    [[maybe_unused]] const uint64_t *hb = reinterpret_cast<const uint64_t *>(a.halo);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(smem + e.poll_dst);
+    if (!RNGX_IDX_OK(src - hb, a.halo_bytes / 8, kSitePersist + __LINE__) || !RNGX_SMEM_OK(dst, smem, 4, kSitePersist + __LINE__))
+        return true;
+    uint64_t v;
+    uint32_t spins = 0;
+    uint64_t t0 = 0;
+    long long c0 = 0;
+    while (((v = ld_relaxed_u64(src)) >> 32) != tag) {
+        if (spins == 0) {
+            t0 = global_ns();
+            c0 = clock64();
+        }
+        if ((++spins & 31u) == 0) {
+            if (global_ns() - t0 > a.wait_budget_ns || static_cast<uint64_t>(clock64() - c0) > 4 * a.wait_budget_ns ||
+                ld_acquire(reinterpret_cast<const uint32_t *>(a.err)) != 0) {
+                atomicCAS(a.err, 0, RNG_ETIMEOUT);
+                return false;
+            }
+            __nanosleep(32);
+        }
+    }
+    *dst = static_cast<uint32_t>(v);
     return true;
 }
 
@@ -707,19 +831,25 @@ __device__ void measure_strips(uint8_t *smem, const SegLocal *S, uint32_t nseg, 
 //      between, and the last warp holds no stream: it polls the
 //      neighbours' rows for the whole half-sweep, so that their arrival
 //      overlaps the interior work (one block of 1024 threads per SM).
+//   6: (SMAX = 3 only) exact checkerboard, one strip of 4 .. 10 rows per
+//      block with a halo of two rows: the strip also updates colour 0 of
+//      rows -1 and R with copies of the neighbours' streams, so that rows are
+//      exchanged once per sweep (the phases A .. D of the mode-6 loop below).
 // Launch bounds: the exact-checkerboard kernel runs multi-slot shapes with
-// at most 512 threads, except mode 5; the multi-hit kernel also runs two
-// slots with up to 1024 threads.
+// at most 512 threads, except modes 5 and 6; the multi-hit kernel also runs
+// two slots with up to 1024 threads.
 template <int KIND, int LAYOUT, int SMAX, int MODE>
-__global__ void __launch_bounds__(MODE == 5 ? 1024 : (SMAX >= ((MODE == 1 || MODE == 2) ? 4 : 2) ? 512 : 1024),
+__global__ void __launch_bounds__(MODE >= 5 ? 1024 : (SMAX >= ((MODE == 1 || MODE == 2) ? 4 : 2) ? 512 : 1024),
                                   ((MODE == 0 || MODE == 3 || MODE == 4) && SMAX == 2) ? 2 : 1)
     k_ising_persist(PersistArgs a)
 {
     static_assert(MODE != 5 || SMAX == 2, "mode 5 holds two stream slots per thread");
+    static_assert(MODE != 6 || SMAX == 3, "mode 6 holds three stream slots per thread");
     constexpr bool MH = MODE == 1 || MODE == 2;
     constexpr bool EXACT_LOOPS = MODE == 0 || MODE == 3;
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ SegLocal S[kPersistMaxSegs];
+    __shared__ Mode6Tab m6tab[MODE == 6 ? 1024 : 1];
     __shared__ uint64_t prefix_end;
     __shared__ int s_abort;
     __shared__ long long red[32];
@@ -737,7 +867,8 @@ __global__ void __launch_bounds__(MODE == 5 ? 1024 : (SMAX >= ((MODE == 1 || MOD
         s.off = d.smem_off;
         s.lat = d.lat;
         s.coarse = d.coarse;
-        s.pstride = (s.R + 2) * (l.layout == ISING_INT8 ? l.half : l.W * 4u);
+        s.hd = MODE == 6 ? 2u : 1u;
+        s.pstride = (s.R + 2 * s.hd) * (l.layout == ISING_INT8 ? l.half : l.W * 4u);
         s.up = d.up;
         s.down = d.down;
         s.gid = static_cast<int32_t>(sb + threadIdx.x);
@@ -818,6 +949,38 @@ __global__ void __launch_bounds__(MODE == 5 ? 1024 : (SMAX >= ((MODE == 1 || MOD
                 slot[k].seg = 0;
                 slot[k].s = static_cast<uint32_t>(sg.s0 + (in ? f : 0));
                 finish_slot<LAYOUT>(sg, in, in && slot[k].s < sg.n_valid, slot[k]);
+            } else if constexpr (MODE == 6) {
+                // the rows of (slot, cell) as mode6_row lays them out; the
+                // halo rows -1 and R hold copies of the neighbours' streams
+                const SegLocal &sg = S[0];
+                const uint32_t spr = sg.half / sg.G, cell = threadIdx.x / spr, j = threadIdx.x - cell * spr;
+                const int R = static_cast<int>(sg.R);
+                const int lr = mode6_row(k, cell, R);
+                const bool in = lr != kNoRow;
+                const uint32_t grow = in ? static_cast<uint32_t>((static_cast<int>(sg.y0 + sg.L) + lr) % static_cast<int>(sg.L)) : 0u;
+                StreamSlot &o = slot[k];
+                o.seg = 0;
+                o.s = in ? static_cast<uint32_t>(static_cast<uint64_t>(grow) * spr + j) : static_cast<uint32_t>(sg.s0);
+                o.xh0 = j * sg.G;
+                o.base = sg.off + static_cast<uint32_t>((in ? lr : 0) + static_cast<int>(sg.hd)) * row_bytes<LAYOUT>(sg);
+                uint32_t f = 0;
+                if (in) {
+                    f = SL_IN | SL_VAL | ((grow & 1u) ? SL_ODD_ROW : 0u) | (o.xh0 == 0 ? SL_ROW_FIRST : 0u) |
+                        (o.xh0 + sg.G == sg.half ? SL_ROW_LAST : 0u);
+                    if (lr == -1 || lr == R) {
+                        f |= SL_PH_B | SL_REPLICA;
+                    } else {
+                        if (lr >= 1 && lr <= R - 2) f |= SL_PH_A;
+                        if (lr == 0 || lr == R - 1) f |= SL_PH_B;
+                        if (lr <= 1 || lr >= R - 2) f |= SL_PH_C;
+                        if (lr >= 2 && lr <= R - 3) f |= SL_PH_D;
+                    }
+                }
+                if (__any_sync(0xffffffffu, in)) f |= SL_WARP_IN;
+                if (LAYOUT != ISING_INT8 && sg.G == 2 &&
+                    __all_sync(0xffffffffu, !in || (o.xh0 & 31u) == 2u * (threadIdx.x & 15u)))
+                    f |= SL_MS_PAIR;
+                o.flags = f;
             } else {
                 setup_slot<LAYOUT>(S, nseg, prefix_end, threadIdx.x + static_cast<uint64_t>(k) * blockDim.x, slot[k]);
             }
@@ -894,6 +1057,69 @@ __global__ void __launch_bounds__(MODE == 5 ? 1024 : (SMAX >= ((MODE == 1 || MOD
                 if (s_abort) goto done;
             }
             if (a.measure_every && (a.sweep0 + t + 1) % a.measure_every == 0) {
+                measure_strips<LAYOUT>(smem, S, nseg, a, meas_idx, red);
+                meas_idx++;
+            }
+        }
+    }
+    if constexpr (MODE == 6) {
+        // the host chose this kernel for one strip of 4 .. 10 rows per block
+        // whose rows and halo copies fit the cells of mode6_row
+        const SegLocal &sg = S[0];
+        const uint32_t spr = sg.half / sg.G;
+        const bool ok = resident && nseg == 1 && sg.up >= 0 && sg.R >= 4 && sg.R <= 10 && spr % 32 == 0 &&
+                        4 * spr <= blockDim.x && 6 * (row_bytes<LAYOUT>(sg) / 4) <= blockDim.x &&
+                        prefix_end == static_cast<uint64_t>(sg.R) * spr;
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) atomicCAS(a.err, 0, RNG_EINVAL);
+            goto done;
+        }
+        mode6_table<LAYOUT>(smem, sg, a, m6tab);
+        __syncthreads();
+        const Mode6Tab &e6 = m6tab[threadIdx.x];
+        bool polled = false;  // the halo already holds the neighbours' rows of the last sweep
+        for (uint64_t t = 0; t < a.n_sweeps; t++) {
+            // colour 0 of the rows between the edges: own rows only
+#pragma unroll
+            for (int k = 0; k < SMAX; k++)
+                if (slot[k].flags & SL_PH_A) update_slot<KIND, LAYOUT>(smem, sg, slot[k], gen[k], 0, lane);
+            // the neighbours' rows after the last sweep (the first sweep of a
+            // launch has them from the lattice itself)
+            if (t > 0 && !polled && !poll6(smem, a, e6, static_cast<uint32_t>((t - 1) & 1), static_cast<uint32_t>(t)))
+                s_abort = 1;
+            polled = false;
+            __syncthreads();
+            if (s_abort) goto done;
+            // colour 0 of the edge rows and of the halo rows -1 and R
+#pragma unroll
+            for (int k = 0; k < SMAX; k++)
+                if (slot[k].flags & SL_PH_B) update_slot<KIND, LAYOUT>(smem, sg, slot[k], gen[k], 0, lane);
+            __syncthreads();
+            // colour 1 of rows 0, 1, R-2, R-1; the halo copies draw the numbers
+            // their owners take now and update nothing (colour 1 of the halo
+            // comes with the next exchange)
+#pragma unroll
+            for (int k = 0; k < SMAX; k++) {
+                if (slot[k].flags & SL_PH_C) {
+                    update_slot<KIND, LAYOUT>(smem, sg, slot[k], gen[k], 1, lane);
+                } else if (slot[k].flags & SL_REPLICA) {
+                    for (uint32_t g = 0; g < sg.G; g++) (void)gen[k].next();
+                }
+            }
+            __syncthreads();
+            publish6(smem, sg, a, e6, static_cast<uint32_t>(t & 1), static_cast<uint32_t>(t + 1));
+            // colour 1 of rows 2 .. R-3 while the published words travel
+#pragma unroll
+            for (int k = 0; k < SMAX; k++)
+                if (slot[k].flags & SL_PH_D) update_slot<KIND, LAYOUT>(smem, sg, slot[k], gen[k], 1, lane);
+            __syncthreads();
+            if (a.measure_every && (a.sweep0 + t + 1) % a.measure_every == 0) {
+                // the energy reads colour 1 of the halo rows: take this
+                // sweep's rows first
+                if (!poll6(smem, a, e6, static_cast<uint32_t>(t & 1), static_cast<uint32_t>(t + 1))) s_abort = 1;
+                polled = true;
+                __syncthreads();
+                if (s_abort) goto done;
                 measure_strips<LAYOUT>(smem, S, nseg, a, meas_idx, red);
                 meas_idx++;
             }
@@ -1089,7 +1315,8 @@ done:
     if (resident) {
 #pragma unroll
         for (int k = 0; k < SMAX; k++)
-            if (slot[k].in() && slot[k].s < S[slot[k].seg].n_inst) gen[k].store(a.lats[S[slot[k].seg].lat].rng, slot[k].s);
+            if (slot[k].in() && !(slot[k].flags & SL_REPLICA) && slot[k].s < S[slot[k].seg].n_inst)
+                gen[k].store(a.lats[S[slot[k].seg].lat].rng, slot[k].s);
     }
 }
 

@@ -33,11 +33,14 @@ def test_cache_hit_miss_and_keys_without_gpu(R, tmp_path, monkeypatch):
     monkeypatch.setattr(R, "ising_autotune", tune)
     monkeypatch.setattr(R, "ising_get_launch", lambda h: {"threads": 256 * h, "ctas_per_sm": h, "min_sites": 1024})
     monkeypatch.setattr(R, "ising_set_launch", lambda h, t, c, m: calls["set"].append((h, t, c, m)))
+    monkeypatch.setattr(R, "ising_get_halo_depth", lambda h: 2)
+    monkeypatch.setattr(R, "ising_set_halo_depth", lambda h, d: calls["set"].append((h, "depth", d)))
     path = str(tmp_path / "sub" / "autotune.json")
     a = R.ising_autotune_cached(1, path=path, device="fake/152")
-    assert a == {"threads": 256, "ctas_per_sm": 1, "min_sites": 1024, "cached": False} and calls["tune"] == 1
+    assert a == {"threads": 256, "ctas_per_sm": 1, "min_sites": 1024, "halo_depth": 2, "cached": False}
+    assert calls["tune"] == 1
     b = R.ising_autotune_cached(1, path=path, device="fake/152")
-    assert b["cached"] and calls["tune"] == 1 and calls["set"] == [(1, 256, 1, 1024)]
+    assert b["cached"] and calls["tune"] == 1 and calls["set"] == [(1, 256, 1, 1024), (1, "depth", 2)]
     # other lattices or another device: a miss, stored beside the first entry
     c = R.ising_autotune_cached(2, path=path, device="fake/152")
     d = R.ising_autotune_cached(1, path=path, device="other/76")

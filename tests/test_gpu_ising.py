@@ -239,8 +239,9 @@ def test_split_role_exact_checkerboard(R, L, G, kind, layout):
         R.ising_destroy(h)
 
 
-def test_default_shape_at_L1024_is_split_role(R):
-    # one strip of 6 or 7 rows per SM, 1024 threads
+def test_default_shape_at_L1024_is_one_strip_per_sm(R):
+    # one strip of 6 or 7 rows per SM, 1024 threads (a halo of two rows: one
+    # exchange per sweep)
     import torch
     h = R.ising_create(1024, BETA_C, 0, O.XORWOW, 0, SEED, 2)
     try:
@@ -327,10 +328,43 @@ def test_batch_in_several_waves_matches_lattices_alone(R):
         R.ising_destroy(h)
 
 
-def test_strip_that_stops_publishing_times_out_without_hanging(R):
+@pytest.mark.parametrize("L,G", [(1024, 2), (768, 2), (1024, 4)])
+@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("kind,flags", [(O.XORWOW, 0), (O.XS1024W, 0), (O.LCG32, 0), (O.PHILOX4X32_10, 0),
+                                        (O.PHILOX4X32_7, O.PHILOX_INTRINSIC_KEY)])
+def test_halo_depths_give_the_same_chain(R, L, G, layout, kind, flags):
+    # one strip of 5 .. 7 rows per SM: boundary rows exchanged after every
+    # half-sweep (depth 1) or once per sweep with the rows just outside each
+    # strip updated from copies of the neighbours' streams (depth 2); both
+    # equal the oracle, measurements included
+    ref, acc, nm = O.ising_run(L, BETA_C, kind, SEED, 40, G=G, flags=flags, measure_every=3)
+    for depth in (1, 2, 0):
+        h = R.ising_create(L, BETA_C, layout, kind, flags, SEED, G)
+        try:
+            R.ising_set_launch(h, 1024, 1, 0)
+            R.ising_set_halo_depth(h, depth)
+            info = R.ising_plan_info(h)
+            assert info["threads"] == 1024 and info["blocks"] == info["strips"] >= 2
+            R.ising_sweep(h, 40, 3)
+            obs = R.ising_observables(h)
+            assert np.array_equal(R.ising_get_spins(h), ref), depth
+            assert obs["acc"] == acc.tolist() and obs["n_meas"] == nm, depth
+        finally:
+            R.ising_destroy(h)
+    with pytest.raises(R.RngError):
+        h = R.ising_create(64, BETA_C, 0, O.XORWOW, 0, SEED, 2)
+        try:
+            R.ising_set_halo_depth(h, 3)
+        finally:
+            R.ising_destroy(h)
+
+
+@pytest.mark.parametrize("depth", [1, 2])
+def test_strip_that_stops_publishing_times_out_without_hanging(R, depth):
     import time
     h = R.ising_create(1024, 0.4, 0, O.XORWOW, 0, SEED, 2)
     try:
+        R.ising_set_halo_depth(h, depth)
         info = R.ising_plan_info(h)
         assert info["strips"] >= 2
         R.ising_debug_mute_strip(h, 1, 20_000_000)  # 20 ms budget
