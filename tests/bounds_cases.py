@@ -57,11 +57,12 @@ def gen_case(kind, n, K, out, layout):
     return bool(np.array_equal(got.view(np.uint32), want.view(np.uint32)))
 
 
-def ising_case(L, G, kind, layout, sweeps, hits=0, strips=0, launch=None):
+def ising_case(L, G, kind, layout, sweeps, hits=0, strips=0, launch=None, depth=0):
     h = R.ising_create(L, 0.4, layout, kind, 0, SEED, G)
     try:
         if launch:
             R.ising_set_launch(h, *launch)
+        R.ising_set_halo_depth(h, depth)
         if hits:
             R.ising_sweep_multihit(h, sweeps, hits, strips, 1)
         else:
@@ -100,11 +101,14 @@ def main():
         cases += 1
         if not ising_case(L, G, kind, layout, 12):
             failed.append(f"ising L={L} G={G} kind={kind} layout={layout}")
-    # one strip per block of 1024 threads, roles split by warp, a polling warp
-    for L, G, kind, layout in [(1024, 2, O.XORWOW, 0), (768, 2, O.PHILOX4X32_10, 1), (512, 1, O.LCG32, 0)]:
+    # one strip per block of 1024 threads: roles split by warp with a polling
+    # warp (halo depth 1), or a halo of two rows (depth 2)
+    for L, G, kind, layout, depth in [(1024, 2, O.XORWOW, 0, 1), (768, 2, O.PHILOX4X32_10, 1, 1), (512, 1, O.LCG32, 0, 1),
+                                      (1024, 2, O.XORWOW, 0, 2), (1024, 2, O.XS1024W, 1, 2), (768, 2, O.PHILOX4X32_10, 0, 2),
+                                      (1024, 4, O.MWC, 1, 2)]:
         cases += 1
-        if not ising_case(L, G, kind, layout, 6, launch=(1024, 1, 0)):
-            failed.append(f"split-role ising L={L} G={G} kind={kind} layout={layout}")
+        if not ising_case(L, G, kind, layout, 6, launch=(1024, 1, 0), depth=depth):
+            failed.append(f"one-strip ising L={L} G={G} kind={kind} layout={layout} depth={depth}")
     for L, kind, layout, hits, strips in [(64, O.XORWOW, 0, 3, 4), (64, O.XS1024W, 1, 2, 2), (128, O.LCG32, 0, 1, 8)]:
         cases += 1
         if not ising_case(L, 2, kind, layout, 4, hits, strips):
