@@ -558,11 +558,25 @@ def ising_section(R, torch, args):
                     nplain = max(20, n // 10)
                     ms_plain = _time_sweeps(R, torch, h, nplain, plain=True)
                     key = f"L{L}/{lname}/{_ising_kind_name(R, kind, flags)}"
+                    by_depth = {}
+                    if L == 1024:
+                        # both exchange variants in the one-strip-per-SM shape:
+                        # after every half-sweep (1), once per sweep with the
+                        # two-row halo (2)
+                        launch, depth = R.ising_get_launch(h), R.ising_get_halo_depth(h)
+                        R.ising_set_launch(h, 1024, 1, 0)
+                        for d in (1, 2):
+                            R.ising_set_halo_depth(h, d)
+                            R.ising_sweep(h, 50)
+                            by_depth[f"depth{d}"] = round(L * L * n / (_time_sweeps(R, torch, h, n) * 1e6), 2)
+                        R.ising_set_launch(h, launch["threads"], launch["ctas_per_sm"], launch["min_sites"])
+                        R.ising_set_halo_depth(h, depth)
                     out[key] = {
                         "flips_per_ns": round(L * L * n / (ms * 1e6), 2),
                         "us_per_sweep": round(1e3 * ms / n, 3),
                         "plain_flips_per_ns": round(L * L * nplain / (ms_plain * 1e6), 3),
                         "sweeps_timed": n, "launch": tuned, "halo_depth": R.ising_get_halo_depth(h),
+                        **({"flips_per_ns_by_halo_depth": by_depth} if by_depth else {}),
                         "plan": R.ising_plan_info(h),
                     }
                 finally:
