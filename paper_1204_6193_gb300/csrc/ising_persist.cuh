@@ -40,14 +40,17 @@ struct PersistArgs {
                                // (mode 4); 3: one strip per block of split roles with a polling warp (mode 5)
 };
 
-struct SegLocal {              // per-segment constants held in shared memory
-    uint32_t L, half, W, G, y0, R, off, lat, coarse;
-    uint32_t hd;               // halo rows above and below the strip (1; 2 in kernel mode 6)
-    uint32_t pstride;          // plane 1 - plane 0 offset in shared memory
-    int32_t up, down, gid;
-    uint64_t s0, prefix, T4, T8;
+struct alignas(16) SegLocal {  // per-segment constants held in shared memory
+    // the site update's constants first, as two 16-byte words (one shared
+    // load each): half, G, pstride, W and t4, t8, a_max, R
+    uint32_t half, G, pstride, W;
     uint32_t t4, t8;           // T4, T8 below 2^32 (beta > 0)
     int32_t a_max;             // flips with a <= a_max always: 0, or 2 / 4 where T4 / T8 = 2^32
+    uint32_t R;
+    uint32_t L, y0, off, lat, coarse;
+    uint32_t hd;               // halo rows above and below the strip (1; 2 in kernel mode 6)
+    int32_t up, down, gid;
+    uint64_t s0, prefix, T4, T8;
     uint64_t n_valid, n_inst;  // streams with sites; generator instances
     DevParams rng;             // the lattice's generator (position at launch start)
 };
@@ -273,9 +276,12 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
                                             int c, int lane)
 {
     const uint32_t p = (c + ((sl.flags & SL_ODD_ROW) ? 1u : 0u)) & 1u;
-    const uint32_t half = sg.half, G = sg.G;
+    // (the field order of SegLocal makes these two 16-byte shared loads)
+    const uint4 q0 = *reinterpret_cast<const uint4 *>(&sg.half), q1 = *reinterpret_cast<const uint4 *>(&sg.t4);
+    const uint32_t half = q0.x, G = q0.y, pstride = q0.z, W_ = q0.w;
+    const uint32_t t4_ = q1.x, t8_ = q1.y;
+    const int a_max_ = static_cast<int>(q1.z);
     const uint64_t T4 = sg.T4, T8 = sg.T8;
-    const uint32_t pstride = sg.pstride;
     uint8_t *own_row = smem + sl.base + (c ? pstride : 0u);
     uint8_t *o_row = smem + sl.base + (c ? 0u : pstride);
     if (LAYOUT == ISING_INT8) {
@@ -322,8 +328,8 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
             const uint32_t k0 = k2 & 0xffu, k1 = k2 >> 8;
             // flip when 4 - 2k <= a_max (every k >= 2, and every k where
             // T = 2^32), else iff r < T(4 - 2k): T8 for k = 0, T4 for k = 1
-            const uint32_t kf = static_cast<uint32_t>(4 - sg.a_max);
-            const uint32_t t4 = sg.t4, t8 = sg.t8;
+            const uint32_t kf = static_cast<uint32_t>(4 - a_max_);
+            const uint32_t t4 = t4_, t8 = t8_;
             const bool f0 = k0 >= kf || r0 < (k0 ? t4 : t8), f1 = k1 >= kf || r1 < (k1 ? t4 : t8);
             if (f0 || f1) {
                 // -s = s ^ 0xfe for s = 0x01, 0xff
@@ -366,7 +372,7 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
         // k = 0 (iff r < T8).  Each lane sets its two draws' acceptance bits
         // at its sites' positions; one OR-reduction per half-warp then gives
         // the word's flips, which its first lane applies.
-        const uint32_t W = sg.W;
+        const uint32_t W = W_;
         uint32_t *own = reinterpret_cast<uint32_t *>(own_row);
         const uint32_t *o = reinterpret_cast<const uint32_t *>(o_row);
         const uint32_t r0 = gen.next(), r1 = gen.next();
@@ -391,8 +397,8 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
             ge2 = c1 | c2 | t;
             // r < T8 <= T4 accepts at k = 0 and 1, r < T4 at k = 1 (k0 set,
             // k < 2); T = 2^32 (a_max) accepts every draw
-            const bool f4 = sg.a_max >= 2, f8 = sg.a_max >= 4;
-            const uint32_t t4 = sg.t4, t8 = sg.t8;
+            const bool f4 = a_max_ >= 2, f8 = a_max_ >= 4;
+            const uint32_t t4 = t4_, t8 = t8_;
             const uint32_t acc4 = ((f4 || r0 < t4) ? 1u : 0u) | ((f4 || r1 < t4) ? 2u : 0u);
             const uint32_t acc8 = ((f8 || r0 < t8) ? 1u : 0u) | ((f8 || r1 < t8) ? 2u : 0u);
             fl = ((k0 & (acc4 << b0)) | (acc8 << b0));
@@ -414,7 +420,7 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
     } else {
         // any G, site by site: the warp's 32 G sites are G consecutive words
         // of plane c, assembled by one OR-reduction each
-        const uint32_t W = sg.W;
+        const uint32_t W = W_;
         const uint32_t *own = reinterpret_cast<const uint32_t *>(own_row);
         const uint32_t *o = reinterpret_cast<const uint32_t *>(o_row);
         const uint32_t *ou = o - W, *od = o + W;
