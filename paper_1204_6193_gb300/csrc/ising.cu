@@ -484,10 +484,11 @@ int build_plan(ising_t h, int kind, int layout, const std::vector<uint32_t> &ids
         // a single lattice without a tuned shape takes the shapes the
         // autotuner finds: one block with one stream per thread when its
         // streams fit (no exchange at all); when one block per SM needs
-        // more than 1024 streams, one block of 1024 threads per SM whose
-        // last warp polls (kernel mode 5) if its strips fit that layout,
-        // else two blocks of 512 threads with two resident streams each per
-        // SM (all of these fit the device)
+        // more than 1024 streams, one block of 1024 threads per SM (a halo
+        // of two rows, kernel mode 6, or a polling last warp, mode 5; see
+        // materialize_plan) if its strips fit those layouts, else two blocks
+        // of 512 threads with two resident streams each per SM (all of these
+        // fit the device)
         const IsingLat &t = h->lats[ids[0]];
         const uint64_t n = t.nstreams;
         if (n <= 1024) {
