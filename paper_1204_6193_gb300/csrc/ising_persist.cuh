@@ -390,18 +390,21 @@ __device__ __forceinline__ void update_slot(uint8_t *smem, const SegLocal &sg, c
             const uint32_t nwi = p ? (wi + 1 == W ? 0u : wi + 1) : (wi == 0 ? W - 1 : wi - 1);
             const uint32_t nw = o[nwi];
             const uint32_t n2 = p ? __funnelshift_r(mw, nw, 1) : __funnelshift_l(nw, mw, 1);
-            const uint32_t a1 = ow ^ mw, a2 = ow ^ n2, a3 = ow ^ o[wi - W], a4 = ow ^ o[wi + W];
-            const uint32_t s1 = a1 ^ a2, c1 = a1 & a2, s2 = a3 ^ a4, c2 = a3 & a4;
-            const uint32_t k0 = s1 ^ s2, t = s1 & s2;
-            // k >= 2: c1 c2 | (c1 ^ c2) t | (c1 ^ c2 ^ t) = c1 | c2 | t
-            ge2 = c1 | c2 | t;
-            // r < T8 <= T4 accepts at k = 0 and 1, r < T4 at k = 1 (k0 set,
-            // k < 2); T = 2^32 (a_max) accepts every draw
+            const uint32_t up = o[wi - W], dn = o[wi + W];
+            // anti-aligned indicators a1..a4 = ow ^ (mw, n2, up, dn), added
+            // as two half adders: s = a1 ^ a2 (ow cancels), c = a1 & a2
+            const uint32_t s1 = mw ^ n2, c1 = (ow ^ mw) & (ow ^ n2);
+            const uint32_t s2 = up ^ dn, c2 = (ow ^ up) & (ow ^ dn);
+            const uint32_t k0 = s1 ^ s2;  // the low bit of k
+            // k >= 2: c1 c2 | (c1 ^ c2) t | (c1 ^ c2 ^ t) = c1 | c2 | t, t = s1 s2
+            ge2 = c1 | c2 | (s1 & s2);
+            // below k = 2 a site flips iff r < T4 (k = 1: k0 set) or r < T8
+            // (k = 0); T = 2^32 (a_max) accepts every draw
             const bool f4 = a_max_ >= 2, f8 = a_max_ >= 4;
-            const uint32_t t4 = t4_, t8 = t8_;
-            const uint32_t acc4 = ((f4 || r0 < t4) ? 1u : 0u) | ((f4 || r1 < t4) ? 2u : 0u);
-            const uint32_t acc8 = ((f8 || r0 < t8) ? 1u : 0u) | ((f8 || r1 < t8) ? 2u : 0u);
-            fl = ((k0 & (acc4 << b0)) | (acc8 << b0));
+            const uint32_t kb = k0 >> b0;
+            const bool p0 = (kb & 1u) ? (f4 || r0 < t4_) : (f8 || r0 < t8_);
+            const bool p1 = (kb & 2u) ? (f4 || r1 < t4_) : (f8 || r1 < t8_);
+            fl = ((p0 ? 1u : 0u) | (p1 ? 2u : 0u)) << b0;
         }
         // the word's flips: k >= 2 (the same in all its lanes) and the
         // lanes' accepted draws
