@@ -296,8 +296,8 @@ int ising_set_launch(ising_t h, uint32_t threads, int ctas_per_sm, uint32_t min_
  * draw exactly as their owners do (the spins are the same either way).
  * Depth 2 needs a plan of one strip of 4 to 10 rows per block of 1024
  * threads whose rows hold at most 256 streams (else depth 1 runs).  0 (the
- * default) takes depth 2 there for the generators with cheap draws (LCG32,
- * LCG64, MWC, XORWOW); ising_autotune times both.  Other values:
+ * default) takes depth 2 there for every generator but Philox4x32-10 on
+ * int8 spins; ising_autotune times both.  Other values:
  * RNG_EINVAL.  Takes effect at the next sweep (replans). */
 int ising_set_halo_depth(ising_t h, uint32_t depth);
 

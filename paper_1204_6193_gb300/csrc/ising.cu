@@ -643,12 +643,12 @@ int materialize_plan(ising_t h, int kind, int layout, const std::vector<std::vec
     // the same with a halo of two rows (kernel mode 6): every block one
     // strip of 4 .. 10 rows whose rows and the two halo copies fill the
     // cells of the kernel's layout (four cells of one row's streams per slot)
-    // (automatic choice: the generators whose draws cost a few instructions;
-    // for Philox and the 1024-bit generator the copies' extra draws cost more
-    // than the exchanges they save, measured on GB300)
-    const bool cheap_draws = kind == RNG_LCG32 || kind == RNG_LCG64 || kind == RNG_MWC || kind == RNG_XORWOW;
+    // (automatic choice: every generator but Philox4x32-10 on int8 spins,
+    // whose copies' extra ten-round draws cost more than the exchanges they
+    // save, measured on GB300)
+    const bool deep_auto = !(kind == RNG_PHILOX4X32_10 && layout == ISING_INT8);
     bool deep = !multihit && threads == 1024 && !blocks.empty() &&
-                (h->cfg_halo_depth == 2 || (h->cfg_halo_depth == 0 && cheap_draws));
+                (h->cfg_halo_depth == 2 || (h->cfg_halo_depth == 0 && deep_auto));
     size_t deep_smem = 0;
     for (size_t b = 0; b < blocks.size() && deep; b++) {
         if (blocks[b].size() != 1) {

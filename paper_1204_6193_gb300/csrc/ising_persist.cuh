@@ -223,7 +223,7 @@ enum : uint32_t {
     // kernel mode 6 (halo of two rows, one exchange per sweep): the phases a slot takes part in
     SL_PH_A = 2048u,    // colour 0, the rows between the first and the last (no halo needed)
     SL_PH_B = 4096u,    // colour 0, the first and last rows and the halo rows -1 and R (after the poll)
-    SL_PH_C = 8192u,    // colour 1, rows 0, 1, R-2, R-1 (published next)
+    SL_PH_C = 8192u,    // colour 1, rows 0, 1, R-2, R-1 (the rows published)
     SL_PH_D = 16384u,   // colour 1, rows 2 .. R-3
     SL_REPLICA = 32768u // a copy of a neighbour's stream (halo row -1 or R): never stored
 };
@@ -684,9 +684,9 @@ __device__ __forceinline__ bool poll_rows_warp(uint8_t *smem, const SegLocal &sg
 // Each strip also updates colour 0 of the rows just outside it (-1 and R),
 // with copies of the neighbours' streams that draw exactly as the owners
 // do, so that colour 1 of its own rows needs nothing from outside; after
-// colour 1 of its rows 0, 1, R-2 and R-1 it publishes six half-rows, which
-// the neighbours take into rows -2 .. -1 and R .. R+1 before their next
-// sweep's edge rows.
+// colour 1 of its rows it publishes six half-rows (rows 0, 1, R-2, R-1),
+// which the neighbours take into rows -2 .. -1 and R .. R+1 before their
+// next sweep's edge rows.
 constexpr int kNoRow = -1000;
 
 // Local row held by slot k, cell `cell` (cell = thread / streams per row) of
@@ -1104,12 +1104,16 @@ __global__ void __launch_bounds__(MODE >= 5 ? 1024 : (SMAX >= ((MODE == 1 || MOD
             for (int k = 0; k < SMAX; k++)
                 if (slot[k].flags & SL_PH_B) update_slot<KIND, LAYOUT>(smem, sg, slot[k], gen[k], 0, lane);
             __syncthreads();
-            // colour 1 of rows 0, 1, R-2, R-1; the halo copies draw the numbers
-            // their owners take now and update nothing (colour 1 of the halo
-            // comes with the next exchange)
+            // colour 1 of all rows in one pass; the halo copies draw the
+            // numbers their owners take now and update nothing (colour 1 of
+            // the halo comes with the next exchange).  Publishing after the
+            // whole pass costs one barrier less per sweep than publishing
+            // rows 0, 1, R-2, R-1 first (measured faster); the words then
+            // travel while the next sweep's rows between the edges update
+            // (they read none of the published rows' colour-0 sites).
 #pragma unroll
             for (int k = 0; k < SMAX; k++) {
-                if (slot[k].flags & SL_PH_C) {
+                if (slot[k].flags & (SL_PH_C | SL_PH_D)) {
                     update_slot<KIND, LAYOUT>(smem, sg, slot[k], gen[k], 1, lane);
                 } else if (slot[k].flags & SL_REPLICA) {
                     for (uint32_t g = 0; g < sg.G; g++) (void)gen[k].next();
@@ -1117,11 +1121,6 @@ __global__ void __launch_bounds__(MODE >= 5 ? 1024 : (SMAX >= ((MODE == 1 || MOD
             }
             __syncthreads();
             publish6(smem, sg, a, e6, static_cast<uint32_t>(t & 1), static_cast<uint32_t>(t + 1));
-            // colour 1 of rows 2 .. R-3 while the published words travel
-#pragma unroll
-            for (int k = 0; k < SMAX; k++)
-                if (slot[k].flags & SL_PH_D) update_slot<KIND, LAYOUT>(smem, sg, slot[k], gen[k], 1, lane);
-            __syncthreads();
             if (a.measure_every && (a.sweep0 + t + 1) % a.measure_every == 0) {
                 // the energy reads colour 1 of the halo rows: take this
                 // sweep's rows first
