@@ -119,10 +119,13 @@ def test_chunk_boundary_and_measurement_phase(R):
     assert obs["acc"] == acc.tolist() and obs["n_meas"] == nm
 
 
-def test_many_short_launches(R):
-    # one-sweep launches back to back: each launch restarts its halo tags
+@pytest.mark.parametrize("layout", [0, 1])
+def test_many_short_launches(R, layout):
+    # one-sweep launches back to back: each launch restarts its halo tags;
+    # odd sweep counts per launch (the int8 two-row-halo loop takes two
+    # sweeps per pass)
     ref, _, _ = O.ising_run(1024, 0.44, O.XORWOW, SEED, 6)
-    h = R.ising_create(1024, 0.44, 1, O.XORWOW, 0, SEED, 2)
+    h = R.ising_create(1024, 0.44, layout, O.XORWOW, 0, SEED, 2)
     try:
         for n in (1, 1, 1, 3):
             R.ising_sweep(h, n)
